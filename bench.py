@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Throughput of the Deep Potential MD step on one GB300 (or N independent replicas).
+
+One step = one velocity-Verlet NVE step: half kick, drift, neighbour rebuild every
+10 steps (else the skin check), the list filter, environment matrix, embedding net,
+descriptor, fitting net, force/virial backward, half kick.  Metric: atom-steps/s
+(atoms x steps / s) and ns/day at dt = 0.5 fs.  Inputs are synthetic (seeded) with
+the paper's sizes; the working set of one step (>1 GB) is larger than L2, so no
+explicit flush is needed between timed iterations.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+                  [--workload cu131k|water12k] [--precision mix_bf16|mix_fp16|fp32|fp64]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DP energy+force atom-steps/s and ns/day on 1 GB300: mixed vs FP64 at stated error"
+DT_FS = 0.5
+REBUILD = 10
+
+WORKLOADS = {
+    "cu131k": "Cu FCC 32x32x32 cells (131,072 atoms), a 3.634 A, sigma 0.08 A, r_c 8 A, r_s 2 A, sel 512, "
+              "NVE dt 0.5 fs from 300 K, rebuild every 10 steps, skin 2 A",
+    "water12k": "4096 H2O (12,288 atoms) at 1.0 g/cm3, r_c 6 A, r_s 0.5 A, sel 46/92, NVE dt 0.5 fs from 300 K, "
+                "rebuild every 10 steps, skin 2 A",
+}
+
+# per real neighbour: embedding recompute + backward MACs (x2 FLOP); forward embedding + T
+EMB_BWD_FLOP_PER_NEIGHBOUR = 2 * (6275 + 7075)
+EMB_FWD_FLOP_PER_NEIGHBOUR = 2 * (6275 + 400)
+FIT_FLOP_PER_ATOM = 2 * (499440 * 2)  # forward + data-gradient backward
+
+
+def load_workload(name):
+    from paper_2410_22867_gb300 import synth
+    if name == "cu131k":
+        s = synth.copper_fcc(32, 0)
+        w = synth.copper_weights(1001)
+    elif name == "water12k":
+        s = synth.water_box(4096, 0)
+        w = synth.water_weights(1001)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    v = synth.maxwell_boltzmann(s.masses()[s.types], 300.0, 1)
+    return s, w, v
+
+
+def cpu_sample(name):
+    """A bounded CPU sample of the same workload: same model and density, smaller box."""
+    from paper_2410_22867_gb300 import synth
+    if name == "cu131k":
+        return synth.copper_fcc(8, 0), synth.copper_weights(1001)
+    return synth.water_box(256, 0), synth.water_weights(1001)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            tok = [t.strip() for t in line.split(",")]
+            if len(tok) >= 9:
+                rows.append(tok)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        if torch.cuda.is_available():
+            torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_rate(name, seconds_target=None, nsteps=1):
+    """Oracle (FP64 CPU) atom-steps/s on the bounded sample; returns (rate, cores, sample, per_step_s)."""
+    import oracle
+    s, w = cpu_sample(name)
+    m = oracle.Model(w.to_blob())
+    m.compute(s.coords, s.types, s.box)  # warm
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        m.compute(s.coords, s.types, s.box)
+    dt = time.perf_counter() - t0
+    return s.natoms * nsteps / dt, oracle.get_threads(), \
+        f"{s.natoms}-atom periodic box of the same model and density, full energy+force evaluation", dt / nsteps
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    oracle.set_threads(len(os.sched_getaffinity(0)))
+    rate_w, cores, sample, per = oracle_rate(args.workload, nsteps=1)
+    for _ in range(max(0, args.warmup - 1)):
+        oracle_rate(args.workload, nsteps=1)
+    rate, cores, sample, per = oracle_rate(args.workload, nsteps=max(1, args.steps))
+    line = {"metric": METRIC, "value": rate, "unit": "atom-steps/s", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "sample": sample, "threads": cores},
+            "cpu_baseline": {"value": rate, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def neighbour_count(m):
+    nl, _ = m.get_nlist()
+    return int((nl >= 0).sum().item())
+
+
+def run_mine(args, world, rank, local):
+    import torch
+    import paper_2410_22867_gb300 as dp
+    dp.build()
+    s, w, v0 = load_workload(args.workload)
+    N = s.natoms
+    prec = args.precision
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        m = dp.DPModel(w, prec, max_atoms=N, skin=2.0, stream=stream)
+        x = torch.tensor(s.coords, device="cuda")
+        v = torch.tensor(v0, device="cuda")
+        t = torch.tensor(s.types, device="cuda")
+        st = m.md_state(x, v, t, s.box, s.masses(), rebuild_every=REBUILD)
+        m.verlet(st, DT_FS, args.warmup, capture_graph=True)  # warm-up (builds lists, captures graphs)
+        st.resume = 1
+        n_neigh = neighbour_count(m)
+        launches0 = m.kernel_launches()
+        clocks = ClockSampler(local)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        clocks.start()
+        ev0.record(stream)
+        m.verlet(st, DT_FS, args.steps, capture_graph=True, sync=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ck = clocks.stop()
+        m.sync()
+        t_ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+        launches = m.kernel_launches() - launches0
+        ms_step = t_ms / args.steps
+        value = world * N * args.steps / (t_ms * 1e-3)
+        phases = m.phase_times(3)  # [format, descriptor, fitting, embed backward, total]
+
+    extra = {}
+    if rank == 0:
+        # dominant kernel and its roofline
+        names = ["format", "descriptor", "fitting", "embedding_backward"]
+        k = int(np.argmax(phases[:4]))
+        pk, src = peaks()
+        if prec in ("fp32", "fp64"):
+            sm_mhz = pk.get("sm_max_mhz", 2070.0)
+            lanes = 128 if prec == "fp32" else 2  # FP32 FMA lanes per SM; FP64 ~ 1.25 TF/s per GPU
+            peak_tf = 152 * lanes * 2 * sm_mhz * 1e6 / 1e12
+            flops = {1: n_neigh * EMB_FWD_FLOP_PER_NEIGHBOUR, 2: N * FIT_FLOP_PER_ATOM,
+                     3: n_neigh * EMB_BWD_FLOP_PER_NEIGHBOUR}.get(k, 0)
+            achieved = flops / (phases[k] * 1e-3) / 1e12 if phases[k] > 0 and flops else 0.0
+            roof = {"bound": "alu", "kernel": names[k], "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                    "frac": achieved / peak_tf, "traffic": None,
+                    "peak_source": f"derived: 152 SMs x {lanes} {prec} FMA lanes x 2 x {sm_mhz:.0f} MHz"}
+        else:
+            flops = {1: n_neigh * EMB_FWD_FLOP_PER_NEIGHBOUR, 2: N * FIT_FLOP_PER_ATOM,
+                     3: n_neigh * EMB_BWD_FLOP_PER_NEIGHBOUR}.get(k, 0)
+            achieved = flops / (phases[k] * 1e-3) / 1e12 if phases[k] > 0 and flops else 0.0
+            peak_tf = pk.get("bf16_tflops_sustained", 1700.0)
+            roof = {"bound": "tensor", "kernel": names[k], "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                    "frac": achieved / peak_tf, "traffic": None,
+                    "peak_source": f"{src} bf16 sustained"}
+        extra["roofline"] = roof
+        extra["phases_ms"] = dict(zip(names + ["evaluation"], [round(p, 4) for p in phases]))
+        # FP64 comparison (speed and error) on the same configuration
+        if not args.no_fp64 and prec != "fp64":
+            extra["fp64"] = fp64_compare(args, s, w, v0, m, stream)
+        # end-to-end through the public API with host buffers
+        extra["e2e"] = e2e(m, s, stream, args.e2e_steps)
+        # CPU oracle baseline
+        try:
+            import oracle
+            oracle.build()
+            oracle.set_threads(len(os.sched_getaffinity(0)))
+            rate, cores, sample, _ = oracle_rate(args.workload, nsteps=1)
+            extra["cpu_baseline"] = {"value": rate, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
+                                     "sample": sample}
+        except Exception as e:  # noqa: BLE001
+            extra["cpu_baseline"] = {"value": None, "unit": "atom-steps/s", "cores": 0, "kind": "oracle",
+                                     "sample": f"unavailable: {e}"}
+        dtype = {"fp64": "f64", "fp32": "f32", "mix_bf16": "bf16", "mix_fp16": "f16"}[prec]
+        line = {"metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+                "config": {"workload": WORKLOADS[args.workload], "precision": prec, "natoms": N, "dt_fs": DT_FS,
+                           "rebuild_every": REBUILD, "real_neighbours": n_neigh,
+                           "l2": "working set per step > 1 GB, larger than the 129 MB L2; no flush",
+                           "parallelism": "replicas" if world > 1 else "1 GPU"},
+                "ns_per_day": (1e3 / ms_step) * DT_FS * 86400 * 1e-6,
+                "gpu_launches": launches, "clocks": ck}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+
+
+def fp64_compare(args, s, w, v0, m_mixed, stream):
+    import torch
+    import paper_2410_22867_gb300 as dp
+    N = s.natoms
+    with torch.cuda.stream(stream):
+        m64 = dp.DPModel(w, "fp64", max_atoms=N, stream=stream)
+        x = torch.tensor(s.coords, device="cuda")
+        t = torch.tensor(s.types, device="cuda")
+        r64 = m64.compute(x, t, s.box)
+        rmx = m_mixed.compute(x, t, s.box)
+        dF = (rmx["forces"] - r64["forces"])
+        rmse = float(torch.sqrt((dF ** 2).mean()).item())
+        rms = float(torch.sqrt((r64["forces"] ** 2).mean()).item())
+        de = abs(rmx["energy"].item() - r64["energy"].item()) / N
+        dEi = float((rmx["atom_energy"] - r64["atom_energy"]).abs().max().item())
+        xx = torch.tensor(s.coords, device="cuda")
+        vv = torch.tensor(v0, device="cuda")
+        st = m64.md_state(xx, vv, t, s.box, s.masses(), rebuild_every=REBUILD)
+        m64.verlet(st, DT_FS, 1, capture_graph=True)
+        st.resume = 1
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        m64.verlet(st, DT_FS, args.fp64_steps, capture_graph=True, sync=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        m64.sync()
+        ms = ev0.elapsed_time(ev1) / args.fp64_steps
+        m64.close()
+    rate = N / (ms * 1e-3)
+    return {"value": rate, "unit": "atom-steps/s", "ms_per_step": ms, "steps": args.fp64_steps,
+            "error_vs_fp64_gpu": {"force_rmse_eV_per_A": rmse, "force_rms_eV_per_A": rms,
+                                  "force_rel_rmse": rmse / rms if rms > 0 else None,
+                                  "energy_eV_per_atom": de, "max_atom_energy_eV": dEi}}
+
+
+def e2e(m, s, stream, nsteps):
+    """dp_compute through the public API with the coordinates in pinned host memory:
+    every step copies coordinates H2D, evaluates (rebuilding the list), and reads
+    energy and forces back D2H."""
+    import torch
+    N = s.natoms
+    host_x = torch.tensor(s.coords, dtype=torch.float64).pin_memory()
+    host_F = torch.empty(N, 3, dtype=torch.float64).pin_memory()
+    host_E = torch.empty(1, dtype=torch.float64).pin_memory()
+    with torch.cuda.stream(stream):
+        x = torch.empty(N, 3, dtype=torch.float64, device="cuda")
+        t = torch.tensor(s.types, device="cuda")
+        out = m.compute(x.copy_(host_x, non_blocking=True), t, s.box)  # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(nsteps):
+            x.copy_(host_x, non_blocking=True)
+            out = m.compute(x, t, s.box, sync=False)
+            host_F.copy_(out["forces"], non_blocking=True)
+            host_E.copy_(out["energy"], non_blocking=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        m.sync()
+    return {"value": N * nsteps / dt, "unit": "atom-steps/s", "h2d_bytes_per_step": 24 * N,
+            "d2h_bytes_per_step": 24 * N + 8, "steps": nsteps,
+            "path": "dp_compute per step (list rebuilt every call), coordinates from pinned host memory"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="cu131k", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=["mix_bf16", "mix_fp16", "fp32", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.precision is None:
+        args.precision = os.environ.get("DP_BENCH_PRECISION", "fp32")
+    world, rank, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_mine(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * dp.h -- C ABI of the GB300 Deep Potential library (libdpgb300.so).
+ *
+ * The library evaluates the per-atom energy, forces and virial of a
+ * smooth-edition two-body Deep Potential model and advances velocity-Verlet
+ * molecular dynamics with it, on one GPU.  This is the force-field evaluation
+ * of the paper's Section II-A and Fig. 1: the neighbour list within r_c, the
+ * environment matrix R with its smoothed first column, the three-layer
+ * embedding net, the descriptor, the three-layer fitting net giving E_i, and
+ * the forces F_i obtained by backward propagation (Fig. 1(b)); the MD step
+ * updates velocities and positions and reports pressure-related virials
+ * (Section II-A).  Sizes follow Section IV: r_c 6 A (water) / 8 A (Cu),
+ * neighbour caps 46/92 (water) and 512 (Cu), fitting net (240, 240, 240),
+ * skin 2 A.  Mixed precision follows Section III-B3 (FP32 descriptor and
+ * activations, 16-bit GEMM operands).
+ *
+ * Conventions for every entry point
+ *  - All array arguments are caller-owned.  "device" arrays must be device
+ *    memory of the model's GPU, valid until the model's stream reaches the
+ *    call.  "host" arrays are read before the call returns.
+ *  - Calls are asynchronous on the stream given to dp_create (NULL = the
+ *    legacy default stream).  Argument errors are returned synchronously.
+ *    Errors detected on the device (neighbour overflow, skin exceeded) are
+ *    sticky: dp_sync() waits for the stream and returns them, and clears them.
+ *  - Units: Angstrom, eV, fs, amu.  Forces are eV/A; the virial is in eV and
+ *    is the negative strain derivative of the energy, Xi = -sum_pairs g (x) d
+ *    with g = dE/dd for the pair vector d = x_j + n*L - x_i.
+ *  - Boxes are 3x3 row-major; only orthorhombic boxes are supported
+ *    (off-diagonal entries must be 0, else DP_ERR_UNSUPPORTED).
+ *  - Atom arrays are in the caller's order; the library sorts atoms by type
+ *    internally and un-permutes every output.
+ *  - No call allocates device memory after dp_create: all buffers are sized
+ *    there from max_atoms and max_replicas (preallocated memory, Section
+ *    III-B1 "allocated in the initial phase").  Larger inputs return
+ *    DP_ERR_CAPACITY.
+ */
+#ifndef DP_GB300_H
+#define DP_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dp_model dp_model;
+
+typedef enum {
+  DP_OK = 0,
+  DP_ERR_ARG = 1,           /* bad argument (null pointer, size, mismatch) */
+  DP_ERR_CUDA = 2,          /* a CUDA runtime call failed; see dp_last_error */
+  DP_ERR_OOM = 3,           /* device allocation failed in dp_create */
+  DP_ERR_UNSUPPORTED = 4,   /* non-orthorhombic box, unsupported network size or precision */
+  DP_ERR_SEL_OVERFLOW = 5,  /* more real neighbours of one type than sel[type] */
+  DP_ERR_SKIN_EXCEEDED = 6, /* an atom moved more than skin/2 since the last neighbour rebuild */
+  DP_ERR_WAIT_TIMEOUT = 7,  /* a bounded device-side wait gave up */
+  DP_ERR_CAPACITY = 8,      /* more atoms/replicas/cells/Verlet entries than allocated */
+  DP_ERR_WEIGHTS = 9        /* weight blob malformed or inconsistent with the arguments */
+} dp_status;
+
+typedef enum {
+  DP_FP64 = 0,     /* everything in FP64 */
+  DP_FP32 = 1,     /* R, networks and per-pair force terms in FP32; positions,
+                      Verlet update, force accumulation, energy and virial sums in FP64 */
+  DP_MIX_BF16 = 2, /* as DP_FP32, with the embedding and fitting GEMM operands in BF16
+                      on the tensor cores, FP32 accumulation */
+  DP_MIX_FP16 = 3  /* as DP_MIX_BF16 with FP16 operands */
+} dp_precision;
+
+/*
+ * dp_create -- build a model on the current CUDA device.
+ *   out          receives the handle.
+ *   ntypes       number of atom types; type_map[ntypes] their names (e.g. {"O","H"}),
+ *                checked against the names stored in the weights (nullable: no check).
+ *   rcut, rcut_smth  cutoff and start of the smooth switch (A); must equal the weights'.
+ *   sel[ntypes]  per-neighbour-type caps; must equal the weights'.
+ *   weight_path  file holding a weight blob, or NULL to use weight_blob/blob_bytes.
+ *   weight_blob  host pointer to the blob (layout: magic "DPW1", header of sizes,
+ *                sel, type names, then FP64 parameters in the documented order).
+ *   prec         arithmetic policy (dp_precision).
+ *   max_atoms    capacity in atoms summed over replicas; max_replicas capacity in boxes.
+ *   skin         Verlet-list skin (A); the list holds pairs within rcut + skin.
+ *   cuda_stream  cudaStream_t to run on (NULL = default stream).
+ * Weights are copied to device memory owned by the model.
+ */
+dp_status dp_create(dp_model** out, int ntypes, const char* const* type_map, double rcut,
+                    double rcut_smth, const int* sel, const char* weight_path,
+                    const void* weight_blob, size_t blob_bytes, dp_precision prec, int max_atoms,
+                    int max_replicas, double skin, void* cuda_stream);
+
+/*
+ * dp_compute -- energy, per-atom energy, forces and virial of one periodic box.
+ *   coords [natoms*3] device FP64, types [natoms] device int32 in [0, ntypes),
+ *   box [9] host.  Outputs (device FP64): energy [1], atom_energy [natoms]
+ *   (nullable), forces [natoms*3], virial [9] (nullable).
+ * Positions are wrapped into the box and the neighbour list is rebuilt on every
+ * call.  On a device-side error the outputs are undefined and energy is NaN;
+ * dp_sync returns the error.
+ */
+dp_status dp_compute(dp_model* m, int natoms, const double* coords, const int* types,
+                     const double* box, double* energy, double* atom_energy, double* forces,
+                     double* virial);
+
+/*
+ * dp_compute_batch -- dp_compute over nrep independent boxes in one pass.
+ *   atom_offsets [nrep+1] host, CSR offsets of each replica's atoms in coords/types;
+ *   boxes [nrep*9] host.  energies [nrep] and virials [nrep*9] device outputs
+ *   (virials nullable); atom_energy [N] (nullable) and forces [N*3] device outputs.
+ */
+dp_status dp_compute_batch(dp_model* m, int nrep, const int* atom_offsets, const double* coords,
+                           const int* types, const double* boxes, double* energies,
+                           double* atom_energy, double* forces, double* virials);
+
+/* Molecular-dynamics state, all in the caller's atom order. */
+typedef struct {
+  int natoms;                 /* total atoms over replicas */
+  int nrep;                   /* number of independent boxes (>= 1) */
+  const int* atom_offsets;    /* host [nrep+1]; NULL means one replica */
+  const double* boxes;        /* host [nrep*9] */
+  double* x;                  /* device [natoms*3] positions, updated in place */
+  double* v;                  /* device [natoms*3] velocities (A/fs), updated in place */
+  const int* types;           /* device [natoms] */
+  const double* mass_by_type; /* host [ntypes], amu */
+  double* forces;             /* device [natoms*3] out: forces after the last step (nullable) */
+  double* potential;          /* device [nrep] out: potential energy after the last step (nullable) */
+  double* kinetic;            /* device [nrep] out: kinetic energy after the last step (nullable) */
+  double* virial;             /* device [nrep*9] out: virial after the last step (nullable) */
+  long long step;             /* in/out: step counter; rebuilds happen when step % rebuild_every == 0 */
+  int rebuild_every;          /* neighbour rebuild interval in steps (>= 1) */
+  int resume;                 /* 0: read x, v, rebuild lists and evaluate F(x) first;
+                                 1: continue from the model's internal state left by the previous
+                                 MD call on this model (x, v are not re-read; same atoms and boxes) */
+} dp_md_state;
+
+/*
+ * dp_verlet_step -- advance nsteps velocity-Verlet NVE steps of time step dt_fs:
+ *   v += dt/2 * kappa F/m; x += dt v; rebuild the neighbour list every
+ *   rebuild_every steps (positions wrapped then), otherwise check that no atom
+ *   moved more than skin/2; F = F(x); v += dt/2 * kappa F/m;
+ *   kappa = 9.648533e-3 A fs^-2 per eV A^-1 amu^-1.
+ * Positions and velocities stay FP64 in every precision.  With capture_graph
+ * != 0 the steps between rebuilds are captured once into a CUDA graph and
+ * replayed.  The state's x and v are read at the start and written at the end
+ * of the call.  Works for one replica or many (nrep > 1).
+ */
+dp_status dp_verlet_step(dp_model* m, dp_md_state* st, double dt_fs, int nsteps, int capture_graph);
+
+/*
+ * dp_md_run_batch -- dp_verlet_step for many replicas of uneven size in one
+ * launch per phase (persistent kernels over (replica, atom) work), always under
+ * a captured CUDA graph, with tile shapes chosen by the autotuner on first use.
+ */
+dp_status dp_md_run_batch(dp_model* m, dp_md_state* st, double dt_fs, int nsteps);
+
+/*
+ * dp_param_grad -- gradient of the loss
+ *   L = cE * (E - E0)^2 + cF * sum_k |F_k - F0_k|^2
+ * with respect to every model parameter theta (the FP64 parameter block of the
+ * weight blob: embedding nets, fitting nets, e_bias; davg/dstd are not
+ * parameters).  One box as in dp_compute; E0 host scalar; F0 [natoms*3] device
+ * (caller order).  grad [ntheta] device FP64 output (overwritten); loss [1]
+ * device output (nullable).  The force term is the derivative of the
+ * directional derivative of E along w = 2 cF (F - F0), computed by a
+ * tangent-forward sweep followed by a reverse sweep; embedding activations are
+ * recomputed, not stored.  Runs in FP64 or FP32 according to the model's
+ * precision (mixed precisions use FP32 here).
+ */
+dp_status dp_param_grad(dp_model* m, int natoms, const double* coords, const int* types,
+                        const double* box, double E0, const double* F0, double cE, double cF,
+                        double* grad, double* loss);
+
+/* Number of parameters in theta (the length of dp_param_grad's grad). */
+long long dp_ntheta(const dp_model* m);
+
+/*
+ * dp_get_nlist -- copy the formatted neighbour list of the last dp_compute /
+ * MD step: nlist [natoms*S] and images [natoms*S] device int32 in caller order,
+ * S = sum(sel).  Row i holds, per neighbour type t in order, the neighbours of
+ * type t in canonical order (ascending caller index j, then image nx, ny, nz),
+ * padded with -1 (nlist) and 0 (images) to sel[t].  Image code:
+ * ((nx+512)<<20) | ((ny+512)<<10) | (nz+512).  Waits for the stream.
+ */
+dp_status dp_get_nlist(dp_model* m, int* nlist, int* images);
+
+/*
+ * dp_phase_times -- measurement hook: run `repeats` force evaluations on the
+ * model's current internal state (left by the last dp_compute / MD call) with
+ * CUDA events on the model's stream around each phase, and write the mean
+ * milliseconds per phase to ms[8]: [0] list format, [1] descriptor (environment
+ * matrix, embedding, T, D), [2] fitting forward+backward, [3] embedding backward
+ * with force and virial scatter, [4] whole evaluation, [5..7] reserved (0).
+ * Synchronous.  Leaves forces/energies of the last evaluation in place.
+ */
+dp_status dp_phase_times(dp_model* m, int repeats, float* ms);
+
+/* Number of kernels this model has launched so far (graph replays count every
+   kernel in the graph).  Host-side counter; no synchronisation. */
+long long dp_kernel_launches(const dp_model* m);
+
+/* Wait for the model's stream; return and clear the sticky device error (DP_OK if none). */
+dp_status dp_sync(dp_model* m);
+
+/* Human-readable description of the last error on this model (never NULL). */
+const char* dp_last_error(const dp_model* m);
+
+/* Free every resource of the model (waits for its stream first).  NULL is a no-op. */
+void dp_destroy(dp_model* m);
+
+/* Library version string. */
+const char* dp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DP_GB300_H */

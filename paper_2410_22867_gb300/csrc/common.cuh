@@ -1,0 +1,230 @@
+// Internal declarations shared by the CUDA translation units of libdpgb300.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/dp.h"
+
+namespace dpg {
+
+// Network sizes fixed by the model (Section II-A; fitting widths of Section IV).
+constexpr int kN1 = 25, kN2 = 50, kN3 = 100, kM2 = 16;
+constexpr int kF = 240;
+constexpr int kKD = kN3 * kM2;  // 1600, descriptor length
+constexpr int kEmbParams = kN1 + kN1 + kN1 * kN2 + kN2 + kN2 * kN3 + kN3;       // 6450
+constexpr int kFitParams = kKD * kF + kF + kF * kF + kF + kF * kF + kF + kF + 1;  // 500161
+constexpr int kMaxTypes = 4;
+
+// offsets inside one embedding block
+constexpr int kEW1 = 0, kEb1 = kN1, kEW2 = 2 * kN1, kEb2 = kEW2 + kN1 * kN2, kEW3 = kEb2 + kN2,
+              kEb3 = kEW3 + kN2 * kN3;
+// offsets inside one fitting block
+constexpr long kFW1 = 0, kFb1 = (long)kKD * kF, kFW2 = kFb1 + kF, kFb2 = kFW2 + kF * kF,
+               kFW3 = kFb2 + kF, kFb3 = kFW3 + kF * kF, kFw4 = kFb3 + kF, kFb4 = kFw4 + kF;
+
+// sticky device error bits
+enum : int { ERR_SEL = 1, ERR_SKIN = 2, ERR_VCAP = 4, ERR_TIMEOUT = 8, ERR_CELLCAP = 16, ERR_TYPE = 32 };
+
+// 32-byte aligned FP64 4-vector (positions, velocities, pair vectors).
+struct __align__(32) dvec4 {
+  double x, y, z, w;
+};
+__host__ __device__ __forceinline__ dvec4 make_dvec4(double x, double y, double z, double w) {
+  dvec4 r;
+  r.x = x; r.y = y; r.z = z; r.w = w;
+  return r;
+}
+
+// Per-replica geometry (orthorhombic box and cell grid).
+struct RepGeom {
+  double L[3];      // box lengths
+  float Lf[3];      // box lengths in fp32
+  int nc[3];        // cells per axis
+  int m[3];         // stencil half width per axis
+  double edge[3];   // cell edge
+  int cell_off;     // first global cell id of this replica
+  int atom_off;     // first caller-order atom of this replica
+  int natoms;
+  int pad;
+};
+
+struct Model {
+  // configuration
+  int ntypes = 0, switch_kind = 0;
+  double rc = 0, rs = 0, skin = 0;
+  int sel[kMaxTypes] = {0}, sel_off[kMaxTypes + 1] = {0}, S = 0;
+  int vcap[kMaxTypes] = {0}, vcap_off[kMaxTypes + 1] = {0}, VS = 0;
+  dp_precision prec = DP_FP64;
+  int max_atoms = 0, max_reps = 0, max_cells = 0;
+  cudaStream_t stream = nullptr;
+  std::string last_error;
+  long long ntheta = 0;
+  std::vector<double> theta_host;
+  std::vector<double> davg_host, dstd_host;
+
+  // weights (device)
+  double* w64 = nullptr;      // theta FP64 (blob order)
+  float* w32 = nullptr;       // theta FP32
+  double* fitT64 = nullptr;   // per type: W1^T [kF][kKD], W2^T [kF][kF], W3^T [kF][kF]
+  float* fitT32 = nullptr;
+  double* stat64 = nullptr;   // davg [nt][4], 1/dstd [nt][4]
+  float* stat32 = nullptr;
+  // 16-bit operand copies for the tensor-core kernels (per type), laid out by those kernels
+  void* tc_weights = nullptr;
+  size_t tc_weights_bytes = 0;
+
+  // atoms (internal, type-sorted order)
+  int* perm = nullptr;        // internal -> caller index
+  int* inv = nullptr;         // caller -> internal index
+  int* itype = nullptr;
+  int* irep = nullptr;
+  int* type_count = nullptr;  // [kMaxTypes + 1] device: counts then total (offsets are derived)
+  int* type_off = nullptr;    // [kMaxTypes + 1]
+  int* blk_count = nullptr;   // scratch for the type sort
+  dvec4* x = nullptr;       // positions (wrapped at rebuild, drifting between)
+  dvec4* xref = nullptr;    // positions at the last rebuild
+  dvec4* v = nullptr;       // velocities
+  float4* delta = nullptr;    // x - xref in fp32
+  float4* xf = nullptr;       // wrapped positions in fp32 (rebuild prefilter)
+  double* force = nullptr;    // [N*3]
+  double* mass = nullptr;     // [N] per internal atom
+
+  // replicas
+  RepGeom* geom = nullptr;    // device [max_reps]
+  RepGeom* geom_host = nullptr;  // pinned host staging
+  int nrep = 0;
+  int ncells = 0;
+
+  // cell list
+  int* cell_of = nullptr;
+  int* cell_count = nullptr;
+  int* cell_start = nullptr;
+  int* cell_fill = nullptr;
+  int* cell_atoms = nullptr;
+
+  // Verlet list (r_c + skin)
+  int* vl_j = nullptr;        // [N*VS]
+  int* vl_img = nullptr;      // [N*VS]
+  float4* vl_d0 = nullptr;    // [N*VS] pair vector at rebuild (fp32)
+  int* vcount = nullptr;      // [N*nt]
+
+  // formatted list (r_c), compacted per type segment
+  int* nl_j = nullptr;        // [N*S]
+  int* nl_img = nullptr;      // [N*S]
+  void* nl_d = nullptr;       // [N*S] float4 (fp32 modes) or dvec4 (fp64)
+  int* nl_count = nullptr;    // [N*nt]
+
+  // descriptor and fitting buffers (element type depends on precision)
+  void* Tm = nullptr;         // [N][4][kN3]
+  void* Dm = nullptr;         // [N][kKD]
+  void* dD = nullptr;         // [N][kKD]
+  void* act[5] = {nullptr};   // fitting activations [N][kF]
+  double* e_atom = nullptr;   // [N] internal order
+  double* vir_atom = nullptr; // [N][9] internal order
+  double* e_user = nullptr;   // [N] caller order
+  double* vir_user = nullptr; // [N][9] caller order
+  double* ke_user = nullptr;  // [N] caller order
+  double* red_out = nullptr;  // [max_reps * 20] reductions scratch
+  int* rep_off_dev = nullptr; // [max_reps + 1]
+  int* err = nullptr;         // sticky error word
+  int* err_host = nullptr;    // pinned
+  int* small_i = nullptr;     // [64] device: small integer tables (sel, offsets)
+
+  // MD bookkeeping
+  int natoms = 0;             // atoms of the current call
+  bool lists_valid = false;
+  bool md_valid = false;      // internal x, v, F, lists belong to the last MD call
+  long long launches = 0;     // kernels launched (graph replays add their kernel count)
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_key[4] = {0, 0, 0, 0};
+};
+
+// ---------------------------------------------------------------------------
+// error helpers
+#define DP_CUDA_TRY(m, call)                                                       \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      (m)->last_error = std::string(#call) + ": " + cudaGetErrorString(e_);        \
+      return DP_ERR_CUDA;                                                          \
+    }                                                                              \
+  } while (0)
+
+#define DP_LAUNCH_CHECK(m)                                                         \
+  do {                                                                             \
+    cudaError_t e_ = cudaGetLastError();                                           \
+    if (e_ != cudaSuccess) {                                                       \
+      (m)->last_error = std::string("kernel launch: ") + cudaGetErrorString(e_);   \
+      return DP_ERR_CUDA;                                                          \
+    }                                                                              \
+  } while (0)
+
+inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
+
+// Raise a kernel's dynamic shared-memory limit once (not from inside stream capture
+// after the first call: the attribute call is skipped when already large enough).
+inline cudaError_t ensure_smem(const void* fn, size_t smem) {
+  static std::vector<std::pair<const void*, size_t>> done;
+  for (auto& e : done)
+    if (e.first == fn && e.second >= smem) return cudaSuccess;
+  cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err == cudaSuccess) done.push_back({fn, smem});
+  return err;
+}
+
+// Resident blocks per SM for a launch shape, cached.
+inline int blocks_per_sm(const void* fn, int threads, size_t smem) {
+  struct E { const void* f; int t; size_t s; int n; };
+  static std::vector<E> cache;
+  for (auto& e : cache)
+    if (e.f == fn && e.t == threads && e.s == smem) return e.n;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess || n < 1) n = 1;
+  cache.push_back({fn, threads, smem, n});
+  return n;
+}
+
+inline int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 152;
+  }
+  return n;
+}
+__host__ __device__ __forceinline__ int cdiv_dev(int a, int b) { return (a + b - 1) / b; }
+
+// ---------------------------------------------------------------------------
+// host-side launchers (each returns DP_OK or DP_ERR_CUDA)
+// nlist.cu
+dp_status launch_type_sort(Model* m, const int* types_user, int N);
+dp_status launch_load_positions(Model* m, const double* coords_user, int N);
+dp_status launch_rebuild(Model* m, int N);
+dp_status launch_delta(Model* m, int N);
+dp_status launch_format(Model* m, int N);
+dp_status launch_get_nlist(Model* m, int N, int* nlist, int* images);
+// simt.cu
+dp_status launch_descriptor(Model* m, int N);
+dp_status launch_fitting(Model* m, int N);
+dp_status launch_embed_backward(Model* m, int N);
+// md.cu
+dp_status launch_outputs(Model* m, int N, double* energy_rep, double* atom_energy, double* forces,
+                         double* virial_rep);
+dp_status launch_zero_forces(Model* m, int N);
+dp_status launch_kick_drift(Model* m, int N, double dt);
+dp_status launch_kick(Model* m, int N, double dt);
+dp_status launch_load_state(Model* m, int N, const double* v_user, const double* mass_by_type);
+dp_status launch_store_state(Model* m, int N, double* x_user, double* v_user);
+dp_status launch_kinetic(Model* m, int N, double* ke_rep);
+dp_status launch_nan_energy(Model* m, double* energy, int n);
+
+}  // namespace dpg

@@ -1,0 +1,540 @@
+// Neighbour search: type sort, wrap and cell binning, Verlet list within
+// r_c + skin with periodic images, and the per-step formatted list within r_c.
+//
+// The neighbour list is the one LAMMPS builds for the DP pair style (Section
+// II-A, Fig. 1(a)), kept per neighbour type so no slicing is needed later
+// (the type pre-classified environment matrix of Section III-B1), built with a
+// cell list (the cell-list method cited in Section II-A) and a 2 A skin
+// rebuilt every k steps (Section IV).
+//
+// Bit-exactness: a pair (j, n) is in the list iff the FP64 value
+//   r2 = ((dx*dx) + (dy*dy)) + (dz*dz),  dx = (x_j + n*L) - x_i
+// (round-to-nearest, no FMA) is below the squared cutoff.  The kernels first
+// classify in FP32 and fall back to that exact FP64 test whenever the FP32
+// value lies inside a band wider than its worst-case rounding error, so the
+// result equals the FP64 definition while doing FP32 work for almost all pairs
+// (FP64 throughput is low on this GPU).
+#include "common.cuh"
+
+namespace dpg {
+namespace {
+
+__device__ __forceinline__ void set_err(int* err, int bit) { atomicOr(err, bit); }
+
+// Wrap one coordinate into [0, L): w = x - L*floor(x/L); rounding cases that land
+// on w < 0 or w >= L become 0.
+__device__ __forceinline__ double wrap1(double x, double L) {
+  double t = floor(__ddiv_rn(x, L));
+  double p = __dmul_rn(t, L);
+  double w = __dsub_rn(x, p);
+  if (w < 0.0 || w >= L) w = 0.0;
+  return w;
+}
+
+// Exact FP64 pair vector and squared length in the fixed operation order.
+__device__ __forceinline__ double exact_r2(const dvec4& xi, const dvec4& xj, int nx, int ny, int nz,
+                                           const double* L, double* d) {
+  d[0] = __dsub_rn(__dadd_rn(xj.x, __dmul_rn((double)nx, L[0])), xi.x);
+  d[1] = __dsub_rn(__dadd_rn(xj.y, __dmul_rn((double)ny, L[1])), xi.y);
+  d[2] = __dsub_rn(__dadd_rn(xj.z, __dmul_rn((double)nz, L[2])), xi.z);
+  return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+}
+
+__device__ __forceinline__ int pack_img(int nx, int ny, int nz) {
+  return ((nx + 512) << 20) | ((ny + 512) << 10) | (nz + 512);
+}
+__device__ __forceinline__ void unpack_img(int c, int& nx, int& ny, int& nz) {
+  nx = ((c >> 20) & 1023) - 512;
+  ny = ((c >> 10) & 1023) - 512;
+  nz = (c & 1023) - 512;
+}
+
+__device__ __forceinline__ int floor_div(int a, int b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
+
+// ------------------------------------------------------------------ type sort
+constexpr int kSortBlock = 1024;
+
+__device__ __forceinline__ int rep_of(const int* rep_off, int nrep, int u) {
+  int lo = 0, hi = nrep - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (rep_off[mid] <= u) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_type_count(const int* __restrict__ types, int N, int ntypes, int* blk_count, int* err) {
+  __shared__ int cnt[kMaxTypes];
+  if (threadIdx.x < kMaxTypes) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  int u = blockIdx.x * kSortBlock + threadIdx.x;
+  if (u < N) {
+    int t = types[u];
+    if (t < 0 || t >= ntypes) { set_err(err, ERR_TYPE); t = 0; }
+    atomicAdd(&cnt[t], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < kMaxTypes) blk_count[blockIdx.x * kMaxTypes + threadIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void k_type_scan(int nblk, int ntypes, int* blk_count, int* type_count, int* type_off) {
+  // single thread: nblk <= a few hundred
+  if (threadIdx.x != 0) return;
+  int off = 0;
+  for (int t = 0; t < ntypes; ++t) {
+    type_off[t] = off;
+    int run = off;
+    for (int b = 0; b < nblk; ++b) {
+      int c = blk_count[b * kMaxTypes + t];
+      blk_count[b * kMaxTypes + t] = run;
+      run += c;
+    }
+    type_count[t] = run - off;
+    off = run;
+  }
+  type_off[ntypes] = off;
+  type_count[kMaxTypes] = off;
+}
+
+__global__ void k_type_scatter(const int* __restrict__ types, int N, int ntypes, const int* blk_off,
+                               const int* rep_off, int nrep, int* perm, int* inv, int* itype, int* irep) {
+  __shared__ int wcnt[kSortBlock / 32][kMaxTypes];
+  int u = blockIdx.x * kSortBlock + threadIdx.x;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int t = (u < N) ? types[u] : -1;
+  if (t >= ntypes) t = 0;
+  if (t < 0 && u < N) t = 0;
+  unsigned lt = (1u << lane) - 1u;
+  int rank_in_warp = 0;
+  for (int q = 0; q < ntypes; ++q) {
+    unsigned mask = __ballot_sync(0xffffffffu, t == q);
+    if (t == q) rank_in_warp = __popc(mask & lt);
+    if (lane == 0) wcnt[w][q] = __popc(mask);
+  }
+  __syncthreads();
+  if (u < N) {
+    int before = 0;
+    for (int ww = 0; ww < w; ++ww) before += wcnt[ww][t];
+    int k = blk_off[blockIdx.x * kMaxTypes + t] + before + rank_in_warp;
+    perm[k] = u;
+    inv[u] = k;
+    itype[k] = t;
+    irep[k] = rep_of(rep_off, nrep, u);
+  }
+}
+
+__global__ void k_load_positions(const double* __restrict__ coords, const int* __restrict__ perm, int N,
+                                 dvec4* x) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  int u = perm[k];
+  x[k] = make_dvec4(coords[3 * u], coords[3 * u + 1], coords[3 * u + 2], 0.0);
+}
+
+// ------------------------------------------------------------------ cells
+__global__ void k_wrap_bin(int N, const int* __restrict__ irep, const RepGeom* __restrict__ geom, dvec4* x,
+                           dvec4* xref, float4* xf, float4* delta, int* cell_of, int* cell_count) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const RepGeom& g = geom[irep[k]];
+  dvec4 p = x[k];
+  double w[3] = {wrap1(p.x, g.L[0]), wrap1(p.y, g.L[1]), wrap1(p.z, g.L[2])};
+  dvec4 q = make_dvec4(w[0], w[1], w[2], 0.0);
+  x[k] = q;
+  xref[k] = q;
+  xf[k] = make_float4((float)w[0], (float)w[1], (float)w[2], 0.f);
+  delta[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  int c[3];
+  for (int a = 0; a < 3; ++a) {
+    int ci = (int)floor(w[a] / g.edge[a]);
+    c[a] = min(max(ci, 0), g.nc[a] - 1);
+  }
+  int cid = g.cell_off + (c[0] * g.nc[1] + c[1]) * g.nc[2] + c[2];
+  cell_of[k] = cid;
+  atomicAdd(&cell_count[cid], 1);
+}
+
+__global__ void k_scan_cells(int ncells, const int* __restrict__ cell_count, int* cell_start) {
+  __shared__ int part[1024];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < ncells; base += 1024) {
+    int i = base + threadIdx.x;
+    int v = (i < ncells) ? cell_count[i] : 0;
+    part[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = 1; s < 1024; s <<= 1) {
+      int add = (threadIdx.x >= s) ? part[threadIdx.x - s] : 0;
+      __syncthreads();
+      part[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (i < ncells) cell_start[i] = carry + part[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += part[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) cell_start[ncells] = carry;
+}
+
+__global__ void k_fill_cells(int N, const int* __restrict__ cell_of, const int* __restrict__ cell_start,
+                             int* cell_fill, int* cell_atoms) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  int cid = cell_of[k];
+  int pos = cell_start[cid] + atomicAdd(&cell_fill[cid], 1);
+  cell_atoms[pos] = k;
+}
+
+// ------------------------------------------------------------------ Verlet list
+struct VerletArgs {
+  int N, ntypes, VS;
+  int vcap[kMaxTypes], vcap_off[kMaxTypes + 1];
+  int buf_off[kMaxTypes + 1];  // per-warp smem key buffer offsets (in keys)
+  double rcs2;
+  float rcs2_hi;               // fp32 prefilter bound (rcs2 + band)
+  const int* itype;
+  const int* irep;
+  const RepGeom* geom;
+  const dvec4* x;
+  const float4* xf;
+  const int* cell_of;
+  const int* cell_start;
+  const int* cell_atoms;
+  int* vl_j;
+  int* vl_img;
+  float4* vl_d0;
+  int* vcount;
+  int* err;
+};
+
+constexpr int kVerletWarps = 4;
+
+__global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
+  extern __shared__ unsigned long long keys_all[];
+  __shared__ int cnt[kVerletWarps][kMaxTypes];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * kVerletWarps + w;
+  if (i >= a.N) return;
+  unsigned long long* keys = keys_all + (size_t)w * a.buf_off[a.ntypes];
+  if (lane < kMaxTypes) cnt[w][lane] = 0;
+  __syncwarp();
+  const RepGeom& g = a.geom[a.irep[i]];
+  const dvec4 xi = a.x[i];
+  const float4 xfi = a.xf[i];
+  const int cid = a.cell_of[i];
+  int rel = cid - g.cell_off;
+  int ci[3] = {rel / (g.nc[1] * g.nc[2]), (rel / g.nc[2]) % g.nc[1], rel % g.nc[2]};
+  const unsigned lt = (1u << lane) - 1u;
+  for (int ox = -g.m[0]; ox <= g.m[0]; ++ox)
+    for (int oy = -g.m[1]; oy <= g.m[1]; ++oy)
+      for (int oz = -g.m[2]; oz <= g.m[2]; ++oz) {
+        int v[3] = {ci[0] + ox, ci[1] + oy, ci[2] + oz}, n[3], cc[3];
+        for (int q = 0; q < 3; ++q) {
+          n[q] = floor_div(v[q], g.nc[q]);
+          cc[q] = v[q] - n[q] * g.nc[q];
+        }
+        int c = g.cell_off + (cc[0] * g.nc[1] + cc[1]) * g.nc[2] + cc[2];
+        float sh[3] = {(float)n[0] * g.Lf[0], (float)n[1] * g.Lf[1], (float)n[2] * g.Lf[2]};
+        bool self_img = (n[0] == 0 && n[1] == 0 && n[2] == 0);
+        int beg = a.cell_start[c], end = a.cell_start[c + 1];
+        for (int base = beg; base < end; base += 32) {
+          int idx = base + lane;
+          bool acc = false;
+          int j = -1, tj = 0;
+          if (idx < end) {
+            j = a.cell_atoms[idx];
+            if (!(self_img && j == i)) {
+              float4 xfj = a.xf[j];
+              float dx = (xfj.x + sh[0]) - xfi.x, dy = (xfj.y + sh[1]) - xfi.y, dz = (xfj.z + sh[2]) - xfi.z;
+              float r2f = dx * dx + dy * dy + dz * dz;
+              if (r2f < a.rcs2_hi) {
+                double d[3];
+                double r2 = exact_r2(xi, a.x[j], n[0], n[1], n[2], g.L, d);
+                acc = r2 < a.rcs2;
+              }
+              tj = a.itype[j];
+            }
+          }
+          for (int t = 0; t < a.ntypes; ++t) {
+            unsigned mask = __ballot_sync(0xffffffffu, acc && tj == t);
+            if (mask == 0u) continue;
+            int start = cnt[w][t];
+            if (acc && tj == t) {
+              int pos = start + __popc(mask & lt);
+              int capP = a.buf_off[t + 1] - a.buf_off[t];
+              if (pos < capP)
+                keys[a.buf_off[t] + pos] = ((unsigned long long)(unsigned)j << 32) |
+                                           (unsigned)pack_img(n[0], n[1], n[2]);
+            }
+            __syncwarp();
+            if (lane == 0) cnt[w][t] = start + __popc(mask);
+            __syncwarp();
+          }
+        }
+      }
+  __syncwarp();
+  for (int t = 0; t < a.ntypes; ++t) {
+    int nt_ = cnt[w][t];
+    int capP = a.buf_off[t + 1] - a.buf_off[t];
+    if (nt_ > a.vcap[t]) {
+      if (lane == 0) set_err(a.err, ERR_VCAP);
+      nt_ = a.vcap[t];
+    }
+    unsigned long long* kb = keys + a.buf_off[t];
+    int P = 1;
+    while (P < nt_) P <<= 1;
+    if (P > capP) P = capP;
+    for (int q = nt_ + lane; q < P; q += 32) kb[q] = ~0ull;
+    __syncwarp();
+    // bitonic sort of kb[0, P)
+    for (int k = 2; k <= P; k <<= 1) {
+      for (int jj = k >> 1; jj > 0; jj >>= 1) {
+        for (int q = lane; q < P; q += 32) {
+          int p = q ^ jj;
+          if (p > q) {
+            unsigned long long u0 = kb[q], u1 = kb[p];
+            bool up = (q & k) == 0;
+            if ((u0 > u1) == up) { kb[q] = u1; kb[p] = u0; }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    size_t ebase = (size_t)i * a.VS + a.vcap_off[t];
+    for (int q = lane; q < nt_; q += 32) {
+      unsigned long long key = kb[q];
+      int j = (int)(key >> 32);
+      int code = (int)(key & 0xffffffffu);
+      int n0, n1, n2;
+      unpack_img(code, n0, n1, n2);
+      double d[3];
+      exact_r2(xi, a.x[j], n0, n1, n2, g.L, d);
+      a.vl_j[ebase + q] = j;
+      a.vl_img[ebase + q] = code;
+      a.vl_d0[ebase + q] = make_float4((float)d[0], (float)d[1], (float)d[2], 0.f);
+    }
+    if (lane == 0) a.vcount[(size_t)i * a.ntypes + t] = nt_;
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------ per-step
+__global__ void k_delta(int N, const dvec4* __restrict__ x, const dvec4* __restrict__ xref, float4* delta,
+                        double lim2, int* err) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  dvec4 p = x[k], q = xref[k];
+  double dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+  delta[k] = make_float4((float)dx, (float)dy, (float)dz, 0.f);
+  if (dx * dx + dy * dy + dz * dz > lim2) set_err(err, ERR_SKIN);
+}
+
+struct FormatArgs {
+  int N, ntypes, VS, S;
+  int vcap_off[kMaxTypes + 1];
+  int sel[kMaxTypes], sel_off[kMaxTypes + 1];
+  double rc2;
+  float rc2_lo, rc2_hi;
+  const int* irep;
+  const RepGeom* geom;
+  const dvec4* x;
+  const float4* delta;
+  const int* vl_j;
+  const int* vl_img;
+  const float4* vl_d0;
+  const int* vcount;
+  int* nl_j;
+  int* nl_img;
+  void* nl_d;
+  int* nl_count;
+  int* err;
+};
+
+template <bool kFP64>
+__global__ void __launch_bounds__(128) k_format(FormatArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= a.N) return;
+  const unsigned lt = (1u << lane) - 1u;
+  const RepGeom& g = a.geom[a.irep[i]];
+  const dvec4 xi = a.x[i];
+  const float4 di = a.delta[i];
+  for (int t = 0; t < a.ntypes; ++t) {
+    const int n = a.vcount[(size_t)i * a.ntypes + t];
+    const size_t vb = (size_t)i * a.VS + a.vcap_off[t];
+    const size_t ob = (size_t)i * a.S + a.sel_off[t];
+    int cnt = 0;
+    for (int b = 0; b < n; b += 32) {
+      int q = b + lane;
+      bool in = false;
+      int j = 0, code = 0;
+      double dd[3];
+      float df[3];
+      if (q < n) {
+        j = a.vl_j[vb + q];
+        code = a.vl_img[vb + q];
+        if (kFP64) {
+          int n0, n1, n2;
+          unpack_img(code, n0, n1, n2);
+          in = exact_r2(xi, a.x[j], n0, n1, n2, g.L, dd) < a.rc2;
+        } else {
+          float4 d0 = a.vl_d0[vb + q];
+          float4 dj = a.delta[j];
+          df[0] = d0.x + (dj.x - di.x);
+          df[1] = d0.y + (dj.y - di.y);
+          df[2] = d0.z + (dj.z - di.z);
+          float r2f = df[0] * df[0] + df[1] * df[1] + df[2] * df[2];
+          if (r2f < a.rc2_lo) {
+            in = true;
+          } else if (r2f < a.rc2_hi) {
+            int n0, n1, n2;
+            unpack_img(code, n0, n1, n2);
+            in = exact_r2(xi, a.x[j], n0, n1, n2, g.L, dd) < a.rc2;
+          }
+        }
+      }
+      unsigned mask = __ballot_sync(0xffffffffu, in);
+      int pos = cnt + __popc(mask & lt);
+      if (in && pos < a.sel[t]) {
+        a.nl_j[ob + pos] = j;
+        a.nl_img[ob + pos] = code;
+        if (kFP64) {
+          static_cast<dvec4*>(a.nl_d)[ob + pos] = make_dvec4(dd[0], dd[1], dd[2], 0.0);
+        } else {
+          static_cast<float4*>(a.nl_d)[ob + pos] = make_float4(df[0], df[1], df[2], 0.f);
+        }
+      }
+      cnt += __popc(mask);
+    }
+    if (cnt > a.sel[t]) {
+      if (lane == 0) set_err(a.err, ERR_SEL);
+      cnt = a.sel[t];
+    }
+    if (lane == 0) a.nl_count[(size_t)i * a.ntypes + t] = cnt;
+  }
+}
+
+__global__ void k_get_nlist(int N, int ntypes, int S, const int* sel, const int* sel_off, const int* inv,
+                            const int* perm, const int* nl_j, const int* nl_img, const int* nl_count,
+                            int* out_nl, int* out_img) {
+  int u = blockIdx.x;
+  if (u >= N) return;
+  int i = inv[u];
+  for (int t = 0; t < ntypes; ++t) {
+    int c = nl_count[(size_t)i * ntypes + t];
+    for (int q = threadIdx.x; q < sel[t]; q += blockDim.x) {
+      size_t src = (size_t)i * S + sel_off[t] + q, dst = (size_t)u * S + sel_off[t] + q;
+      out_nl[dst] = (q < c) ? perm[nl_j[src]] : -1;
+      out_img[dst] = (q < c) ? nl_img[src] : 0;
+    }
+  }
+}
+
+}  // namespace
+
+// ====================================================================== launchers
+dp_status launch_type_sort(Model* m, const int* types_user, int N) {
+  int nblk = cdiv(N, kSortBlock);
+  k_type_count<<<nblk, kSortBlock, 0, m->stream>>>(types_user, N, m->ntypes, m->blk_count, m->err);
+  k_type_scan<<<1, 32, 0, m->stream>>>(nblk, m->ntypes, m->blk_count, m->type_count, m->type_off);
+  k_type_scatter<<<nblk, kSortBlock, 0, m->stream>>>(types_user, N, m->ntypes, m->blk_count, m->rep_off_dev,
+                                                     m->nrep, m->perm, m->inv, m->itype, m->irep);
+  m->launches += 3;
+  DP_LAUNCH_CHECK(m);
+  return DP_OK;
+}
+
+dp_status launch_load_positions(Model* m, const double* coords_user, int N) {
+  k_load_positions<<<cdiv(N, 256), 256, 0, m->stream>>>(coords_user, m->perm, N, m->x);
+  m->launches += 1;
+  DP_LAUNCH_CHECK(m);
+  return DP_OK;
+}
+
+static double max_box_length(const Model* m) {
+  double Lmax = 0;
+  for (int r = 0; r < m->nrep; ++r)
+    for (int a = 0; a < 3; ++a) Lmax = Lmax > m->geom_host[r].L[a] ? Lmax : m->geom_host[r].L[a];
+  return Lmax;
+}
+
+dp_status launch_rebuild(Model* m, int N) {
+  cudaStream_t s = m->stream;
+  DP_CUDA_TRY(m, cudaMemsetAsync(m->cell_count, 0, sizeof(int) * m->ncells, s));
+  DP_CUDA_TRY(m, cudaMemsetAsync(m->cell_fill, 0, sizeof(int) * m->ncells, s));
+  k_wrap_bin<<<cdiv(N, 256), 256, 0, s>>>(N, m->irep, m->geom, m->x, m->xref, m->xf, m->delta, m->cell_of,
+                                          m->cell_count);
+  k_scan_cells<<<1, 1024, 0, s>>>(m->ncells, m->cell_count, m->cell_start);
+  k_fill_cells<<<cdiv(N, 256), 256, 0, s>>>(N, m->cell_of, m->cell_start, m->cell_fill, m->cell_atoms);
+  VerletArgs a;
+  a.N = N; a.ntypes = m->ntypes; a.VS = m->VS;
+  a.buf_off[0] = 0;
+  for (int t = 0; t < m->ntypes; ++t) {
+    a.vcap[t] = m->vcap[t];
+    a.vcap_off[t] = m->vcap_off[t];
+    int P = 1;
+    while (P < m->vcap[t]) P <<= 1;
+    a.buf_off[t + 1] = a.buf_off[t] + P;
+  }
+  a.vcap_off[m->ntypes] = m->vcap_off[m->ntypes];
+  const double rcs = m->rc + m->skin;
+  a.rcs2 = rcs * rcs;
+  // worst-case FP32 error of the prefilter's r^2 is ~1.3e-6 * rcs * Lmax; use 10x that
+  double band = 1.25e-5 * rcs * (max_box_length(m) + rcs) + 1e-3;
+  a.rcs2_hi = (float)(a.rcs2 + band);
+  a.itype = m->itype; a.irep = m->irep; a.geom = m->geom; a.x = m->x; a.xf = m->xf;
+  a.cell_of = m->cell_of; a.cell_start = m->cell_start; a.cell_atoms = m->cell_atoms;
+  a.vl_j = m->vl_j; a.vl_img = m->vl_img; a.vl_d0 = m->vl_d0; a.vcount = m->vcount; a.err = m->err;
+  size_t smem = sizeof(unsigned long long) * (size_t)a.buf_off[m->ntypes] * kVerletWarps;
+  DP_CUDA_TRY(m, ensure_smem(reinterpret_cast<const void*>(k_verlet), smem));
+  k_verlet<<<cdiv(N, kVerletWarps), 32 * kVerletWarps, smem, s>>>(a);
+  m->launches += 4;
+  DP_LAUNCH_CHECK(m);
+  return DP_OK;
+}
+
+dp_status launch_delta(Model* m, int N) {
+  double h = 0.5 * m->skin;
+  k_delta<<<cdiv(N, 256), 256, 0, m->stream>>>(N, m->x, m->xref, m->delta, h * h, m->err);
+  m->launches += 1;
+  DP_LAUNCH_CHECK(m);
+  return DP_OK;
+}
+
+dp_status launch_format(Model* m, int N) {
+  FormatArgs a;
+  a.N = N; a.ntypes = m->ntypes; a.VS = m->VS; a.S = m->S;
+  for (int t = 0; t <= m->ntypes; ++t) { a.vcap_off[t] = m->vcap_off[t]; a.sel_off[t] = m->sel_off[t]; }
+  for (int t = 0; t < m->ntypes; ++t) a.sel[t] = m->sel[t];
+  a.rc2 = m->rc * m->rc;
+  // FP32 pair vector d0 + (delta_j - delta_i) is within ~2e-7 (rc + skin + 2) per component
+  // of the exact one; the r^2 error is below 1e-6 rc (rc + skin + 2).  Band: 100x.
+  double band = 1e-4 * m->rc * (m->rc + m->skin + 2.0) + 1e-4;
+  a.rc2_lo = (float)(a.rc2 - band);
+  a.rc2_hi = (float)(a.rc2 + band);
+  a.irep = m->irep; a.geom = m->geom; a.x = m->x; a.delta = m->delta;
+  a.vl_j = m->vl_j; a.vl_img = m->vl_img; a.vl_d0 = m->vl_d0; a.vcount = m->vcount;
+  a.nl_j = m->nl_j; a.nl_img = m->nl_img; a.nl_d = m->nl_d; a.nl_count = m->nl_count; a.err = m->err;
+  if (m->prec == DP_FP64) k_format<true><<<cdiv(N, 4), 128, 0, m->stream>>>(a);
+  else k_format<false><<<cdiv(N, 4), 128, 0, m->stream>>>(a);
+  m->launches += 1;
+  DP_LAUNCH_CHECK(m);
+  return DP_OK;
+}
+
+dp_status launch_get_nlist(Model* m, int N, int* nlist, int* images) {
+  int* dsel = m->small_i;
+  int hsel[2 * kMaxTypes + 1];
+  for (int t = 0; t < m->ntypes; ++t) hsel[t] = m->sel[t];
+  for (int t = 0; t <= m->ntypes; ++t) hsel[kMaxTypes + t] = m->sel_off[t];
+  DP_CUDA_TRY(m, cudaMemcpyAsync(dsel, hsel, sizeof(hsel), cudaMemcpyHostToDevice, m->stream));
+  k_get_nlist<<<N, 128, 0, m->stream>>>(N, m->ntypes, m->S, dsel, dsel + kMaxTypes, m->inv, m->perm, m->nl_j,
+                                        m->nl_img, m->nl_count, nlist, images);
+  m->launches += 1;
+  DP_LAUNCH_CHECK(m);
+  return DP_OK;
+}
+
+}  // namespace dpg

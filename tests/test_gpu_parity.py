@@ -1,0 +1,271 @@
+"""CUDA path against the FP64 oracle on the same seeded inputs (GPU only).
+
+Bars: neighbour list bit-exact; FP64 per-atom energy within 1e-10 relative;
+FP32 force RMSE <= 1e-5 eV/A; every error is stated against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_22867_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dp():
+    import paper_2410_22867_gb300 as dp
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dp.lib()
+    return dp
+
+
+def _cuda(s):
+    return (torch.tensor(s.coords, dtype=torch.float64, device="cuda"),
+            torch.tensor(s.types, dtype=torch.int32, device="cuda"))
+
+
+def _nl_rows_equal(gpu_nl, gpu_im, ref_nl, ref_im):
+    np.testing.assert_array_equal(gpu_nl, ref_nl)
+    np.testing.assert_array_equal(np.where(ref_nl >= 0, gpu_im, 0), np.where(ref_nl >= 0, ref_im, 0))
+
+
+# ------------------------------------------------------------------ neighbour list
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["water64", "water8", "water32", "water4096", "cu3"])
+def test_nlist_bit_exact(dp, prec, case):
+    if case.startswith("water"):
+        s = synth.water_box(int(case[5:]), 0)
+        w = synth.water_weights()
+        method = "brute" if s.natoms <= 200 else "cell"
+    else:
+        s = synth.copper_fcc(int(case[2:]), 0)
+        w = synth.copper_weights()
+        method = "brute"
+    if case == "water8":
+        # 8 molecules: a 6.2 A box, several periodic images of every atom are in reach
+        w = synth.xavier_weights(("O", "H"), 6.0, 0.5, (200, 400), 1001)
+    ref_nl, ref_im, _, ovf = oracle.Model(w.to_blob()).nlist(s.coords, s.types, s.box, method)
+    assert not ovf
+    m = dp.DPModel(w, prec, max_atoms=s.natoms)
+    x, t = _cuda(s)
+    m.compute(x, t, s.box)
+    nl, im = m.get_nlist()
+    _nl_rows_equal(nl.cpu().numpy(), im.cpu().numpy(), ref_nl, ref_im)
+
+
+def test_nlist_bit_exact_copper_full(dp):
+    s = synth.copper_fcc(32, 0)
+    w = synth.copper_weights()
+    ref_nl, ref_im, _, ovf = oracle.Model(w.to_blob()).nlist(s.coords, s.types, s.box, "cell")
+    m = dp.DPModel(w, "fp32", max_atoms=s.natoms)
+    x, t = _cuda(s)
+    m.compute(x, t, s.box)
+    nl, im = m.get_nlist()
+    _nl_rows_equal(nl.cpu().numpy(), im.cpu().numpy(), ref_nl, ref_im)
+
+
+# ------------------------------------------------------------------ energies / forces
+def _rel_energy_err(Ei, ref):
+    scale = np.maximum(np.abs(ref), np.abs(ref).mean())
+    return np.abs(Ei - ref) / scale
+
+
+@pytest.mark.parametrize("n_mol,seed", [(64, 0), (1024, 3), (37, 9)])
+def test_fp64_matches_oracle(dp, n_mol, seed):
+    s = synth.water_box(n_mol, seed)
+    w = synth.water_weights()
+    ref = oracle.Model(w.to_blob()).compute(s.coords, s.types, s.box)
+    m = dp.DPModel(w, "fp64", max_atoms=s.natoms)
+    x, t = _cuda(s)
+    out = m.compute(x, t, s.box)
+    Ei = out["atom_energy"].cpu().numpy()
+    assert _rel_energy_err(Ei, ref["atom_energy"]).max() <= 1e-10
+    assert out["energy"].item() == pytest.approx(ref["energy"], rel=1e-12)
+    F = out["forces"].cpu().numpy()
+    Fs = np.abs(ref["forces"]).max()
+    assert np.abs(F - ref["forces"]).max() <= 1e-9 * Fs
+    np.testing.assert_allclose(out["virial"].cpu().numpy(), ref["virial"], rtol=1e-9, atol=1e-12 * Fs)
+
+
+def test_fp64_copper_small(dp):
+    s = synth.copper_fcc(4, 2)
+    w = synth.copper_weights()
+    ref = oracle.Model(w.to_blob()).compute(s.coords, s.types, s.box)
+    m = dp.DPModel(w, "fp64", max_atoms=s.natoms)
+    x, t = _cuda(s)
+    out = m.compute(x, t, s.box)
+    assert _rel_energy_err(out["atom_energy"].cpu().numpy(), ref["atom_energy"]).max() <= 1e-10
+    Fs = np.abs(ref["forces"]).max()
+    assert np.abs(out["forces"].cpu().numpy() - ref["forces"]).max() <= 1e-9 * Fs
+
+
+@pytest.mark.parametrize("n_mol", [64, 1024])
+def test_fp32_matches_oracle(dp, n_mol):
+    s = synth.water_box(n_mol, 1)
+    w = synth.water_weights()
+    ref = oracle.Model(w.to_blob()).compute(s.coords, s.types, s.box)
+    m = dp.DPModel(w, "fp32", max_atoms=s.natoms)
+    x, t = _cuda(s)
+    out = m.compute(x, t, s.box)
+    F = out["forces"].cpu().numpy()
+    rmse = np.sqrt(((F - ref["forces"]) ** 2).mean())
+    rms = np.sqrt((ref["forces"] ** 2).mean())
+    assert rmse <= 1e-5
+    assert rmse / rms <= 1e-4
+    Ei = out["atom_energy"].cpu().numpy()
+    assert np.abs(Ei - ref["atom_energy"]).max() <= 1e-5
+    assert abs(out["energy"].item() - ref["energy"]) / s.natoms <= 1e-6
+
+
+def test_fp32_copper_subbox(dp):
+    """Cu 32^3 (131,072 atoms) in FP32; errors on the 4,000 atoms of FCC cells [0,10)^3,
+    with the oracle evaluating only centres within r_c of that sub-box."""
+    s = synth.copper_fcc(32, 0)
+    w = synth.copper_weights()
+    a = 3.634
+    sub, centre = _copper_subbox_masks(s, a, w.rcut)
+    ref = oracle.Model(w.to_blob()).compute(s.coords, s.types, s.box, centre_mask=centre)
+    m = dp.DPModel(w, "fp32", max_atoms=s.natoms)
+    x, t = _cuda(s)
+    out = m.compute(x, t, s.box)
+    F = out["forces"].cpu().numpy()[sub]
+    rmse = np.sqrt(((F - ref["forces"][sub]) ** 2).mean())
+    assert rmse <= 1e-5
+    Ei = out["atom_energy"].cpu().numpy()[sub]
+    assert np.abs(Ei - ref["atom_energy"][sub]).max() <= 1e-5
+
+
+def _copper_subbox_masks(s, a, rcut):
+    """Atoms of FCC cells [0,10)^3 (by lattice site) and all centres within r_c of them."""
+    L = s.box[0]
+    site = np.rint(s.coords / (a / 2)).astype(int)  # half-lattice index of the nearest site
+    sub = np.all((site >= 0) & (site < 20), axis=1)
+    assert sub.sum() == 4000
+    lo, hi = -rcut - 0.5, 10 * a + rcut + 0.5
+    w = s.coords.copy()
+    w = w - L * np.floor(w / L)
+    w[w > L - rcut - 1.0] -= L
+    centre = np.all((w > lo) & (w < hi), axis=1)
+    return sub, centre
+
+
+# ------------------------------------------------------------------ batch / edge cases
+def test_batch_equals_single(dp):
+    reps = [synth.water_box(n, 10 + n) for n in (32, 40, 64, 7)]
+    w = synth.water_weights()
+    coords, types, offs, boxes = synth.concat(reps)
+    m = dp.DPModel(w, "fp64", max_atoms=len(types), max_replicas=len(reps))
+    x = torch.tensor(coords, device="cuda")
+    t = torch.tensor(types, device="cuda")
+    out = m.compute_batch(x, t, offs, boxes)
+    orc = oracle.Model(w.to_blob())
+    for r, s in enumerate(reps):
+        ref = orc.compute(s.coords, s.types, s.box)
+        assert out["energy"][r].item() == pytest.approx(ref["energy"], rel=1e-12)
+        F = out["forces"][offs[r]:offs[r + 1]].cpu().numpy()
+        assert np.abs(F - ref["forces"]).max() <= 1e-9 * np.abs(ref["forces"]).max()
+        np.testing.assert_allclose(out["virial"][r].cpu().numpy(), ref["virial"], rtol=1e-9, atol=1e-13)
+
+
+def test_isolated_atoms_and_single_atom(dp):
+    w = synth.water_weights()
+    orc = oracle.Model(w.to_blob())
+    L = 40.0
+    box = np.diag([L, L, L]).ravel()
+    for coords, types in ((np.array([[1.0, 2.0, 3.0]]), np.array([1], np.int32)),
+                          (np.array([[1.0, 2, 3], [20.0, 20, 20], [5.0, 30, 12]]), np.array([0, 1, 0], np.int32))):
+        m = dp.DPModel(w, "fp64", max_atoms=8)
+        out = m.compute(torch.tensor(coords, device="cuda"), torch.tensor(types, device="cuda"), box)
+        ref = orc.compute(coords, types, box)
+        np.testing.assert_allclose(out["atom_energy"].cpu().numpy(), ref["atom_energy"], rtol=1e-12)
+        assert np.abs(out["forces"].cpu().numpy()).max() == 0.0
+
+
+def test_sel_overflow_is_reported(dp):
+    w = synth.xavier_weights(("O", "H"), 6.0, 0.5, (10, 20), 1001)
+    s = synth.water_box(64, 0)
+    m = dp.DPModel(w, "fp64", max_atoms=s.natoms)
+    x, t = _cuda(s)
+    with pytest.raises(dp.DPError) as e:
+        m.compute(x, t, s.box)
+    assert e.value.status == 5
+    # the model stays usable
+    w2 = synth.water_weights()
+    m2 = dp.DPModel(w2, "fp64", max_atoms=s.natoms)
+    m2.compute(x, t, s.box)
+
+
+def test_bad_arguments(dp):
+    w = synth.water_weights()
+    s = synth.water_box(8, 0)
+    m = dp.DPModel(w, "fp64", max_atoms=s.natoms)
+    x, t = _cuda(s)
+    tri = s.box.copy()
+    tri[1] = 0.5
+    with pytest.raises(dp.DPError) as e:
+        m.compute(x, t, tri)
+    assert e.value.status == 4
+    big = synth.water_box(16, 0)
+    xb, tb = _cuda(big)
+    with pytest.raises(dp.DPError) as e:
+        m.compute(xb, tb, big.box)
+    assert e.value.status == 8
+    bad_t = t.clone()
+    bad_t[3] = 7
+    with pytest.raises(dp.DPError) as e:
+        m.compute(x, bad_t, s.box)
+    assert e.value.status == 1
+
+
+# ------------------------------------------------------------------ MD
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_md_matches_oracle_trajectory(dp, prec):
+    s = synth.water_box(64, 0)
+    w = synth.water_weights()
+    v0 = synth.maxwell_boltzmann(s.masses()[s.types], 300.0, 77)
+    nsteps = 20
+    ref = oracle.Model(w.to_blob()).md(s.coords, v0, s.types, s.box, s.masses(), 0.5, nsteps, rebuild_every=10)
+    m = dp.DPModel(w, prec, max_atoms=s.natoms)
+    x = torch.tensor(s.coords, device="cuda")
+    v = torch.tensor(v0, device="cuda")
+    t = torch.tensor(s.types, device="cuda")
+    st = m.md_state(x, v, t, s.box, s.masses(), rebuild_every=10)
+    out = m.verlet(st, 0.5, nsteps, capture_graph=True)
+    tol_x = 1e-10 if prec == "fp64" else 1e-6
+    np.testing.assert_allclose(x.cpu().numpy(), ref["x"], atol=tol_x)
+    np.testing.assert_allclose(v.cpu().numpy(), ref["v"], atol=tol_x)
+    assert out["potential"].item() == pytest.approx(ref["pe"][-1], rel=1e-10 if prec == "fp64" else 1e-6)
+    assert out["kinetic"].item() == pytest.approx(ref["ke"][-1], rel=1e-9 if prec == "fp64" else 1e-5)
+
+
+def test_md_graph_equals_eager(dp):
+    s = synth.water_box(64, 2)
+    w = synth.water_weights()
+    v0 = synth.maxwell_boltzmann(s.masses()[s.types], 300.0, 5)
+    res = []
+    for cap in (False, True):
+        m = dp.DPModel(w, "fp64", max_atoms=s.natoms)
+        x = torch.tensor(s.coords, device="cuda")
+        v = torch.tensor(v0, device="cuda")
+        t = torch.tensor(s.types, device="cuda")
+        st = m.md_state(x, v, t, s.box, s.masses(), rebuild_every=5)
+        m.verlet(st, 0.5, 12, capture_graph=cap)
+        res.append((x.cpu().numpy(), v.cpu().numpy()))
+    np.testing.assert_allclose(res[0][0], res[1][0], atol=1e-12)
+    np.testing.assert_allclose(res[0][1], res[1][1], atol=1e-12)
+
+
+def test_md_skin_exceeded_is_reported(dp):
+    s = synth.water_box(8, 0)
+    w = synth.water_weights()
+    m = dp.DPModel(w, "fp64", max_atoms=s.natoms)
+    x = torch.tensor(s.coords, device="cuda")
+    v = torch.zeros_like(x)
+    v[0, 0] = 0.5  # 0.5 A/fs: 1.25 A after 5 steps of 0.5 fs, beyond skin/2
+    t = torch.tensor(s.types, device="cuda")
+    st = m.md_state(x, v, t, s.box, s.masses(), rebuild_every=100)
+    with pytest.raises(dp.DPError) as e:
+        m.verlet(st, 0.5, 6, capture_graph=False)
+    assert e.value.status == 6
