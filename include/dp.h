@@ -197,6 +197,15 @@ dp_status dp_phase_times(dp_model* m, int repeats, float* ms);
    kernel in the graph).  Host-side counter; no synchronisation. */
 long long dp_kernel_launches(const dp_model* m);
 
+/*
+ * dp_selftest -- built-in check of the tensor-core operand layouts on the current
+ * device: runs one tcgen05 MMA of a known small-integer problem (case `which`:
+ * 0..4 = shapes N 64/112/240/32/160, bf16 or fp16 operands) and writes
+ * result[0] = max |error| against the exact product, result[1] = max |value|.
+ * Returns DP_ERR_UNSUPPORTED on a device without tcgen05.
+ */
+dp_status dp_selftest(int which, double* result);
+
 /* Wait for the model's stream; return and clear the sticky device error (DP_OK if none). */
 dp_status dp_sync(dp_model* m);
 

@@ -31,7 +31,7 @@ STATUS = {0: "DP_OK", 1: "DP_ERR_ARG", 2: "DP_ERR_CUDA", 3: "DP_ERR_OOM", 4: "DP
 # exported symbols of include/dp.h
 EXPORTS = ("dp_create", "dp_compute", "dp_compute_batch", "dp_verlet_step", "dp_md_run_batch", "dp_param_grad",
            "dp_ntheta", "dp_get_nlist", "dp_phase_times", "dp_kernel_launches", "dp_sync", "dp_last_error",
-           "dp_destroy", "dp_version")
+           "dp_destroy", "dp_version", "dp_selftest")
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -83,8 +83,9 @@ def lib():
             L.dp_phase_times.argtypes = [_P, _I, _P]
             L.dp_kernel_launches.argtypes = [_P]
             L.dp_kernel_launches.restype = ctypes.c_longlong
+            L.dp_selftest.argtypes = [_I, _P]
             for name in ("dp_create", "dp_compute", "dp_compute_batch", "dp_verlet_step", "dp_md_run_batch",
-                         "dp_param_grad", "dp_get_nlist", "dp_phase_times", "dp_sync"):
+                         "dp_param_grad", "dp_get_nlist", "dp_phase_times", "dp_sync", "dp_selftest"):
                 getattr(L, name).restype = _I
             _lib = L
     return _lib
@@ -98,6 +99,15 @@ def _ptr(t):
 
 def _host_f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def selftest(which: int):
+    """Run the library's tensor-core layout self check; returns (max error, max value)."""
+    out = (ctypes.c_double * 2)()
+    st = lib().dp_selftest(int(which), ctypes.cast(out, _P))
+    if st != 0:
+        raise DPError(st, "dp_selftest failed")
+    return out[0], out[1]
 
 
 class DPModel:

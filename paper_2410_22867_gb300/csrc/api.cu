@@ -242,12 +242,21 @@ unsigned long long hash_geom(const Model* m) {
 
 dp_status capture_step(Model* m, int N, double dt, bool rebuild, cudaGraphExec_t* out, long long* kernels) {
   cudaGraph_t graph = nullptr;
-  DP_CUDA_TRY(m, cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
+  // capture on the model's own stream (the caller's may be the uncapturable legacy stream)
+  cudaStream_t user = m->stream;
+  m->stream = m->capture_stream;
+  cudaError_t e0 = cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal);
+  if (e0 != cudaSuccess) {
+    m->stream = user;
+    m->last_error = std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e0);
+    return DP_ERR_CUDA;
+  }
   const long long before = m->launches;
   dp_status st = md_step(m, N, dt, rebuild);
   *kernels = m->launches - before;  // counted when the graph is replayed, not now
   m->launches = before;
   cudaError_t e = cudaStreamEndCapture(m->stream, &graph);
+  m->stream = user;
   if (st != DP_OK) { if (graph) cudaGraphDestroy(graph); return st; }
   if (e != cudaSuccess) { m->last_error = std::string("stream capture: ") + cudaGetErrorString(e); return DP_ERR_CUDA; }
   e = cudaGraphInstantiate(out, graph, 0);
@@ -373,6 +382,8 @@ dp_status dp_create(dp_model** out, int ntypes, const char* const* type_map, dou
   }
   m->ntypes = ntypes; m->switch_kind = P.switch_kind; m->rc = P.rc; m->rs = P.rs; m->skin = skin; m->prec = prec;
   m->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaStreamCreateWithFlags(&m->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(DP_ERR_CUDA, "cannot create the capture stream");
   m->max_atoms = max_atoms; m->max_reps = max_replicas;
   m->max_cells = max_atoms + 64 * max_replicas + 1024;
   m->sel_off[0] = 0; m->vcap_off[0] = 0;
@@ -423,6 +434,12 @@ dp_status dp_create(dp_model** out, int ntypes, const char* const* type_map, dou
   A_(rep_off_dev, 4 * (R + 1));
   A_(err, 16);
   A_(small_i, 4 * 64 + 8 * kMaxTypes);
+  if (prec == DP_MIX_BF16 || prec == DP_MIX_FP16) {
+    A_(rowoff, 4 * (size_t)nt * (N + 1));
+    A_(scan_blk, 4 * (size_t)nt * (N / 1024 + 2));
+    A_(Tseg, 4 * (size_t)nt * N * 400);
+    A_(dTm, 16 * N * kN3);
+  }
 #undef A_
   if (halloc(m, &m->geom_host, sizeof(RepGeom) * R + sizeof(int) * (R + 1) + 64) != DP_OK) return fail(DP_ERR_OOM, m->last_error);
   if (halloc(m, &m->err_host, 64) != DP_OK) return fail(DP_ERR_OOM, m->last_error);
@@ -572,6 +589,7 @@ void dp_destroy(dp_model* h) {
   Model* m = &h->m;
   cudaStreamSynchronize(m->stream);
   drop_graphs(m);
+  if (m->capture_stream) cudaStreamDestroy(m->capture_stream);
   for (void* p : allocs(m).dev) cudaFree(p);
   for (void* p : allocs(m).host) cudaFreeHost(p);
   forget(m);

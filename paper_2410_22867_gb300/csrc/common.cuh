@@ -64,6 +64,7 @@ struct Model {
   dp_precision prec = DP_FP64;
   int max_atoms = 0, max_reps = 0, max_cells = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t capture_stream = nullptr;  // owned; graphs are captured here, replayed on `stream`
   std::string last_error;
   long long ntheta = 0;
   std::vector<double> theta_host;
@@ -136,6 +137,11 @@ struct Model {
   int* err = nullptr;         // sticky error word
   int* err_host = nullptr;    // pinned
   int* small_i = nullptr;     // [64] device: small integer tables (sel, offsets)
+  // mixed-precision path
+  int* rowoff = nullptr;      // [nt][N + 1] row offsets of each atom in the per-type neighbour streams
+  int* scan_blk = nullptr;    // [nt][N / 1024 + 1]
+  float* Tseg = nullptr;      // [nt][N][400] partial T per neighbour type
+  void* dTm = nullptr;        // [N][100] float4
 
   // MD bookkeeping
   int natoms = 0;             // atoms of the current call
@@ -216,6 +222,10 @@ dp_status launch_get_nlist(Model* m, int N, int* nlist, int* images);
 dp_status launch_descriptor(Model* m, int N);
 dp_status launch_fitting(Model* m, int N);
 dp_status launch_embed_backward(Model* m, int N);
+// mix_embed.cu (tensor-core embedding net)
+dp_status launch_mix_descriptor(Model* m, int N);
+dp_status launch_mix_embed_backward(Model* m, int N);
+inline bool is_mixed(const Model* m) { return m->prec == DP_MIX_BF16 || m->prec == DP_MIX_FP16; }
 // md.cu
 dp_status launch_outputs(Model* m, int N, double* energy_rep, double* atom_energy, double* forces,
                          double* virial_rep);

@@ -1,0 +1,813 @@
+// Mixed-precision embedding net, descriptor and embedding backward on the
+// tensor cores (tcgen05 / TMEM), Section III-B3's mixed precision mapped to
+// Blackwell: the 25->50 and 50->100 layers of the embedding net (and their
+// backward) are MMAs with 16-bit operands and FP32 accumulation in TMEM; the
+// environment matrix, the 1->25 layer, all tanh (on the SFU) and residuals, the
+// reduction T = (1/S) R_hat^T G and the descriptor D stay FP32 on the CUDA cores.
+//
+// Work decomposition.  For each neighbour type tj the real neighbours of all
+// atoms form one "row stream" (atoms in internal, type-sorted order; rows of an
+// atom contiguous).  The concatenated streams are split into one contiguous chunk
+// per CTA, walked in tiles of at most 128 rows (one row per thread and TMEM lane)
+// that never cross a centre-type boundary and hold at most kMaxAtoms atoms.  T of
+// an atom is accumulated in shared memory across consecutive tiles and written
+// once; only atoms split between two CTAs use global atomics.  Activations of the
+// embedding net are recomputed in the backward instead of being stored.
+#include "tc_common.cuh"
+
+namespace dpg {
+namespace {
+
+constexpr int kRows = 128;     // rows per tile = threads per CTA = TMEM lanes
+constexpr int kMaxAtoms = 8;   // atom segments per tile
+constexpr int kGS = kN3;       // fp32 G row stride in smem (100 floats = 25 x 16 B: conflict-free)
+
+struct MixArgs {
+  int N, ntypes, S;
+  int sel_off[kMaxTypes + 1];
+  float rc, rs, invS;
+  int switch_kind;
+  const float* w;        // theta (fp32)
+  const float* stat;     // davg [nt][4], 1/dstd [nt][4]
+  const int* itype;
+  const int* type_off;   // device [nt + 1]
+  const int* rowoff;     // [nt][N + 1] exclusive scan of nl_count over atoms, per neighbour type
+  const int* nl_j;
+  const float4* nl_d;
+  float* Tseg;           // [nt][N][400] partial T per neighbour type
+  const float4* dT;      // [N][100]: dE/dT[c][a] * (1/S), c in x..w
+  double* force;         // [N][3]
+  double* vir_atom;      // [N][9]
+  int* err;
+};
+
+__device__ __forceinline__ unsigned char* align1024(unsigned char* p) {
+  uint32_t a = tc::smem_u32(p);
+  return p + ((1024u - (a & 1023u)) & 1023u);
+}
+
+template <class T>
+__device__ __forceinline__ void switch_fn(T r, T rs, T rc, int kind, T& sw, T& dsw) {
+  if (r < rs) { sw = T(1); dsw = T(0); return; }
+  if (r >= rc) { sw = T(0); dsw = T(0); return; }
+  T w = rc - rs;
+  T u = (r - rs) / w;
+  if (kind == 1) {
+    const T pi = T(3.14159265358979323846);
+    sw = T(0.5) * cosf(pi * u) + T(0.5);
+    dsw = T(-0.5) * pi * sinf(pi * u) / w;
+  } else {
+    T u2 = u * u;
+    sw = u2 * u * (T(-6) * u2 + T(15) * u - T(10)) + T(1);
+    dsw = T(-30) * u2 * (u - T(1)) * (u - T(1)) / w;
+  }
+}
+
+// Shared state of a tile walk.
+struct TileInfo {
+  int tj, ti, p, nrows, a0, cs, ce;  // stream, centre type, first row (stream coords), rows, first atom, chunk
+};
+
+// Thread 0 locates the tile starting at global row `cur` (chunk [c0, c1)).
+__device__ void locate_tile(const MixArgs& a, int cur, int c0, int c1, TileInfo* ti_out, int* sRow) {
+  int base = 0, tj = 0;
+  for (;; ++tj) {
+    int tot = a.rowoff[(size_t)tj * (a.N + 1) + a.N];
+    if (cur < base + tot || tj == a.ntypes - 1) break;
+    base += tot;
+  }
+  const int* ro = a.rowoff + (size_t)tj * (a.N + 1);
+  const int p = cur - base;
+  int lo = 0, hi = a.N - 1;  // largest atom i with ro[i] <= p
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (ro[mid] <= p) lo = mid; else hi = mid - 1;
+  }
+  const int a0 = lo;
+  const int ti = a.itype[a0];
+  int end = min(c1 - base, ro[a.N]);
+  end = min(end, ro[a.type_off[ti + 1]]);
+  end = min(end, ro[min(a0 + kMaxAtoms, a.N)]);
+  end = min(end, p + kRows);
+  TileInfo t;
+  t.tj = tj; t.ti = ti; t.p = p; t.nrows = end - p; t.a0 = a0; t.cs = c0 - base; t.ce = c1 - base;
+  *ti_out = t;
+  for (int k = 0; k <= kMaxAtoms; ++k) sRow[k] = ro[min(a0 + k, a.N)];
+}
+
+// Embedding weights of pair (ti, tj) into the MMA operand blocks and small fp32 arrays.
+//   B2: [64 x 64] rows n (layer-2 output), K = layer-1 unit (25 used) -> W2[k][n]
+//   B3: [112 x 64] rows a (layer-3 output), K = layer-2 unit (50 used) -> W3[m][a]
+template <bool F16>
+__device__ void load_fwd_weights(const float* __restrict__ W, unsigned char* sB2, unsigned char* sB3, float* small) {
+  const int t = threadIdx.x;
+  for (int q = t; q < 64 * 8; q += kRows) {
+    int n = q >> 3, k0 = (q & 7) * 8;
+    uint32_t p[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      int k = k0 + 2 * h;
+      float x0 = (n < kN2 && k < kN1) ? W[kEW2 + k * kN2 + n] : 0.f;
+      float x1 = (n < kN2 && k + 1 < kN1) ? W[kEW2 + (k + 1) * kN2 + n] : 0.f;
+      p[h] = tc::pack2<F16>(x0, x1);
+    }
+    tc::st_chunk(sB2, n, k0, make_uint4(p[0], p[1], p[2], p[3]));
+  }
+  for (int q = t; q < 112 * 8; q += kRows) {
+    int n = q >> 3, k0 = (q & 7) * 8;
+    uint32_t p[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      int k = k0 + 2 * h;
+      float x0 = (n < kN3 && k < kN2) ? W[kEW3 + k * kN3 + n] : 0.f;
+      float x1 = (n < kN3 && k + 1 < kN2) ? W[kEW3 + (k + 1) * kN3 + n] : 0.f;
+      p[h] = tc::pack2<F16>(x0, x1);
+    }
+    tc::st_chunk(sB3, n, k0, make_uint4(p[0], p[1], p[2], p[3]));
+  }
+  // small: W1[25], b1[25], b2[50], b3[100]
+  for (int q = t; q < 200; q += kRows) {
+    float v;
+    if (q < 25) v = W[kEW1 + q];
+    else if (q < 50) v = W[kEb1 + q - 25];
+    else if (q < 100) v = W[kEb2 + q - 50];
+    else v = W[kEb3 + q - 100];
+    small[q] = v;
+  }
+}
+
+// Backward operand blocks: W3 as [64 (m) x 112 (a)] in two K blocks, W2 as [32 (k) x 64 (m)].
+template <bool F16>
+__device__ void load_bwd_weights(const float* __restrict__ W, unsigned char* sB3b, unsigned char* sB2b) {
+  const int t = threadIdx.x;
+  for (int q = t; q < 2 * 64 * 8; q += kRows) {
+    int kb = q / 512, rem = q % 512;
+    int m = rem >> 3, k0 = (rem & 7) * 8;
+    uint32_t p[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      int a0 = kb * 64 + k0 + 2 * h;
+      float x0 = (m < kN2 && a0 < kN3) ? W[kEW3 + m * kN3 + a0] : 0.f;
+      float x1 = (m < kN2 && a0 + 1 < kN3) ? W[kEW3 + m * kN3 + a0 + 1] : 0.f;
+      p[h] = tc::pack2<F16>(x0, x1);
+    }
+    tc::st_chunk(sB3b + kb * 64 * 128, m, k0, make_uint4(p[0], p[1], p[2], p[3]));
+  }
+  for (int q = t; q < 32 * 8; q += kRows) {
+    int k = q >> 3, m0 = (q & 7) * 8;
+    uint32_t p[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      int m = m0 + 2 * h;
+      float x0 = (k < kN1 && m < kN2) ? W[kEW2 + k * kN2 + m] : 0.f;
+      float x1 = (k < kN1 && m + 1 < kN2) ? W[kEW2 + k * kN2 + m + 1] : 0.f;
+      p[h] = tc::pack2<F16>(x0, x1);
+    }
+    tc::st_chunk(sB2b, k, m0, make_uint4(p[0], p[1], p[2], p[3]));
+  }
+}
+
+// Per-row front end shared by forward and backward: environment row and layer 1.
+struct RowFront {
+  float d[3], R[4], r, sw, dsw;
+  int atom, la, j;
+};
+
+__device__ __forceinline__ int local_atom(const int* sRow, int row) {
+  int la = 0;
+#pragma unroll
+  for (int k = 1; k < kMaxAtoms; ++k) la += (sRow[k] <= row) ? 1 : 0;
+  return la;
+}
+
+__device__ __forceinline__ void row_front(const MixArgs& a, const TileInfo& ti, const int* sRow, int t,
+                                          bool want_j, RowFront& f) {
+  const int row = ti.p + t;
+  f.la = local_atom(sRow, row);
+  f.atom = ti.a0 + f.la;
+  const size_t e = (size_t)f.atom * a.S + a.sel_off[ti.tj] + (row - sRow[f.la]);
+  float4 dv = a.nl_d[e];
+  f.j = want_j ? a.nl_j[e] : 0;
+  f.d[0] = dv.x; f.d[1] = dv.y; f.d[2] = dv.z;
+  f.r = sqrtf(dv.x * dv.x + dv.y * dv.y + dv.z * dv.z);
+  switch_fn<float>(f.r, a.rs, a.rc, a.switch_kind, f.sw, f.dsw);
+  const float s = f.sw / f.r;
+  f.R[0] = s; f.R[1] = s * dv.x / f.r; f.R[2] = s * dv.y / f.r; f.R[3] = s * dv.z / f.r;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) f.R[c] = (f.R[c] - a.stat[ti.ti * 4 + c]) * a.stat[(a.ntypes + ti.ti) * 4 + c];
+}
+
+// h1 = tanh(s_hat W1 + b1) and its 16-bit copy into the A block (K = 32 used).
+template <bool F16>
+__device__ __forceinline__ void layer1(const float* small, float x, float* h1, unsigned char* sA, int t) {
+#pragma unroll
+  for (int k = 0; k < kN1; ++k) h1[k] = tc::tanh_fast(fmaf(x, small[k], small[25 + k]));
+#pragma unroll
+  for (int k0 = 0; k0 < 32; k0 += 8) {
+    uint32_t p[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      int k = k0 + 2 * h;
+      p[h] = tc::pack2<F16>(k < kN1 ? h1[k] : 0.f, k + 1 < kN1 ? h1[k + 1] : 0.f);
+    }
+    tc::st_chunk(sA, t, k0, make_uint4(p[0], p[1], p[2], p[3]));
+  }
+}
+
+// Layer-2 epilogue: h2 = [h1, h1] + tanh(z2 + b2); 16-bit copy into the A block (K = 64, 50 used).
+template <bool F16>
+__device__ __forceinline__ void layer2_epi(uint32_t tl, const float* small, const float* h1, float* h2,
+                                           unsigned char* sA, int t) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    float z[16];
+    tc::tmem_ld16(tl + 16 * c, z);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int m = 16 * c + u;
+      if (m < kN2) h2[m] = h1[m % kN1] + tc::tanh_fast(z[u] + small[50 + m]);
+    }
+  }
+#pragma unroll
+  for (int k0 = 0; k0 < 64; k0 += 8) {
+    uint32_t p[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      int m = k0 + 2 * h;
+      p[h] = tc::pack2<F16>(m < kN2 ? h2[m] : 0.f, m + 1 < kN2 ? h2[m + 1] : 0.f);
+    }
+    tc::st_chunk(sA, t, k0, make_uint4(p[0], p[1], p[2], p[3]));
+  }
+}
+
+__device__ __forceinline__ void mma_sync_wait(uint64_t* bar, uint32_t& phase, int* err, bool& ok) {
+  ok = tc::mbar_wait(bar, phase, err) && ok;
+  phase ^= 1u;
+  tc::tc_fence_after();
+}
+
+__device__ __forceinline__ void operand_barrier() {
+  tc::fence_async_smem();
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+}
+
+// ------------------------------------------------------------------ forward
+template <bool F16>
+__global__ void __launch_bounds__(kRows, 2) k_mix_embed_fwd(MixArgs a) {
+  extern __shared__ unsigned char sraw[];
+  unsigned char* sm = align1024(sraw);
+  unsigned char* sA = sm;                          // 16 KB operand block (h1, then h2)
+  float* sG = reinterpret_cast<float*>(sm);        // [128][100] fp32, aliases sA after MMA 3
+  unsigned char* sB2 = sm + 52224;                 // 8 KB
+  unsigned char* sB3 = sB2 + 8192;                 // 14 KB
+  float4* sR = reinterpret_cast<float4*>(sB3 + 14336);  // [128]
+  float* sTacc = reinterpret_cast<float*>(sR + kRows);  // [kMaxAtoms][400]
+  float* small = sTacc + kMaxAtoms * 400;               // 200
+  int* sRow = reinterpret_cast<int*>(small + 200);      // kMaxAtoms + 1
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tslot;
+  __shared__ TileInfo sti;
+  const int t = threadIdx.x, w = t >> 5;
+
+  int total = 0;
+  for (int tj = 0; tj < a.ntypes; ++tj) total += a.rowoff[(size_t)tj * (a.N + 1) + a.N];
+  const int per = (total + gridDim.x - 1) / gridDim.x;
+  const int c0 = min(total, blockIdx.x * per), c1 = min(total, c0 + per);
+
+  if (t == 0) { tc::mbar_init(&bar, 1); tc::mbar_fence_init(); }
+  if (w == 0) { tc::tmem_alloc(&tslot, 256); tc::tmem_relinquish(); }
+  for (int q = t; q < kMaxAtoms * 400; q += kRows) sTacc[q] = 0.f;
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tslot;
+  const uint32_t tl = tmem + ((uint32_t)(32 * w) << 16);
+  uint32_t phase = 0;
+  bool ok = true;
+  int pair = -1;
+  long long carry = -1;  // (tj, atom) whose partial T sits in slot 0
+
+  for (int cur = c0; cur < c1 && ok;) {
+    if (t == 0) locate_tile(a, cur, c0, c1, &sti, sRow);
+    __syncthreads();
+    const TileInfo ti = sti;
+    const int np = ti.ti * a.ntypes + ti.tj;
+    if (np != pair) {
+      load_fwd_weights<F16>(a.w + (size_t)np * kEmbParams, sB2, sB3, small);
+      pair = np;
+    }
+    const long long key0 = (long long)ti.tj * a.N + ti.a0;
+    if (carry != key0)
+      for (int q = t; q < 400; q += kRows) sTacc[q] = 0.f;
+    __syncthreads();
+
+    // environment row and layer 1
+    float h1[kN1], h2[kN2];
+    RowFront f;
+    const bool valid = t < ti.nrows;
+    if (valid) {
+      row_front(a, ti, sRow, t, false, f);
+    } else {
+      f.R[0] = f.R[1] = f.R[2] = f.R[3] = 0.f;
+      f.la = 0;
+    }
+    sR[t] = make_float4(f.R[0], f.R[1], f.R[2], f.R[3]);
+    layer1<F16>(small, f.R[0], h1, sA, t);
+    operand_barrier();
+    if (t == 0) {
+      tc::mma_kblock(tmem, tc::smem_u32(sA), tc::smem_u32(sB2), tc::idesc_f16(128, 64, F16), false, 2);
+      tc::mma_commit(&bar);
+    }
+    mma_sync_wait(&bar, phase, a.err, ok);
+    layer2_epi<F16>(tl, small, h1, h2, sA, t);
+    operand_barrier();
+    if (t == 0) {
+      tc::mma_kblock(tmem + 64, tc::smem_u32(sA), tc::smem_u32(sB3), tc::idesc_f16(128, 112, F16), false, 4);
+      tc::mma_commit(&bar);
+    }
+    mma_sync_wait(&bar, phase, a.err, ok);
+    // layer-3 epilogue: G = [h2, h2] + tanh(z3 + b3) into sG (fp32)
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+      float z[16];
+      tc::tmem_ld16(tl + 64 + 16 * c, z);
+      tc::tmem_wait_ld();
+      if (c * 16 < kN3) {
+        float g[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int q = 16 * c + u;
+          g[u] = (q < kN3) ? h2[q % kN2] + tc::tanh_fast(z[u] + small[100 + (q < kN3 ? q : 0)]) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 16; u += 4)
+          if (16 * c + u < kN3)
+            *reinterpret_cast<float4*>(&sG[t * kGS + 16 * c + u]) = make_float4(g[u], g[u + 1], g[u + 2], g[u + 3]);
+      }
+    }
+    __syncthreads();
+    // T partial sums: thread (g, q) handles rows g, g+5, ... and columns 4q..4q+3
+    if (t < 125) {
+      const int g = t / 25, q = t - g * 25;
+      float acc[4][4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[c][u] = 0.f;
+      int cur_la = -1;
+      for (int r = g; r < ti.nrows; r += 5) {
+        const int la = local_atom(sRow, ti.p + r);
+        if (la != cur_la) {
+          if (cur_la >= 0) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                atomicAdd(&sTacc[cur_la * 400 + c * kN3 + 4 * q + u], acc[c][u]);
+                acc[c][u] = 0.f;
+              }
+          }
+          cur_la = la;
+        }
+        const float4 R = sR[r];
+        const float4 G = *reinterpret_cast<const float4*>(&sG[r * kGS + 4 * q]);
+        const float Rv[4] = {R.x, R.y, R.z, R.w}, Gv[4] = {G.x, G.y, G.z, G.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[c][u] = fmaf(Rv[c], Gv[u], acc[c][u]);
+      }
+      if (cur_la >= 0) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) atomicAdd(&sTacc[cur_la * 400 + c * kN3 + 4 * q + u], acc[c][u]);
+      }
+    }
+    __syncthreads();
+    // write complete atoms; carry the open one into slot 0
+    const int last_la = local_atom(sRow, ti.p + ti.nrows - 1);
+    const bool last_done = (ti.p + ti.nrows == sRow[last_la + 1]);
+    const int n_out = last_done ? last_la + 1 : last_la;
+    for (int la = 0; la < n_out; ++la) {
+      const bool shared = (sRow[la] < ti.cs) || (sRow[la + 1] > ti.ce);
+      float* dst = a.Tseg + ((size_t)ti.tj * a.N + ti.a0 + la) * 400;
+      for (int q = t; q < 400; q += kRows) {
+        const float v = sTacc[la * 400 + q];
+        if (shared) atomicAdd(&dst[q], v); else dst[q] = v;
+      }
+    }
+    __syncthreads();
+    if (!last_done) {
+      if (last_la != 0)
+        for (int q = t; q < 400; q += kRows) sTacc[q] = sTacc[last_la * 400 + q];
+      carry = (long long)ti.tj * a.N + ti.a0 + last_la;
+    } else {
+      carry = -1;
+    }
+    for (int q = t; q < (kMaxAtoms - 1) * 400; q += kRows) sTacc[400 + q] = 0.f;
+    __syncthreads();
+    cur += ti.nrows;
+  }
+  // an atom left open at the chunk end continues in the next CTA
+  if (carry >= 0) {
+    float* dst = a.Tseg + (size_t)carry * 400;
+    for (int q = t; q < 400; q += kRows) atomicAdd(&dst[q], sTacc[q]);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (w == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+// ------------------------------------------------------------------ backward
+template <bool F16>
+__global__ void __launch_bounds__(kRows, 2) k_mix_embed_bwd(MixArgs a) {
+  extern __shared__ unsigned char sraw[];
+  unsigned char* sm = align1024(sraw);
+  unsigned char* sA = sm;                          // 32 KB: h1 / h2 (block 0), dz3 (blocks 0-1), dz2 (block 0)
+  unsigned char* sB2 = sm + 32768;                 // 8 KB
+  unsigned char* sB3 = sB2 + 8192;                 // 14 KB
+  unsigned char* sB3b = sB3 + 14336;               // 16 KB (two K blocks of 64 rows)
+  unsigned char* sB2b = sB3b + 16384;              // 4 KB
+  float4* sdT = reinterpret_cast<float4*>(sB2b + 4096);  // [kMaxAtoms][100]
+  float* small = reinterpret_cast<float*>(sdT + kMaxAtoms * kN3);  // 200
+  int* sRow = reinterpret_cast<int*>(small + 200);
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tslot;
+  __shared__ TileInfo sti;
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+
+  int total = 0;
+  for (int tj = 0; tj < a.ntypes; ++tj) total += a.rowoff[(size_t)tj * (a.N + 1) + a.N];
+  const int per = (total + gridDim.x - 1) / gridDim.x;
+  const int c0 = min(total, blockIdx.x * per), c1 = min(total, c0 + per);
+
+  if (t == 0) { tc::mbar_init(&bar, 1); tc::mbar_fence_init(); }
+  if (w == 0) { tc::tmem_alloc(&tslot, 256); tc::tmem_relinquish(); }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tslot;
+  const uint32_t tl = tmem + ((uint32_t)(32 * w) << 16);
+  uint32_t phase = 0;
+  bool ok = true;
+  int pair = -1;
+
+  for (int cur = c0; cur < c1 && ok;) {
+    if (t == 0) locate_tile(a, cur, c0, c1, &sti, sRow);
+    __syncthreads();
+    const TileInfo ti = sti;
+    const int np = ti.ti * a.ntypes + ti.tj;
+    if (np != pair) {
+      const float* W = a.w + (size_t)np * kEmbParams;
+      load_fwd_weights<F16>(W, sB2, sB3, small);
+      load_bwd_weights<F16>(W, sB3b, sB2b);
+      pair = np;
+    }
+    const int natoms_tile = local_atom(sRow, ti.p + ti.nrows - 1) + 1;
+    for (int q = t; q < natoms_tile * kN3; q += kRows) sdT[q] = a.dT[(size_t)ti.a0 * kN3 + q];
+    __syncthreads();
+
+    float h1[kN1], h2[kN2];
+    RowFront f;
+    const bool valid = t < ti.nrows;
+    if (valid) {
+      row_front(a, ti, sRow, t, true, f);
+    } else {
+      f.R[0] = f.R[1] = f.R[2] = f.R[3] = 0.f;
+      f.la = 0; f.j = 0; f.atom = ti.a0;
+    }
+    layer1<F16>(small, f.R[0], h1, sA, t);
+    operand_barrier();
+    if (t == 0) {
+      tc::mma_kblock(tmem, tc::smem_u32(sA), tc::smem_u32(sB2), tc::idesc_f16(128, 64, F16), false, 2);
+      tc::mma_commit(&bar);
+    }
+    mma_sync_wait(&bar, phase, a.err, ok);
+    layer2_epi<F16>(tl, small, h1, h2, sA, t);
+    operand_barrier();
+    if (t == 0) {
+      tc::mma_kblock(tmem + 64, tc::smem_u32(sA), tc::smem_u32(sB3), tc::idesc_f16(128, 112, F16), false, 4);
+      tc::mma_commit(&bar);
+    }
+    mma_sync_wait(&bar, phase, a.err, ok);
+    // layer-3 epilogue (backward): G, dR_hat, dG, dz3 = dG (1 - t3^2) into A (two K blocks)
+    float dR[4] = {0.f, 0.f, 0.f, 0.f};
+    float dh2[kN2];
+#pragma unroll
+    for (int m = 0; m < kN2; ++m) dh2[m] = 0.f;
+    const float4* dTa = sdT + f.la * kN3;
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+      float z[16];
+      tc::tmem_ld16(tl + 64 + 16 * c, z);
+      tc::tmem_wait_ld();
+      float dz[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int q = 16 * c + u;
+        dz[u] = 0.f;
+        if (q < kN3) {
+          const float t3 = tc::tanh_fast(z[u] + small[100 + q]);
+          const float G = h2[q % kN2] + t3;
+          const float4 d4 = dTa[q];
+          dR[0] = fmaf(d4.x, G, dR[0]);
+          dR[1] = fmaf(d4.y, G, dR[1]);
+          dR[2] = fmaf(d4.z, G, dR[2]);
+          dR[3] = fmaf(d4.w, G, dR[3]);
+          const float dG = f.R[0] * d4.x + f.R[1] * d4.y + f.R[2] * d4.z + f.R[3] * d4.w;
+          dz[u] = dG * (1.f - t3 * t3);
+          dh2[q % kN2] += dG;
+        }
+      }
+      // 16 values = two 8-element chunks of K block (16c / 64)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k0 = 16 * c + 8 * h;
+        uint32_t p[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) p[v] = tc::pack2<F16>(dz[8 * h + 2 * v], dz[8 * h + 2 * v + 1]);
+        tc::st_chunk(sA + (k0 >> 6) * 16384, t, k0 & 63, make_uint4(p[0], p[1], p[2], p[3]));
+      }
+    }
+    operand_barrier();
+    // dh2 += dz3 W3^T  (N = 64 over m, K = 112 over a: two K blocks, the second with 48 used)
+    if (t == 0) {
+      const uint32_t id = tc::idesc_f16(128, 64, F16);
+      tc::mma_kblock(tmem, tc::smem_u32(sA), tc::smem_u32(sB3b), id, false, 4);
+      tc::mma_kblock(tmem, tc::smem_u32(sA + 16384), tc::smem_u32(sB3b + 8192), id, true, 3);
+      tc::mma_commit(&bar);
+    }
+    mma_sync_wait(&bar, phase, a.err, ok);
+    float dh1[kN1];
+#pragma unroll
+    for (int k = 0; k < kN1; ++k) dh1[k] = 0.f;
+    {
+      float dz2[64];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float z[16];
+        tc::tmem_ld16(tl + 16 * c, z);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int m = 16 * c + u;
+          dz2[m] = 0.f;
+          if (m < kN2) {
+            const float g2 = z[u] + dh2[m];
+            const float t2 = h2[m] - h1[m % kN1];
+            dz2[m] = g2 * (1.f - t2 * t2);
+            dh1[m % kN1] += g2;
+          }
+        }
+      }
+#pragma unroll
+      for (int k0 = 0; k0 < 64; k0 += 8) {
+        uint32_t p[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) p[v] = tc::pack2<F16>(dz2[k0 + 2 * v], dz2[k0 + 2 * v + 1]);
+        tc::st_chunk(sA, t, k0, make_uint4(p[0], p[1], p[2], p[3]));
+      }
+    }
+    operand_barrier();
+    // dh1 += dz2 W2^T  (N = 32 over k, K = 64 over m)
+    if (t == 0) {
+      tc::mma_kblock(tmem + 64, tc::smem_u32(sA), tc::smem_u32(sB2b), tc::idesc_f16(128, 32, F16), false, 4);
+      tc::mma_commit(&bar);
+    }
+    mma_sync_wait(&bar, phase, a.err, ok);
+    float ds = 0.f;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float z[16];
+      tc::tmem_ld16(tl + 64 + 16 * c, z);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int k = 16 * c + u;
+        if (k < kN1) {
+          const float g1 = z[u] + dh1[k];
+          ds = fmaf(g1 * (1.f - h1[k] * h1[k]), small[k], ds);
+        }
+      }
+    }
+    // chain rule through the normalisation and the environment row
+    double g3[3] = {0.0, 0.0, 0.0};
+    if (valid) {
+      dR[0] += ds;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) dR[c] *= a.stat[(a.ntypes + ti.ti) * 4 + c];
+      const float rinv = 1.f / f.r;
+      const float dsr = f.dsw * rinv - f.sw * rinv * rinv;
+      const float qv = f.sw * rinv * rinv;
+      const float dq = f.dsw * rinv * rinv - 2.f * f.sw * rinv * rinv * rinv;
+      const float proj = dR[1] * f.d[0] + dR[2] * f.d[1] + dR[3] * f.d[2];
+      const float common = (dR[0] * dsr + dq * proj) * rinv;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) g3[c] = (double)(common * f.d[c] + qv * dR[1 + c]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) atomicAdd(&a.force[3 * (size_t)f.j + c], -g3[c]);
+    }
+    // centre force and per-atom virial: warp-segmented sums over rows of the same atom
+    double vals[12];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) vals[c] = g3[c];
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) vals[3 + 3 * p + q] = -g3[p] * (double)f.d[q];
+    const int my = valid ? f.la : -1;
+    unsigned todo = __ballot_sync(0xffffffffu, valid);
+    while (todo) {
+      const int leader = __ffs(todo) - 1;
+      const int seg = __shfl_sync(0xffffffffu, my, leader);
+      const bool in = (my == seg);
+      const unsigned mask = __ballot_sync(0xffffffffu, in);
+#pragma unroll
+      for (int q = 0; q < 12; ++q) {
+        double v = in ? vals[q] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == leader) {
+          const size_t atom = (size_t)ti.a0 + seg;
+          if (q < 3) atomicAdd(&a.force[3 * atom + q], v);
+          else atomicAdd(&a.vir_atom[9 * atom + q - 3], v);
+        }
+      }
+      todo &= ~mask;
+    }
+    __syncthreads();
+    cur += ti.nrows;
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (w == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+// ------------------------------------------------------------------ small kernels
+// Exclusive scan of nl_count[i][tj] over atoms, per neighbour type: local (1024 per block),
+// block totals, fix-up.
+__global__ void k_scan_local(int N, int ntypes, const int* __restrict__ cnt, int* rowoff, int* blk) {
+  __shared__ int ws[32];
+  const int tj = blockIdx.y;
+  const int i = blockIdx.x * 1024 + threadIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int v = (i < N) ? cnt[(size_t)i * ntypes + tj] : 0;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int s = ws[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    ws[lane] = s;
+  }
+  __syncthreads();
+  const int excl = x - v + (w > 0 ? ws[w - 1] : 0);
+  if (i < N) rowoff[(size_t)tj * (N + 1) + i] = excl;
+  if (threadIdx.x == 1023) blk[tj * gridDim.x + blockIdx.x] = ws[31];
+}
+
+__global__ void k_scan_fix(int N, int nblk, int* rowoff, const int* blk) {
+  const int tj = blockIdx.y;
+  __shared__ int off;
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int b = 0; b < blockIdx.x; ++b) s += blk[tj * nblk + b];
+    off = s;
+    if (blockIdx.x == nblk - 1) {
+      int tot = s;
+      tot += blk[tj * nblk + blockIdx.x];
+      rowoff[(size_t)tj * (N + 1) + N] = tot;
+    }
+  }
+  __syncthreads();
+  const int i = blockIdx.x * 1024 + threadIdx.x;
+  if (i < N) rowoff[(size_t)tj * (N + 1) + i] += off;
+}
+
+// T = sum over neighbour types of the partial sums, scaled by 1/S; D = T^T T[:, :16]
+// (fp32 copy for the fitting net).
+__global__ void k_mix_descriptor(int N, int ntypes, float invS, const float* __restrict__ Tseg, float* Tm,
+                                 float* Dm) {
+  __shared__ float sT[400];
+  for (int i = blockIdx.x; i < N; i += gridDim.x) {
+    for (int q = threadIdx.x; q < 400; q += blockDim.x) {
+      float v = 0.f;
+      for (int tj = 0; tj < ntypes; ++tj) v += Tseg[((size_t)tj * N + i) * 400 + q];
+      v *= invS;
+      sT[q] = v;
+      Tm[(size_t)i * 400 + q] = v;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < kN3; q += blockDim.x) {
+      float out[kM2];
+#pragma unroll
+      for (int b = 0; b < kM2; ++b) {
+        float v = 0.f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v = fmaf(sT[c * kN3 + q], sT[c * kN3 + b], v);
+        out[b] = v;
+      }
+      float4* dst = reinterpret_cast<float4*>(Dm + (size_t)i * kKD + q * kM2);
+#pragma unroll
+      for (int b = 0; b < kM2; b += 4) dst[b / 4] = make_float4(out[b], out[b + 1], out[b + 2], out[b + 3]);
+    }
+    __syncthreads();
+  }
+}
+
+// dT[c][a] = (1/S) (sum_b dD[a][b] T[c][b] + [a < 16] sum_a' dD[a'][a] T[c][a']), stored [N][100] float4.
+__global__ void k_mix_dT(int N, float invS, const float* __restrict__ Tm, const float* __restrict__ dD,
+                         float4* dT) {
+  __shared__ float sT[400];
+  __shared__ float sD[kKD];
+  for (int i = blockIdx.x; i < N; i += gridDim.x) {
+    for (int q = threadIdx.x; q < 400; q += blockDim.x) sT[q] = Tm[(size_t)i * 400 + q];
+    for (int q = threadIdx.x; q < kKD; q += blockDim.x) sD[q] = dD[(size_t)i * kKD + q];
+    __syncthreads();
+    for (int q = threadIdx.x; q < kN3; q += blockDim.x) {
+      float v[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float s = 0.f;
+#pragma unroll
+        for (int b = 0; b < kM2; ++b) s = fmaf(sD[q * kM2 + b], sT[c * kN3 + b], s);
+        if (q < kM2)
+          for (int a2 = 0; a2 < kN3; ++a2) s = fmaf(sD[a2 * kM2 + q], sT[c * kN3 + a2], s);
+        v[c] = s * invS;
+      }
+      dT[(size_t)i * kN3 + q] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    __syncthreads();
+  }
+}
+
+MixArgs make_mix_args(Model* m, int N) {
+  MixArgs a{};
+  a.N = N; a.ntypes = m->ntypes; a.S = m->S;
+  for (int t = 0; t <= m->ntypes; ++t) a.sel_off[t] = m->sel_off[t];
+  a.rc = (float)m->rc; a.rs = (float)m->rs; a.invS = 1.f / (float)m->S; a.switch_kind = m->switch_kind;
+  a.w = m->w32; a.stat = m->stat32; a.itype = m->itype; a.type_off = m->type_off; a.rowoff = m->rowoff;
+  a.nl_j = m->nl_j; a.nl_d = static_cast<const float4*>(m->nl_d);
+  a.Tseg = m->Tseg; a.dT = static_cast<const float4*>(m->dTm);
+  a.force = m->force; a.vir_atom = m->vir_atom; a.err = m->err;
+  return a;
+}
+
+constexpr size_t kFwdSmem = 52224 + 8192 + 14336 + kRows * 16 + kMaxAtoms * 400 * 4 + 200 * 4 + 64 + 1024;
+constexpr size_t kBwdSmem = 32768 + 8192 + 14336 + 16384 + 4096 + kMaxAtoms * kN3 * 16 + 200 * 4 + 64 + 1024;
+
+}  // namespace
+
+dp_status launch_mix_descriptor(Model* m, int N) {
+  const int nblk = cdiv(N, 1024);
+  k_scan_local<<<dim3(nblk, m->ntypes), 1024, 0, m->stream>>>(N, m->ntypes, m->nl_count, m->rowoff, m->scan_blk);
+  k_scan_fix<<<dim3(nblk, m->ntypes), 1024, 0, m->stream>>>(N, nblk, m->rowoff, m->scan_blk);
+  DP_CUDA_TRY(m, cudaMemsetAsync(m->Tseg, 0, sizeof(float) * 400 * (size_t)N * m->ntypes, m->stream));
+  MixArgs a = make_mix_args(m, N);
+  const bool f16 = m->prec == DP_MIX_FP16;
+  const void* fn = f16 ? reinterpret_cast<const void*>(k_mix_embed_fwd<true>)
+                       : reinterpret_cast<const void*>(k_mix_embed_fwd<false>);
+  DP_CUDA_TRY(m, ensure_smem(fn, kFwdSmem));
+  const int grid = num_sms() * blocks_per_sm(fn, kRows, kFwdSmem);
+  if (f16) k_mix_embed_fwd<true><<<grid, kRows, kFwdSmem, m->stream>>>(a);
+  else k_mix_embed_fwd<false><<<grid, kRows, kFwdSmem, m->stream>>>(a);
+  k_mix_descriptor<<<std::min(N, 4 * num_sms()), 128, 0, m->stream>>>(N, m->ntypes, 1.f / (float)m->S, m->Tseg,
+                                                                       static_cast<float*>(m->Tm),
+                                                                       static_cast<float*>(m->Dm));
+  m->launches += 4;
+  DP_LAUNCH_CHECK(m);
+  return DP_OK;
+}
+
+dp_status launch_mix_embed_backward(Model* m, int N) {
+  k_mix_dT<<<std::min(N, 4 * num_sms()), 128, 0, m->stream>>>(N, 1.f / (float)m->S, static_cast<const float*>(m->Tm),
+                                                              static_cast<const float*>(m->dD),
+                                                              static_cast<float4*>(m->dTm));
+  DP_CUDA_TRY(m, cudaMemsetAsync(m->vir_atom, 0, sizeof(double) * 9 * (size_t)N, m->stream));
+  MixArgs a = make_mix_args(m, N);
+  const bool f16 = m->prec == DP_MIX_FP16;
+  const void* fn = f16 ? reinterpret_cast<const void*>(k_mix_embed_bwd<true>)
+                       : reinterpret_cast<const void*>(k_mix_embed_bwd<false>);
+  DP_CUDA_TRY(m, ensure_smem(fn, kBwdSmem));
+  const int grid = num_sms() * blocks_per_sm(fn, kRows, kBwdSmem);
+  if (f16) k_mix_embed_bwd<true><<<grid, kRows, kBwdSmem, m->stream>>>(a);
+  else k_mix_embed_bwd<false><<<grid, kRows, kBwdSmem, m->stream>>>(a);
+  m->launches += 2;
+  DP_LAUNCH_CHECK(m);
+  return DP_OK;
+}
+
+}  // namespace dpg

@@ -141,7 +141,12 @@ __global__ void __launch_bounds__(EB<T>::v) k_embed_fwd(EmbArgs<T> a) {
     T avg[4], isd[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) { avg[c] = a.stat[ti * 4 + c]; isd[c] = a.stat[(a.ntypes + ti) * 4 + c]; }
-    T acc[4] = {T(0), T(0), T(0), T(0)};
+    constexpr int NCOL = (kN3 + NB - 1) / NB;  // T columns owned by each thread
+    T acc[NCOL][4];
+#pragma unroll
+    for (int u = 0; u < NCOL; ++u)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[u][c] = T(0);
     for (int tj = 0; tj < a.ntypes; ++tj) {
       const int cnt = a.nl_count[(size_t)i * a.ntypes + tj];
       const T* W = sW + tj * kEmbParams;
@@ -171,22 +176,30 @@ __global__ void __launch_bounds__(EB<T>::v) k_embed_fwd(EmbArgs<T> a) {
           }
         }
         __syncthreads();
-        if (tid < kN3) {
-          for (int rr = 0; rr < rows; ++rr) {
-            T gv = sG[rr * kGP + tid];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[c] += sR[rr * 4 + c] * gv;
+        for (int u = 0; u < NCOL; ++u) {
+          const int col = tid + u * NB;
+          if (col < kN3) {
+            for (int rr = 0; rr < rows; ++rr) {
+              T gv = sG[rr * kGP + col];
+#pragma unroll
+              for (int c = 0; c < 4; ++c) acc[u][c] += sR[rr * 4 + c] * gv;
+            }
           }
         }
         __syncthreads();
       }
     }
-    if (tid < kN3) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        T v = acc[c] * a.invS;
-        sT[c * kN3 + tid] = v;
-        a.Tm[(size_t)i * 4 * kN3 + c * kN3 + tid] = v;
+    for (int u = 0; u < NCOL; ++u) {
+      const int col = tid + u * NB;
+      if (col < kN3) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          T v = acc[u][c] * a.invS;
+          sT[c * kN3 + col] = v;
+          a.Tm[(size_t)i * 4 * kN3 + c * kN3 + col] = v;
+        }
       }
     }
     __syncthreads();
@@ -555,12 +568,14 @@ dp_status run_embed_backward(Model* m, int N) {
 }  // namespace
 
 dp_status launch_descriptor(Model* m, int N) {
+  if (is_mixed(m)) return launch_mix_descriptor(m, N);
   return m->prec == DP_FP64 ? run_descriptor<double>(m, N) : run_descriptor<float>(m, N);
 }
 dp_status launch_fitting(Model* m, int N) {
   return m->prec == DP_FP64 ? run_fitting<double>(m, N) : run_fitting<float>(m, N);
 }
 dp_status launch_embed_backward(Model* m, int N) {
+  if (is_mixed(m)) return launch_mix_embed_backward(m, N);
   return m->prec == DP_FP64 ? run_embed_backward<double>(m, N) : run_embed_backward<float>(m, N);
 }
 

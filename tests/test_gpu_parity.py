@@ -269,3 +269,49 @@ def test_md_skin_exceeded_is_reported(dp):
     with pytest.raises(dp.DPError) as e:
         m.verlet(st, 0.5, 6, capture_graph=False)
     assert e.value.status == 6
+
+
+# ------------------------------------------------------------------ mixed precision (tensor cores)
+@pytest.mark.parametrize("which", [0, 1, 2, 3, 4])
+def test_tensor_core_layout_selftest(dp, which):
+    err, vmax = dp.selftest(which)
+    assert vmax > 1.0
+    assert err == 0.0
+
+
+@pytest.mark.parametrize("prec", ["mix_bf16", "mix_fp16"])
+@pytest.mark.parametrize("n_mol", [64, 1024])
+def test_mixed_matches_oracle_water(dp, prec, n_mol):
+    s = synth.water_box(n_mol, 2)
+    w = synth.water_weights()
+    ref = oracle.Model(w.to_blob()).compute(s.coords, s.types, s.box)
+    m = dp.DPModel(w, prec, max_atoms=s.natoms)
+    x, t = _cuda(s)
+    out = m.compute(x, t, s.box)
+    F = out["forces"].cpu().numpy()
+    rmse = np.sqrt(((F - ref["forces"]) ** 2).mean())
+    rms = np.sqrt((ref["forces"] ** 2).mean())
+    assert rmse <= 2e-3
+    assert rmse / rms <= 0.05, (rmse, rms)
+    e_atom = abs(out["energy"].item() - ref["energy"]) / s.natoms
+    assert e_atom <= 1e-4
+    np.testing.assert_allclose(out["virial"].cpu().numpy(), ref["virial"], rtol=0.05,
+                               atol=0.05 * np.abs(ref["virial"]).max())
+
+
+@pytest.mark.parametrize("prec", ["mix_bf16", "mix_fp16"])
+def test_mixed_copper_subbox(dp, prec):
+    s = synth.copper_fcc(32, 0)
+    w = synth.copper_weights()
+    sub, centre = _copper_subbox_masks(s, 3.634, w.rcut)
+    ref = oracle.Model(w.to_blob()).compute(s.coords, s.types, s.box, centre_mask=centre)
+    m = dp.DPModel(w, prec, max_atoms=s.natoms)
+    x, t = _cuda(s)
+    out = m.compute(x, t, s.box)
+    F = out["forces"].cpu().numpy()[sub]
+    Fr = ref["forces"][sub]
+    rmse = np.sqrt(((F - Fr) ** 2).mean())
+    assert rmse <= 2e-3
+    assert rmse / np.sqrt((Fr ** 2).mean()) <= 0.05
+    Ei = out["atom_energy"].cpu().numpy()[sub]
+    assert abs(Ei.sum() - ref["atom_energy"][sub].sum()) / 4000 <= 1e-4
