@@ -19,7 +19,7 @@
 namespace dpg {
 namespace tc {
 
-constexpr uint32_t kSpinLimit = 1u << 26;  // bounded waits: ~seconds, then error
+constexpr uint32_t kSpinLimit = 1u << 22;  // bounded waits (well under a second), then an error flag
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
