@@ -439,6 +439,7 @@ dp_status dp_create(dp_model** out, int ntypes, const char* const* type_map, dou
     A_(scan_blk, 4 * (size_t)nt * (N / 1024 + 2));
     A_(Tseg, 4 * (size_t)nt * N * 400);
     A_(dTm, 16 * N * kN3);
+    A_(tc_weights, mix_fit_weight_bytes(nt));
   }
 #undef A_
   if (halloc(m, &m->geom_host, sizeof(RepGeom) * R + sizeof(int) * (R + 1) + 64) != DP_OK) return fail(DP_ERR_OOM, m->last_error);

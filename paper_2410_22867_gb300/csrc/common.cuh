@@ -181,19 +181,37 @@ inline cudaError_t ensure_smem(const void* fn, size_t smem) {
   for (auto& e : done)
     if (e.first == fn && e.second >= smem) return cudaSuccess;
   cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err == cudaSuccess)  // prefer the largest shared-memory carveout so several CTAs fit per SM
+    err = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   if (err == cudaSuccess) done.push_back({fn, smem});
   return err;
 }
 
-// Resident blocks per SM for a launch shape, cached.
-inline int blocks_per_sm(const void* fn, int threads, size_t smem) {
-  struct E { const void* f; int t; size_t s; int n; };
+// Resident blocks per SM for a launch shape, from the kernel's registers and static
+// shared memory, the dynamic shared memory, and an optional TMEM column budget
+// (tcgen05 kernels hold `tmem_cols` of the SM's 512 columns each).  Cached.
+inline int blocks_per_sm(const void* fn, int threads, size_t smem, int tmem_cols = 0) {
+  struct E { const void* f; int t; size_t s; int c; int n; };
   static std::vector<E> cache;
   for (auto& e : cache)
-    if (e.f == fn && e.t == threads && e.s == smem) return e.n;
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess || n < 1) n = 1;
-  cache.push_back({fn, threads, smem, n});
+    if (e.f == fn && e.t == threads && e.s == smem && e.c == tmem_cols) return e.n;
+  int dev = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  cudaFuncAttributes fa;
+  int n = 1;
+  if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess && smem_sm > 0 && regs_sm > 0) {
+    const size_t per_block = smem + fa.sharedSizeBytes + 1024;  // 1 KB reserved per block
+    const int regs = ((fa.numRegs + 7) / 8) * 8 * threads;       // allocation granularity 8 per thread
+    n = (int)(smem_sm / per_block);
+    if (regs > 0) n = std::min(n, regs_sm / regs);
+    if (thr_sm > 0) n = std::min(n, thr_sm / threads);
+    if (tmem_cols > 0) n = std::min(n, 512 / tmem_cols);
+    n = std::max(1, std::min(n, 32));
+  }
+  cache.push_back({fn, threads, smem, tmem_cols, n});
   return n;
 }
 
@@ -225,6 +243,10 @@ dp_status launch_embed_backward(Model* m, int N);
 // mix_embed.cu (tensor-core embedding net)
 dp_status launch_mix_descriptor(Model* m, int N);
 dp_status launch_mix_embed_backward(Model* m, int N);
+// mix_fit.cu (tensor-core fitting net)
+dp_status mix_fit_setup(Model* m);
+size_t mix_fit_weight_bytes(int ntypes);
+dp_status launch_mix_fitting(Model* m, int N);
 inline bool is_mixed(const Model* m) { return m->prec == DP_MIX_BF16 || m->prec == DP_MIX_FP16; }
 // md.cu
 dp_status launch_outputs(Model* m, int N, double* energy_rep, double* atom_energy, double* forces,

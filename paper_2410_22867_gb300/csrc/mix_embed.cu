@@ -19,8 +19,10 @@ namespace dpg {
 namespace {
 
 constexpr int kRows = 128;     // rows per tile = threads per CTA = TMEM lanes
-constexpr int kMaxAtoms = 8;   // atom segments per tile
-constexpr int kGS = kN3;       // fp32 G row stride in smem (100 floats = 25 x 16 B: conflict-free)
+constexpr int kMaxAtoms = 6;   // atom segments per tile
+constexpr int kGS = 36;        // fp32 G staging row stride: 32 columns + 4 (9 x 16 B: conflict-free float4)
+constexpr int kGStage = 18432; // 128 x 36 x 4 bytes (>= the 16 KB operand block it aliases)
+constexpr uint32_t kTmemCols = 128;  // per CTA: D2/D3 share columns 0..111
 
 struct MixArgs {
   int N, ntypes, S;
@@ -68,31 +70,69 @@ struct TileInfo {
   int tj, ti, p, nrows, a0, cs, ce;  // stream, centre type, first row (stream coords), rows, first atom, chunk
 };
 
-// Thread 0 locates the tile starting at global row `cur` (chunk [c0, c1)).
-__device__ void locate_tile(const MixArgs& a, int cur, int c0, int c1, TileInfo* ti_out, int* sRow) {
-  int base = 0, tj = 0;
-  for (;; ++tj) {
-    int tot = a.rowoff[(size_t)tj * (a.N + 1) + a.N];
-    if (cur < base + tot || tj == a.ntypes - 1) break;
-    base += tot;
+// Walk state of one CTA over the concatenated streams (held uniformly by warp 0).
+struct Walk {
+  int tj, base, hint;  // current stream, its first row in concatenated coordinates, atom at or before the tile
+};
+
+// Per-CTA tables: tot[tj] rows of stream tj; tiend[tj * nt + ti] end row of centre type ti in stream tj.
+__device__ void walk_tables(const MixArgs& a, int* tot, int* tiend) {
+  if (threadIdx.x == 0) {
+    for (int tj = 0; tj < a.ntypes; ++tj) {
+      const int* ro = a.rowoff + (size_t)tj * (a.N + 1);
+      tot[tj] = ro[a.N];
+      for (int ti = 0; ti < a.ntypes; ++ti) tiend[tj * a.ntypes + ti] = ro[a.type_off[ti + 1]];
+    }
   }
+}
+
+// Warp 0 locates the tile starting at global row `cur` of chunk [c0, c1): one coalesced
+// load of 32 row offsets from the hint atom finds the first atom; a binary search runs
+// only when a CTA enters a stream.
+__device__ void locate_tile(const MixArgs& a, int cur, int c0, int c1, Walk& wk, const int* tot, const int* tiend,
+                            TileInfo* ti_out, int* sRow) {
+  const int lane = threadIdx.x & 31;
+  while (wk.tj < a.ntypes - 1 && cur >= wk.base + tot[wk.tj]) {
+    wk.base += tot[wk.tj];
+    wk.tj += 1;
+    wk.hint = -1;
+  }
+  const int tj = wk.tj;
   const int* ro = a.rowoff + (size_t)tj * (a.N + 1);
-  const int p = cur - base;
-  int lo = 0, hi = a.N - 1;  // largest atom i with ro[i] <= p
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (ro[mid] <= p) lo = mid; else hi = mid - 1;
+  const int p = cur - wk.base;
+  int a0 = -1;
+  if (wk.hint >= 0) {
+    const int v = ro[min(wk.hint + lane, a.N)];
+    const unsigned m = __ballot_sync(0xffffffffu, v <= p);  // a prefix of the lanes (offsets ascend)
+    if (m != 0xffffffffu && m != 0u) a0 = wk.hint + __popc(m) - 1;
   }
-  const int a0 = lo;
-  const int ti = a.itype[a0];
-  int end = min(c1 - base, ro[a.N]);
-  end = min(end, ro[a.type_off[ti + 1]]);
-  end = min(end, ro[min(a0 + kMaxAtoms, a.N)]);
+  if (a0 < 0) {  // largest atom i with ro[i] <= p
+    int lo = 0, hi = a.N - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (ro[mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    a0 = lo;
+  }
+  int ti = 0;
+  while (ti < a.ntypes - 1 && p >= tiend[tj * a.ntypes + ti]) ++ti;
+  const int rk = ro[min(a0 + (lane < kMaxAtoms + 1 ? lane : 0), a.N)];
+  if (lane <= kMaxAtoms) sRow[lane] = rk;
+  const int r8 = __shfl_sync(0xffffffffu, rk, kMaxAtoms);
+  int end = min(c1 - wk.base, tot[tj]);
+  end = min(end, tiend[tj * a.ntypes + ti]);
+  end = min(end, r8);
   end = min(end, p + kRows);
-  TileInfo t;
-  t.tj = tj; t.ti = ti; t.p = p; t.nrows = end - p; t.a0 = a0; t.cs = c0 - base; t.ce = c1 - base;
-  *ti_out = t;
-  for (int k = 0; k <= kMaxAtoms; ++k) sRow[k] = ro[min(a0 + k, a.N)];
+  if (lane == 0) {
+    TileInfo t;
+    t.tj = tj; t.ti = ti; t.p = p; t.nrows = end - p; t.a0 = a0; t.cs = c0 - wk.base; t.ce = c1 - wk.base;
+    *ti_out = t;
+  }
+  // the last atom of this tile is at or before the first atom of the next one
+  int last = a0;
+#pragma unroll
+  for (int k = 1; k < kMaxAtoms; ++k) last += (__shfl_sync(0xffffffffu, rk, k) <= end - 1) ? 1 : 0;
+  wk.hint = last;
 }
 
 // Embedding weights of pair (ti, tj) into the MMA operand blocks and small fp32 arrays.
@@ -256,20 +296,22 @@ __device__ __forceinline__ void operand_barrier() {
 
 // ------------------------------------------------------------------ forward
 template <bool F16>
-__global__ void __launch_bounds__(kRows, 2) k_mix_embed_fwd(MixArgs a) {
+__global__ void __launch_bounds__(kRows, 4) k_mix_embed_fwd(MixArgs a) {
   extern __shared__ unsigned char sraw[];
   unsigned char* sm = align1024(sraw);
   unsigned char* sA = sm;                          // 16 KB operand block (h1, then h2)
-  float* sG = reinterpret_cast<float*>(sm);        // [128][100] fp32, aliases sA after MMA 3
-  unsigned char* sB2 = sm + 52224;                 // 8 KB
+  float* sG = reinterpret_cast<float*>(sm);        // [128][kGS0] fp32 staging, aliases sA after MMA 3
+  unsigned char* sB2 = sm + kGStage;               // 8 KB
   unsigned char* sB3 = sB2 + 8192;                 // 14 KB
   float4* sR = reinterpret_cast<float4*>(sB3 + 14336);  // [128]
   float* sTacc = reinterpret_cast<float*>(sR + kRows);  // [kMaxAtoms][400]
   float* small = sTacc + kMaxAtoms * 400;               // 200
   int* sRow = reinterpret_cast<int*>(small + 200);      // kMaxAtoms + 1
+  unsigned char* sLA = reinterpret_cast<unsigned char*>(sRow + kMaxAtoms + 1);  // [128] local atom of each row
   __shared__ uint64_t bar;
   __shared__ uint32_t tslot;
   __shared__ TileInfo sti;
+  __shared__ int s_tot[kMaxTypes], s_tiend[kMaxTypes * kMaxTypes];
   const int t = threadIdx.x, w = t >> 5;
 
   int total = 0;
@@ -278,7 +320,7 @@ __global__ void __launch_bounds__(kRows, 2) k_mix_embed_fwd(MixArgs a) {
   const int c0 = min(total, blockIdx.x * per), c1 = min(total, c0 + per);
 
   if (t == 0) { tc::mbar_init(&bar, 1); tc::mbar_fence_init(); }
-  if (w == 0) { tc::tmem_alloc(&tslot, 256); tc::tmem_relinquish(); }
+  if (w == 0) { tc::tmem_alloc(&tslot, kTmemCols); tc::tmem_relinquish(); }
   for (int q = t; q < kMaxAtoms * 400; q += kRows) sTacc[q] = 0.f;
   tc::tc_fence_before();
   __syncthreads();
@@ -288,10 +330,13 @@ __global__ void __launch_bounds__(kRows, 2) k_mix_embed_fwd(MixArgs a) {
   uint32_t phase = 0;
   bool ok = true;
   int pair = -1;
+  walk_tables(a, s_tot, s_tiend);
+  __syncthreads();
+  Walk wk{0, 0, -1};
   long long carry = -1;  // (tj, atom) whose partial T sits in slot 0
 
   for (int cur = c0; cur < c1 && ok;) {
-    if (t == 0) locate_tile(a, cur, c0, c1, &sti, sRow);
+    if (w == 0) locate_tile(a, cur, c0, c1, wk, s_tot, s_tiend, &sti, sRow);
     __syncthreads();
     const TileInfo ti = sti;
     const int np = ti.ti * a.ntypes + ti.tj;
@@ -302,7 +347,6 @@ __global__ void __launch_bounds__(kRows, 2) k_mix_embed_fwd(MixArgs a) {
     const long long key0 = (long long)ti.tj * a.N + ti.a0;
     if (carry != key0)
       for (int q = t; q < 400; q += kRows) sTacc[q] = 0.f;
-    __syncthreads();
 
     // environment row and layer 1
     float h1[kN1], h2[kN2];
@@ -315,6 +359,7 @@ __global__ void __launch_bounds__(kRows, 2) k_mix_embed_fwd(MixArgs a) {
       f.la = 0;
     }
     sR[t] = make_float4(f.R[0], f.R[1], f.R[2], f.R[3]);
+    sLA[t] = (unsigned char)f.la;
     layer1<F16>(small, f.R[0], h1, sA, t);
     operand_barrier();
     if (t == 0) {
@@ -324,72 +369,81 @@ __global__ void __launch_bounds__(kRows, 2) k_mix_embed_fwd(MixArgs a) {
     mma_sync_wait(&bar, phase, a.err, ok);
     layer2_epi<F16>(tl, small, h1, h2, sA, t);
     operand_barrier();
+    // layer 3 reuses the TMEM columns of layer 2 (already read)
     if (t == 0) {
-      tc::mma_kblock(tmem + 64, tc::smem_u32(sA), tc::smem_u32(sB3), tc::idesc_f16(128, 112, F16), false, 4);
+      tc::mma_kblock(tmem, tc::smem_u32(sA), tc::smem_u32(sB3), tc::idesc_f16(128, 112, F16), false, 4);
       tc::mma_commit(&bar);
     }
     mma_sync_wait(&bar, phase, a.err, ok);
-    // layer-3 epilogue: G = [h2, h2] + tanh(z3 + b3) into sG (fp32)
+    // layer-3 epilogue, G = [h2, h2] + tanh(z3 + b3) staged in fp32, and the T partial
+    // sums, in four feature phases of 32 columns (the last one holds columns 96..99)
 #pragma unroll
-    for (int c = 0; c < 7; ++c) {
-      float z[16];
-      tc::tmem_ld16(tl + 64 + 16 * c, z);
-      tc::tmem_wait_ld();
-      if (c * 16 < kN3) {
-        float g[16];
+    for (int ph = 0; ph < 4; ++ph) {
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int q = 16 * c + u;
-          g[u] = (q < kN3) ? h2[q % kN2] + tc::tanh_fast(z[u] + small[100 + (q < kN3 ? q : 0)]) : 0.f;
+      for (int c = 2 * ph; c < (ph < 3 ? 2 * ph + 2 : 7); ++c) {
+        float z[16];
+        tc::tmem_ld16(tl + 16 * c, z);
+        tc::tmem_wait_ld();
+        if (16 * c < kN3) {
+          float g[16];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int q = 16 * c + u;
+            g[u] = (q < kN3) ? h2[q % kN2] + tc::tanh_fast(z[u] + small[100 + (q < kN3 ? q : 0)]) : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 16; u += 4)
+            if (16 * c + u < kN3)
+              *reinterpret_cast<float4*>(&sG[t * kGS + 16 * c + u - 32 * ph]) =
+                  make_float4(g[u], g[u + 1], g[u + 2], g[u + 3]);
         }
-#pragma unroll
-        for (int u = 0; u < 16; u += 4)
-          if (16 * c + u < kN3)
-            *reinterpret_cast<float4*>(&sG[t * kGS + 16 * c + u]) = make_float4(g[u], g[u + 1], g[u + 2], g[u + 3]);
       }
-    }
-    __syncthreads();
-    // T partial sums: thread (g, q) handles rows g, g+5, ... and columns 4q..4q+3
-    if (t < 125) {
-      const int g = t / 25, q = t - g * 25;
-      float acc[4][4];
+      __syncthreads();
+      // thread (g, q): column quad q of this phase, a contiguous block of rows
+      const int nq = ph < 3 ? 8 : 1;
+      const int ng = 16;
+      const int gi = t / nq, q = t - gi * nq;
+      if (gi < ng) {
+        const int r_beg = (ti.nrows * gi) / ng, r_end = (ti.nrows * (gi + 1)) / ng;
+        float acc[4][4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
+        for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[c][u] = 0.f;
-      int cur_la = -1;
-      for (int r = g; r < ti.nrows; r += 5) {
-        const int la = local_atom(sRow, ti.p + r);
-        if (la != cur_la) {
-          if (cur_la >= 0) {
+          for (int u = 0; u < 4; ++u) acc[c][u] = 0.f;
+        int cur_la = r_beg < r_end ? sLA[r_beg] : 0;
+        const int col0 = 32 * ph + 4 * q;
+        const int stride = kGS;
+        for (int r = r_beg; r < r_end; ++r) {
+          const int la = sLA[r];
+          if (la != cur_la) {
 #pragma unroll
             for (int c = 0; c < 4; ++c)
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
-                atomicAdd(&sTacc[cur_la * 400 + c * kN3 + 4 * q + u], acc[c][u]);
+                atomicAdd(&sTacc[cur_la * 400 + c * kN3 + col0 + u], acc[c][u]);
                 acc[c][u] = 0.f;
               }
+            cur_la = la;
           }
-          cur_la = la;
+          const float4 R = sR[r];
+          const float4 G = *reinterpret_cast<const float4*>(&sG[r * stride + 4 * q]);
+          const float Rv[4] = {R.x, R.y, R.z, R.w}, Gv[4] = {G.x, G.y, G.z, G.w};
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[c][u] = fmaf(Rv[c], Gv[u], acc[c][u]);
         }
-        const float4 R = sR[r];
-        const float4 G = *reinterpret_cast<const float4*>(&sG[r * kGS + 4 * q]);
-        const float Rv[4] = {R.x, R.y, R.z, R.w}, Gv[4] = {G.x, G.y, G.z, G.w};
+        if (r_beg < r_end) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
+          for (int c = 0; c < 4; ++c)
 #pragma unroll
-          for (int u = 0; u < 4; ++u) acc[c][u] = fmaf(Rv[c], Gv[u], acc[c][u]);
+            for (int u = 0; u < 4; ++u) atomicAdd(&sTacc[cur_la * 400 + c * kN3 + col0 + u], acc[c][u]);
+        }
       }
-      if (cur_la >= 0) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int u = 0; u < 4; ++u) atomicAdd(&sTacc[cur_la * 400 + c * kN3 + 4 * q + u], acc[c][u]);
-      }
+      __syncthreads();
     }
-    __syncthreads();
     // write complete atoms; carry the open one into slot 0
-    const int last_la = local_atom(sRow, ti.p + ti.nrows - 1);
+    const int last_la = sLA[ti.nrows - 1];
     const bool last_done = (ti.p + ti.nrows == sRow[last_la + 1]);
     const int n_out = last_done ? last_la + 1 : last_la;
     for (int la = 0; la < n_out; ++la) {
@@ -408,18 +462,19 @@ __global__ void __launch_bounds__(kRows, 2) k_mix_embed_fwd(MixArgs a) {
     } else {
       carry = -1;
     }
-    for (int q = t; q < (kMaxAtoms - 1) * 400; q += kRows) sTacc[400 + q] = 0.f;
     __syncthreads();
+    for (int q = t; q < (kMaxAtoms - 1) * 400; q += kRows) sTacc[400 + q] = 0.f;
     cur += ti.nrows;
   }
   // an atom left open at the chunk end continues in the next CTA
+  __syncthreads();
   if (carry >= 0) {
     float* dst = a.Tseg + (size_t)carry * 400;
     for (int q = t; q < 400; q += kRows) atomicAdd(&dst[q], sTacc[q]);
   }
   tc::tc_fence_before();
   __syncthreads();
-  if (w == 0) tc::tmem_dealloc(tmem, 256);
+  if (w == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
 // ------------------------------------------------------------------ backward
@@ -438,6 +493,7 @@ __global__ void __launch_bounds__(kRows, 2) k_mix_embed_bwd(MixArgs a) {
   __shared__ uint64_t bar;
   __shared__ uint32_t tslot;
   __shared__ TileInfo sti;
+  __shared__ int s_tot[kMaxTypes], s_tiend[kMaxTypes * kMaxTypes];
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
 
   int total = 0;
@@ -446,7 +502,7 @@ __global__ void __launch_bounds__(kRows, 2) k_mix_embed_bwd(MixArgs a) {
   const int c0 = min(total, blockIdx.x * per), c1 = min(total, c0 + per);
 
   if (t == 0) { tc::mbar_init(&bar, 1); tc::mbar_fence_init(); }
-  if (w == 0) { tc::tmem_alloc(&tslot, 256); tc::tmem_relinquish(); }
+  if (w == 0) { tc::tmem_alloc(&tslot, kTmemCols); tc::tmem_relinquish(); }
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
@@ -455,9 +511,12 @@ __global__ void __launch_bounds__(kRows, 2) k_mix_embed_bwd(MixArgs a) {
   uint32_t phase = 0;
   bool ok = true;
   int pair = -1;
+  walk_tables(a, s_tot, s_tiend);
+  __syncthreads();
+  Walk wk{0, 0, -1};
 
   for (int cur = c0; cur < c1 && ok;) {
-    if (t == 0) locate_tile(a, cur, c0, c1, &sti, sRow);
+    if (w == 0) locate_tile(a, cur, c0, c1, wk, s_tot, s_tiend, &sti, sRow);
     __syncthreads();
     const TileInfo ti = sti;
     const int np = ti.ti * a.ntypes + ti.tj;
@@ -490,7 +549,7 @@ __global__ void __launch_bounds__(kRows, 2) k_mix_embed_bwd(MixArgs a) {
     layer2_epi<F16>(tl, small, h1, h2, sA, t);
     operand_barrier();
     if (t == 0) {
-      tc::mma_kblock(tmem + 64, tc::smem_u32(sA), tc::smem_u32(sB3), tc::idesc_f16(128, 112, F16), false, 4);
+      tc::mma_kblock(tmem, tc::smem_u32(sA), tc::smem_u32(sB3), tc::idesc_f16(128, 112, F16), false, 4);
       tc::mma_commit(&bar);
     }
     mma_sync_wait(&bar, phase, a.err, ok);
@@ -503,7 +562,7 @@ __global__ void __launch_bounds__(kRows, 2) k_mix_embed_bwd(MixArgs a) {
 #pragma unroll
     for (int c = 0; c < 7; ++c) {
       float z[16];
-      tc::tmem_ld16(tl + 64 + 16 * c, z);
+      tc::tmem_ld16(tl + 16 * c, z);
       tc::tmem_wait_ld();
       float dz[16];
 #pragma unroll
@@ -644,7 +703,7 @@ __global__ void __launch_bounds__(kRows, 2) k_mix_embed_bwd(MixArgs a) {
   }
   tc::tc_fence_before();
   __syncthreads();
-  if (w == 0) tc::tmem_dealloc(tmem, 256);
+  if (w == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
 // ------------------------------------------------------------------ small kernels
@@ -699,8 +758,9 @@ __global__ void k_scan_fix(int N, int nblk, int* rowoff, const int* blk) {
 
 // T = sum over neighbour types of the partial sums, scaled by 1/S; D = T^T T[:, :16]
 // (fp32 copy for the fitting net).
+template <bool F16>
 __global__ void k_mix_descriptor(int N, int ntypes, float invS, const float* __restrict__ Tseg, float* Tm,
-                                 float* Dm) {
+                                 unsigned short* Dm) {
   __shared__ float sT[400];
   for (int i = blockIdx.x; i < N; i += gridDim.x) {
     for (int q = threadIdx.x; q < 400; q += blockDim.x) {
@@ -720,9 +780,12 @@ __global__ void k_mix_descriptor(int N, int ntypes, float invS, const float* __r
         for (int c = 0; c < 4; ++c) v = fmaf(sT[c * kN3 + q], sT[c * kN3 + b], v);
         out[b] = v;
       }
-      float4* dst = reinterpret_cast<float4*>(Dm + (size_t)i * kKD + q * kM2);
+      uint32_t pk[8];
 #pragma unroll
-      for (int b = 0; b < kM2; b += 4) dst[b / 4] = make_float4(out[b], out[b + 1], out[b + 2], out[b + 3]);
+      for (int h = 0; h < 8; ++h) pk[h] = tc::pack2<F16>(out[2 * h], out[2 * h + 1]);
+      uint4* dst = reinterpret_cast<uint4*>(Dm + (size_t)i * kKD + q * kM2);
+      dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
     }
     __syncthreads();
   }
@@ -766,7 +829,7 @@ MixArgs make_mix_args(Model* m, int N) {
   return a;
 }
 
-constexpr size_t kFwdSmem = 52224 + 8192 + 14336 + kRows * 16 + kMaxAtoms * 400 * 4 + 200 * 4 + 64 + 1024;
+constexpr size_t kFwdSmem = kGStage + 8192 + 14336 + kRows * 16 + kMaxAtoms * 400 * 4 + 200 * 4 + 64 + kRows + 1024;
 constexpr size_t kBwdSmem = 32768 + 8192 + 14336 + 16384 + 4096 + kMaxAtoms * kN3 * 16 + 200 * 4 + 64 + 1024;
 
 }  // namespace
@@ -781,12 +844,15 @@ dp_status launch_mix_descriptor(Model* m, int N) {
   const void* fn = f16 ? reinterpret_cast<const void*>(k_mix_embed_fwd<true>)
                        : reinterpret_cast<const void*>(k_mix_embed_fwd<false>);
   DP_CUDA_TRY(m, ensure_smem(fn, kFwdSmem));
-  const int grid = num_sms() * blocks_per_sm(fn, kRows, kFwdSmem);
+  const int grid = num_sms() * blocks_per_sm(fn, kRows, kFwdSmem, kTmemCols);
   if (f16) k_mix_embed_fwd<true><<<grid, kRows, kFwdSmem, m->stream>>>(a);
   else k_mix_embed_fwd<false><<<grid, kRows, kFwdSmem, m->stream>>>(a);
-  k_mix_descriptor<<<std::min(N, 4 * num_sms()), 128, 0, m->stream>>>(N, m->ntypes, 1.f / (float)m->S, m->Tseg,
-                                                                       static_cast<float*>(m->Tm),
-                                                                       static_cast<float*>(m->Dm));
+  if (f16)
+    k_mix_descriptor<true><<<std::min(N, 4 * num_sms()), 128, 0, m->stream>>>(
+        N, m->ntypes, 1.f / (float)m->S, m->Tseg, static_cast<float*>(m->Tm), static_cast<unsigned short*>(m->Dm));
+  else
+    k_mix_descriptor<false><<<std::min(N, 4 * num_sms()), 128, 0, m->stream>>>(
+        N, m->ntypes, 1.f / (float)m->S, m->Tseg, static_cast<float*>(m->Tm), static_cast<unsigned short*>(m->Dm));
   m->launches += 4;
   DP_LAUNCH_CHECK(m);
   return DP_OK;
@@ -802,7 +868,7 @@ dp_status launch_mix_embed_backward(Model* m, int N) {
   const void* fn = f16 ? reinterpret_cast<const void*>(k_mix_embed_bwd<true>)
                        : reinterpret_cast<const void*>(k_mix_embed_bwd<false>);
   DP_CUDA_TRY(m, ensure_smem(fn, kBwdSmem));
-  const int grid = num_sms() * blocks_per_sm(fn, kRows, kBwdSmem);
+  const int grid = num_sms() * blocks_per_sm(fn, kRows, kBwdSmem, kTmemCols);
   if (f16) k_mix_embed_bwd<true><<<grid, kRows, kBwdSmem, m->stream>>>(a);
   else k_mix_embed_bwd<false><<<grid, kRows, kBwdSmem, m->stream>>>(a);
   m->launches += 2;

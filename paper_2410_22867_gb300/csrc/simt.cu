@@ -572,6 +572,7 @@ dp_status launch_descriptor(Model* m, int N) {
   return m->prec == DP_FP64 ? run_descriptor<double>(m, N) : run_descriptor<float>(m, N);
 }
 dp_status launch_fitting(Model* m, int N) {
+  if (is_mixed(m)) return launch_mix_fitting(m, N);
   return m->prec == DP_FP64 ? run_fitting<double>(m, N) : run_fitting<float>(m, N);
 }
 dp_status launch_embed_backward(Model* m, int N) {

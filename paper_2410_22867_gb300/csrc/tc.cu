@@ -104,7 +104,7 @@ dp_status run_selftest(float* dout, int* derr, float* host) {
 
 }  // namespace
 
-dp_status launch_tc_setup(Model*) { return DP_OK; }
+dp_status launch_tc_setup(Model* m) { return mix_fit_setup(m); }
 
 }  // namespace dpg
 
