@@ -2,17 +2,21 @@
 // tensor cores (tcgen05 / TMEM), Section III-B3's mixed precision mapped to
 // Blackwell: the 25->50 and 50->100 layers of the embedding net (and their
 // backward) are MMAs with 16-bit operands and FP32 accumulation in TMEM; the
-// environment matrix, the 1->25 layer, all tanh (on the SFU) and residuals, the
-// reduction T = (1/S) R_hat^T G and the descriptor D stay FP32 on the CUDA cores.
+// environment matrix, the 1->25 layer, all tanh (on the SFU) and residuals stay
+// FP32 on the CUDA cores.  The reduction T = R_hat^T G (Eq. 4) is a third MMA
+// per tile with fp16 operands: G^T [feature][row] against a block-sparse R_hat^T
+// whose column (atom slot, c) is non-zero only on that atom's rows, so one
+// 128x32x128 product yields the partial T of every atom in the tile.
 //
 // Work decomposition.  For each neighbour type tj the real neighbours of all
 // atoms form one "row stream" (atoms in internal, type-sorted order; rows of an
 // atom contiguous).  The concatenated streams are split into one contiguous chunk
 // per CTA, walked in tiles of at most 128 rows (one row per thread and TMEM lane)
-// that never cross a centre-type boundary and hold at most kMaxAtoms atoms.  T of
-// an atom is accumulated in shared memory across consecutive tiles and written
-// once; only atoms split between two CTAs use global atomics.  Activations of the
-// embedding net are recomputed in the backward instead of being stored.
+// that never cross a centre-type boundary and hold at most kMaxAtoms atoms.  The
+// partial T of an atom that continues into the next tile stays in registers
+// (thread = feature) and is written once the atom is complete; only atoms split
+// between two CTAs use global atomics.  Activations of the embedding net are
+// recomputed in the backward instead of being stored.
 #include "tc_common.cuh"
 
 namespace dpg {
@@ -20,8 +24,6 @@ namespace {
 
 constexpr int kRows = 128;     // rows per tile = threads per CTA = TMEM lanes
 constexpr int kMaxAtoms = 6;   // atom segments per tile
-constexpr int kGS = 36;        // fp32 G staging row stride: 32 columns + 4 (9 x 16 B: conflict-free float4)
-constexpr int kGStage = 18432; // 128 x 36 x 4 bytes (>= the 16 KB operand block it aliases)
 constexpr uint32_t kTmemCols = 128;  // per CTA: D2/D3 share columns 0..111
 
 struct MixArgs {
@@ -296,18 +298,16 @@ __device__ __forceinline__ void operand_barrier() {
 
 // ------------------------------------------------------------------ forward
 template <bool F16>
-__global__ void __launch_bounds__(kRows, 4) k_mix_embed_fwd(MixArgs a) {
+__global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
   extern __shared__ unsigned char sraw[];
   unsigned char* sm = align1024(sraw);
   unsigned char* sA = sm;                          // 16 KB operand block (h1, then h2)
-  float* sG = reinterpret_cast<float*>(sm);        // [128][kGS0] fp32 staging, aliases sA after MMA 3
-  unsigned char* sB2 = sm + kGStage;               // 8 KB
+  unsigned char* sGt = sm;                         // 32 KB: G^T [feature][row] fp16, aliases sA after MMA 2
+  unsigned char* sRs = sm + 32768;                 // 8 KB: block-sparse R_hat^T [(atom, c)][row] fp16
+  unsigned char* sB2 = sRs + 8192;                 // 8 KB
   unsigned char* sB3 = sB2 + 8192;                 // 14 KB
-  float4* sR = reinterpret_cast<float4*>(sB3 + 14336);  // [128]
-  float* sTacc = reinterpret_cast<float*>(sR + kRows);  // [kMaxAtoms][400]
-  float* small = sTacc + kMaxAtoms * 400;               // 200
-  int* sRow = reinterpret_cast<int*>(small + 200);      // kMaxAtoms + 1
-  unsigned char* sLA = reinterpret_cast<unsigned char*>(sRow + kMaxAtoms + 1);  // [128] local atom of each row
+  float* small = reinterpret_cast<float*>(sB3 + 14336);  // 200
+  int* sRow = reinterpret_cast<int*>(small + 200);       // kMaxAtoms + 1
   __shared__ uint64_t bar;
   __shared__ uint32_t tslot;
   __shared__ TileInfo sti;
@@ -321,7 +321,6 @@ __global__ void __launch_bounds__(kRows, 4) k_mix_embed_fwd(MixArgs a) {
 
   if (t == 0) { tc::mbar_init(&bar, 1); tc::mbar_fence_init(); }
   if (w == 0) { tc::tmem_alloc(&tslot, kTmemCols); tc::tmem_relinquish(); }
-  for (int q = t; q < kMaxAtoms * 400; q += kRows) sTacc[q] = 0.f;
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
@@ -333,20 +332,35 @@ __global__ void __launch_bounds__(kRows, 4) k_mix_embed_fwd(MixArgs a) {
   walk_tables(a, s_tot, s_tiend);
   __syncthreads();
   Walk wk{0, 0, -1};
+  // T partial sums of the tile's atom slots for feature t (thread t = TMEM lane t of
+  // the T product); slot 0 carries an atom that continues into the next tile.
+  float tacc[kMaxAtoms][4];
+#pragma unroll
+  for (int s = 0; s < kMaxAtoms; ++s)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tacc[s][c] = 0.f;
   long long carry = -1;  // (tj, atom) whose partial T sits in slot 0
 
   for (int cur = c0; cur < c1 && ok;) {
     if (w == 0) locate_tile(a, cur, c0, c1, wk, s_tot, s_tiend, &sti, sRow);
+    // the R_hat^T operand starts from zero (rows of other atoms stay zero)
+    {
+      uint4* z = reinterpret_cast<uint4*>(sRs);
+      for (int q = t; q < 8192 / 16; q += kRows) z[q] = make_uint4(0, 0, 0, 0);
+    }
     __syncthreads();
     const TileInfo ti = sti;
     const int np = ti.ti * a.ntypes + ti.tj;
     if (np != pair) {
       load_fwd_weights<F16>(a.w + (size_t)np * kEmbParams, sB2, sB3, small);
       pair = np;
+      __syncthreads();  // layer 1 reads biases written by other threads
     }
     const long long key0 = (long long)ti.tj * a.N + ti.a0;
-    if (carry != key0)
-      for (int q = t; q < 400; q += kRows) sTacc[q] = 0.f;
+    if (carry != key0) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) tacc[0][c] = 0.f;
+    }
 
     // environment row and layer 1
     float h1[kN1], h2[kN2];
@@ -358,8 +372,6 @@ __global__ void __launch_bounds__(kRows, 4) k_mix_embed_fwd(MixArgs a) {
       f.R[0] = f.R[1] = f.R[2] = f.R[3] = 0.f;
       f.la = 0;
     }
-    sR[t] = make_float4(f.R[0], f.R[1], f.R[2], f.R[3]);
-    sLA[t] = (unsigned char)f.la;
     layer1<F16>(small, f.R[0], h1, sA, t);
     operand_barrier();
     if (t == 0) {
@@ -375,102 +387,96 @@ __global__ void __launch_bounds__(kRows, 4) k_mix_embed_fwd(MixArgs a) {
       tc::mma_commit(&bar);
     }
     mma_sync_wait(&bar, phase, a.err, ok);
-    // layer-3 epilogue, G = [h2, h2] + tanh(z3 + b3) staged in fp32, and the T partial
-    // sums, in four feature phases of 32 columns (the last one holds columns 96..99)
+    // layer-3 epilogue: G = [h2, h2] + tanh(z3 + b3); G^T and this row's R_hat column go to
+    // the fp16 operands of the T product T_slot[c][a] = sum_rows R_hat[row][c] G[row][a]
+    {
+      const uint32_t kb = (uint32_t)(t >> 6) * 16384u, kr = (uint32_t)(t & 63);
+      unsigned char* gcol = sGt + kb + (kr & 7) * 2;
 #pragma unroll
-    for (int ph = 0; ph < 4; ++ph) {
-#pragma unroll
-      for (int c = 2 * ph; c < (ph < 3 ? 2 * ph + 2 : 7); ++c) {
+      for (int c = 0; c < 7; ++c) {
         float z[16];
         tc::tmem_ld16(tl + 16 * c, z);
         tc::tmem_wait_ld();
-        if (16 * c < kN3) {
-          float g[16];
 #pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            const int q = 16 * c + u;
-            g[u] = (q < kN3) ? h2[q % kN2] + tc::tanh_fast(z[u] + small[100 + (q < kN3 ? q : 0)]) : 0.f;
+        for (int u = 0; u < 16; ++u) {
+          const int q = 16 * c + u;
+          if (q < kN3) {
+            const float g = h2[q % kN2] + tc::tanh_fast(z[u] + small[100 + q]);
+            *reinterpret_cast<__half*>(gcol + q * 128 + (((kr >> 3) ^ (q & 7)) << 4)) = __float2half_rn(g);
           }
-#pragma unroll
-          for (int u = 0; u < 16; u += 4)
-            if (16 * c + u < kN3)
-              *reinterpret_cast<float4*>(&sG[t * kGS + 16 * c + u - 32 * ph]) =
-                  make_float4(g[u], g[u + 1], g[u + 2], g[u + 3]);
         }
       }
-      __syncthreads();
-      // thread (g, q): column quad q of this phase, a contiguous block of rows
-      const int nq = ph < 3 ? 8 : 1;
-      const int ng = 16;
-      const int gi = t / nq, q = t - gi * nq;
-      if (gi < ng) {
-        const int r_beg = (ti.nrows * gi) / ng, r_end = (ti.nrows * (gi + 1)) / ng;
-        float acc[4][4];
+      if (valid) {
+        unsigned char* rcol = sRs + (uint32_t)(t >> 6) * 4096u + (kr & 7) * 2;
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int u = 0; u < 4; ++u) acc[c][u] = 0.f;
-        int cur_la = r_beg < r_end ? sLA[r_beg] : 0;
-        const int col0 = 32 * ph + 4 * q;
-        const int stride = kGS;
-        for (int r = r_beg; r < r_end; ++r) {
-          const int la = sLA[r];
-          if (la != cur_la) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                atomicAdd(&sTacc[cur_la * 400 + c * kN3 + col0 + u], acc[c][u]);
-                acc[c][u] = 0.f;
-              }
-            cur_la = la;
-          }
-          const float4 R = sR[r];
-          const float4 G = *reinterpret_cast<const float4*>(&sG[r * stride + 4 * q]);
-          const float Rv[4] = {R.x, R.y, R.z, R.w}, Gv[4] = {G.x, G.y, G.z, G.w};
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int u = 0; u < 4; ++u) acc[c][u] = fmaf(Rv[c], Gv[u], acc[c][u]);
-        }
-        if (r_beg < r_end) {
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int u = 0; u < 4; ++u) atomicAdd(&sTacc[cur_la * 400 + c * kN3 + col0 + u], acc[c][u]);
+        for (int c = 0; c < 4; ++c) {
+          const int n = f.la * 4 + c;
+          *reinterpret_cast<__half*>(rcol + n * 128 + (((kr >> 3) ^ (n & 7)) << 4)) = __float2half_rn(f.R[c]);
         }
       }
-      __syncthreads();
     }
-    // write complete atoms; carry the open one into slot 0
-    const int last_la = sLA[ti.nrows - 1];
+    operand_barrier();
+    // T product on the tensor core: D[feature][(slot, c)] over the 128 rows (two K blocks)
+    if (t == 0) {
+      const uint32_t id = tc::idesc_f16(128, 32, true);
+      tc::mma_kblock(tmem, tc::smem_u32(sGt), tc::smem_u32(sRs), id, false, 4);
+      tc::mma_kblock(tmem, tc::smem_u32(sGt + 16384), tc::smem_u32(sRs + 4096), id, true, 4);
+      tc::mma_commit(&bar);
+    }
+    mma_sync_wait(&bar, phase, a.err, ok);
+    {
+      float v[32];
+      tc::tmem_ld16(tl, v);
+      tc::tmem_ld16(tl + 16, v + 16);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int s = 0; s < kMaxAtoms; ++s)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tacc[s][c] += v[4 * s + c];
+    }
+    // write complete atoms (feature t of each); carry the open one into slot 0
+    const int last_la = local_atom(sRow, ti.p + ti.nrows - 1);
     const bool last_done = (ti.p + ti.nrows == sRow[last_la + 1]);
     const int n_out = last_done ? last_la + 1 : last_la;
-    for (int la = 0; la < n_out; ++la) {
-      const bool shared = (sRow[la] < ti.cs) || (sRow[la + 1] > ti.ce);
-      float* dst = a.Tseg + ((size_t)ti.tj * a.N + ti.a0 + la) * 400;
-      for (int q = t; q < 400; q += kRows) {
-        const float v = sTacc[la * 400 + q];
-        if (shared) atomicAdd(&dst[q], v); else dst[q] = v;
+    if (t < kN3) {
+#pragma unroll
+      for (int s = 0; s < kMaxAtoms; ++s) {
+        if (s < n_out) {
+          const bool shared = (sRow[s] < ti.cs) || (sRow[s + 1] > ti.ce);
+          float* dst = a.Tseg + ((size_t)ti.tj * a.N + ti.a0 + s) * 400 + t;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            if (shared) atomicAdd(dst + c * kN3, tacc[s][c]);
+            else dst[c * kN3] = tacc[s][c];
+          }
+        }
       }
     }
-    __syncthreads();
+    float keep[4] = {0.f, 0.f, 0.f, 0.f};
     if (!last_done) {
-      if (last_la != 0)
-        for (int q = t; q < 400; q += kRows) sTacc[q] = sTacc[last_la * 400 + q];
+#pragma unroll
+      for (int s = 0; s < kMaxAtoms; ++s)
+        if (s == last_la)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) keep[c] = tacc[s][c];
       carry = (long long)ti.tj * a.N + ti.a0 + last_la;
     } else {
       carry = -1;
     }
+#pragma unroll
+    for (int s = 0; s < kMaxAtoms; ++s)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) tacc[s][c] = (s == 0) ? keep[c] : 0.f;
+    tc::tc_fence_before();
     __syncthreads();
-    for (int q = t; q < (kMaxAtoms - 1) * 400; q += kRows) sTacc[400 + q] = 0.f;
+    tc::tc_fence_after();
     cur += ti.nrows;
   }
   // an atom left open at the chunk end continues in the next CTA
-  __syncthreads();
-  if (carry >= 0) {
-    float* dst = a.Tseg + (size_t)carry * 400;
-    for (int q = t; q < 400; q += kRows) atomicAdd(&dst[q], sTacc[q]);
+  if (carry >= 0 && t < kN3) {
+    float* dst = a.Tseg + (size_t)carry * 400 + t;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) atomicAdd(dst + c * kN3, tacc[0][c]);
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -829,7 +835,7 @@ MixArgs make_mix_args(Model* m, int N) {
   return a;
 }
 
-constexpr size_t kFwdSmem = kGStage + 8192 + 14336 + kRows * 16 + kMaxAtoms * 400 * 4 + 200 * 4 + 64 + kRows + 1024;
+constexpr size_t kFwdSmem = 32768 + 8192 + 8192 + 14336 + 200 * 4 + 64 + 1024;
 constexpr size_t kBwdSmem = 32768 + 8192 + 14336 + 16384 + 4096 + kMaxAtoms * kN3 * 16 + 200 * 4 + 64 + 1024;
 
 }  // namespace

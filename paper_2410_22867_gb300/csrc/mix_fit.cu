@@ -67,9 +67,9 @@ struct FitArgs {
 
 // Staging slots: one full/empty mbarrier pair each; `uses` counts completed jobs per slot.
 struct Slots {
-  uint64_t* full;   // [7]
-  uint64_t* empty;  // [7]
-  uint32_t uses[7];
+  uint64_t* full;   // [8]: L1 0..3, B1 0..5, split hi 6, split lo 7
+  uint64_t* empty;  // [8]
+  uint32_t uses[8];
 };
 
 __device__ __forceinline__ unsigned char* align1k(unsigned char* p) {
@@ -143,30 +143,37 @@ struct Issuer {
   int ty, row0;
   int* err;
   bool* ok;
-  uint32_t split_loads;   // split jobs loaded so far (all tiles)
+  // Every CTA walks the shared weight matrices starting at a different block, so the
+  // SMs do not all request the same L2 lines at the same moment.
+  int rot_l1, rot_s, rot_b1;
+  __device__ int l1_block(int j) const { return (j + rot_l1) % kL1Jobs; }
+  __device__ int split_block(int kb) const { return (kb + rot_s) & 3; }
+  __device__ int b1_chunk(int n) const { return (n + rot_b1) % (kKD / kBChunk); }
 
-  // L1 job j: A (D rows row0.., K block j) + W1T block j into slot j % 4
+  // L1 job j: A (D rows row0.., K block l1_block(j)) + the matching W1T block into slot j % 4
   __device__ void load_l1(int j) {
     const int k = j % kL1Slots;
     slot_acquire(*s, k, s->uses[k], err, *ok);
     unsigned char* a = sm + k * kL1Slot;
+    const int kb = l1_block(j);
     tc::mbar_arrive_expect_tx(&s->full[k], kL1Slot);
-    tc::tma_load_2d(a, &mp->D, &s->full[k], 64 * j, row0);
-    tc::tma_load_2d(a + kBlk, &mp->W1T[ty], &s->full[k], 64 * j, 0);
+    tc::tma_load_2d(a, &mp->D, &s->full[k], 64 * kb, row0);
+    tc::tma_load_2d(a + kBlk, &mp->W1T[ty], &s->full[k], 64 * kb, 0);
   }
-  // B1 job j: W1 rows of chunk j / 4, K block j % 4, into slot j % 6 (inside X_lo + split area)
+  // B1 job j: W1 rows of chunk b1_chunk(j / 4), K block j % 4, into slot j % 6 (X_lo + split area)
   __device__ void load_b1(int j) {
     const int k = j % kB1Slots;
     slot_acquire(*s, k, s->uses[k], err, *ok);
     tc::mbar_arrive_expect_tx(&s->full[k], kB1Slot);
-    tc::tma_load_2d(sm + kXLo + k * kB1Slot, &mp->W1[ty], &s->full[k], 64 * (j & 3), kBChunk * (j >> 2));
+    tc::tma_load_2d(sm + kXLo + k * kB1Slot, &mp->W1[ty], &s->full[k], 64 * (j & 3), kBChunk * b1_chunk(j >> 2));
   }
-  // split job: hi and lo weight blocks of GEMM g, K block kb
-  __device__ void load_split(int g, int kb) {
-    slot_acquire(*s, kSplitSlot, s->uses[kSplitSlot], err, *ok);
-    tc::mbar_arrive_expect_tx(&s->full[kSplitSlot], 2 * kWB);
-    tc::tma_load_2d(sm + kSt, &mp->S[ty][g][0], &s->full[kSplitSlot], 64 * kb, 0);
-    tc::tma_load_2d(sm + kSt + kWB, &mp->S[ty][g][1], &s->full[kSplitSlot], 64 * kb, 0);
+  // split job i of GEMM g: weight half (i & 1: 0 = hi, 1 = lo) of K block split_block(i / 2),
+  // into split slot i & 1 (hi slot at kSt, lo slot at kSt + kWB)
+  __device__ void load_split(int g, int i) {
+    const int k = kSplitSlot + (i & 1);
+    slot_acquire(*s, k, s->uses[k], err, *ok);
+    tc::mbar_arrive_expect_tx(&s->full[k], kWB);
+    tc::tma_load_2d(sm + kSt + (i & 1) * kWB, &mp->S[ty][g][i & 1], &s->full[k], 64 * split_block(i >> 1), 0);
   }
   // wait for the data of the oldest outstanding job in slot k and mark it consumed after the MMAs
   __device__ void consume_begin(int k) {
@@ -184,7 +191,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
   extern __shared__ unsigned char sraw[];
   unsigned char* sm = align1k(sraw);
   float* prm = reinterpret_cast<float*>(sm + kPrm);  // b1, b2, b3, w4 [4][240]
-  __shared__ uint64_t full[7], empty[7], accb[2];
+  __shared__ uint64_t full[8], empty[8], accb[2];
   __shared__ uint32_t tslot;
   __shared__ int s_tiles[kMaxTypes + 1];
   __shared__ float sE[kFR];
@@ -192,7 +199,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
   const int row = t & (kFR - 1), half = t >> 7;  // TMEM lane / atom, column half
 
   if (t == 0) {
-    for (int q = 0; q < 7; ++q) { tc::mbar_init(&full[q], 1); tc::mbar_init(&empty[q], 1); }
+    for (int q = 0; q < 8; ++q) { tc::mbar_init(&full[q], 1); tc::mbar_init(&empty[q], 1); }
     for (int q = 0; q < 2; ++q) tc::mbar_init(&accb[q], 1);
     tc::mbar_fence_init();
     int acc = 0;
@@ -210,7 +217,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
   const uint32_t resid = acc1;
   Slots sl;
   sl.full = full; sl.empty = empty;
-  for (int q = 0; q < 7; ++q) sl.uses[q] = 0;
+  for (int q = 0; q < 8; ++q) sl.uses[q] = 0;
   uint32_t aph[2] = {0, 0};
   bool ok = true;
   int cur_type = -1;
@@ -220,6 +227,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
   const int c_beg = half ? 8 : 0, c_end = half ? 15 : 8;
   Issuer is;
   is.s = &sl; is.sm = sm; is.mp = &maps; is.err = a.err; is.ok = &ok;
+  is.rot_l1 = blockIdx.x % kL1Jobs;
+  is.rot_s = blockIdx.x & 3;
+  is.rot_b1 = blockIdx.x % (kKD / kBChunk);
 
   auto sync_all = [&]() {
     tc::fence_async_smem();
@@ -232,17 +242,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
     aph[r] ^= 1u;
     tc::tc_fence_after();
   };
-  // thread 0: the MMAs of split GEMM g (its first weight block was prefetched)
+  // thread 0: the MMAs of split GEMM g (its first job, the hi block of K block 0, was
+  // prefetched).  Jobs alternate hi / lo halves; after issuing job i the slot of job i - 1
+  // is refilled, so the tensor pipe always has the MMAs of job i queued while it waits.
   auto issue_split = [&](int g) {
-    for (int kb = 0; kb < 4 && ok; ++kb) {
-      if (kb > 0) is.load_split(g, kb);
-      is.consume_begin(kSplitSlot);
-      const uint32_t xh = tc::smem_u32(sm + kXHi + kb * kBlk), xl = tc::smem_u32(sm + kXLo + kb * kBlk);
-      const uint32_t wh = tc::smem_u32(sm + kSt), wl = tc::smem_u32(sm + kSt + kWB);
-      tc::mma_kblock(tmem, xh, wh, id240, kb > 0, 4);
-      tc::mma_kblock(tmem, xh, wl, id240, true, 4);
-      tc::mma_kblock(tmem, xl, wh, id240, true, 4);
-      is.consume_end(kSplitSlot);
+    for (int i = 0; i < 8 && ok; ++i) {
+      const int k = kSplitSlot + (i & 1);
+      is.consume_begin(k);
+      const int kx = is.split_block(i >> 1);
+      const uint32_t xh = tc::smem_u32(sm + kXHi + kx * kBlk), xl = tc::smem_u32(sm + kXLo + kx * kBlk);
+      const uint32_t wv = tc::smem_u32(sm + kSt + (i & 1) * kWB);
+      if ((i & 1) == 0) {  // hi weights: x_hi w_hi + x_lo w_hi
+        tc::mma_kblock(tmem, xh, wv, id240, i > 0, 4);
+        tc::mma_kblock(tmem, xl, wv, id240, true, 4);
+      } else {             // lo weights: x_hi w_lo
+        tc::mma_kblock(tmem, xh, wv, id240, true, 4);
+      }
+      is.consume_end(k);
+      if (i + 1 < 8) is.load_split(g, i + 1);
     }
     tc::mma_commit(&accb[0]);
   };
@@ -275,12 +292,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
     if (t == 0) {
       for (int j = 0; j < kL1Slots - 1; ++j) is.load_l1(j);
       for (int j = 0; j < kL1Jobs && ok; ++j) {
-        if (j + kL1Slots - 1 < kL1Jobs) is.load_l1(j + kL1Slots - 1);
         const int s = j % kL1Slots;
         is.consume_begin(s);
         unsigned char* st = sm + s * kL1Slot;
         tc::mma_kblock(tmem, tc::smem_u32(st), tc::smem_u32(st + kBlk), id240, j > 0, 4);
         is.consume_end(s);
+        // refill the slot of job j - 1 (MMAs of job j stay queued meanwhile)
+        if (j + kL1Slots - 1 < kL1Jobs) is.load_l1(j + kL1Slots - 1);
       }
       tc::mma_commit(&accb[0]);
     }
@@ -440,12 +458,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
     auto issue_b1_chunk = [&](int n) {
       for (int kb = 0; kb < 4 && ok; ++kb) {
         const int j = 4 * n + kb;
-        while (next_load < kB1Jobs && next_load <= j + kB1Slots - 1) is.load_b1(next_load++);
         const int s = j % kB1Slots;
         is.consume_begin(s);
         tc::mma_kblock(tmem + 256 * (n & 1), tc::smem_u32(sm + kXHi + kb * kBlk),
                        tc::smem_u32(sm + kXLo + s * kB1Slot), id160, kb > 0, 4);
         is.consume_end(s);
+        // refill freed slots (the slot of job j - 1 at the latest) while job j's MMAs run
+        while (next_load < kB1Jobs && next_load <= j + kB1Slots - 1) is.load_b1(next_load++);
       }
       tc::mma_commit(&accb[n & 1]);
     };
@@ -463,7 +482,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
         tc::tmem_ld16(src + 16 * c, z);
         tc::tmem_wait_ld();
         if (valid) {
-          float4* d = reinterpret_cast<float4*>(a.dD + grow * kKD + kBChunk * n + 16 * c);
+          float4* d = reinterpret_cast<float4*>(a.dD + grow * kKD + kBChunk * is.b1_chunk(n) + 16 * c);
 #pragma unroll
           for (int u = 0; u < 4; ++u) d[u] = make_float4(z[4 * u], z[4 * u + 1], z[4 * u + 2], z[4 * u + 3]);
         }
