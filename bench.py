@@ -36,6 +36,9 @@ WORKLOADS = {
               "NVE dt 0.5 fs from 300 K, rebuild every 10 steps, skin 2 A",
     "water12k": "4096 H2O (12,288 atoms) at 1.0 g/cm3, r_c 6 A, r_s 0.5 A, sel 46/92, NVE dt 0.5 fs from 300 K, "
                 "rebuild every 10 steps, skin 2 A",
+    # a smaller copper box for kernel profiles: same model, density and neighbour count per atom
+    "cu32k": "Cu FCC 20x20x20 cells (32,000 atoms), a 3.634 A, sigma 0.08 A, r_c 8 A, r_s 2 A, sel 512, "
+             "NVE dt 0.5 fs from 300 K, rebuild every 10 steps, skin 2 A",
 }
 
 # per real neighbour: embedding recompute + backward MACs (x2 FLOP); forward embedding + T
@@ -49,6 +52,9 @@ def load_workload(name):
     if name == "cu131k":
         s = synth.copper_fcc(32, 0)
         w = synth.copper_weights(1001)
+    elif name == "cu32k":
+        s = synth.copper_fcc(20, 0)
+        w = synth.copper_weights(1001)
     elif name == "water12k":
         s = synth.water_box(4096, 0)
         w = synth.water_weights(1001)
@@ -61,7 +67,7 @@ def load_workload(name):
 def cpu_sample(name):
     """A bounded CPU sample of the same workload: same model and density, smaller box."""
     from paper_2410_22867_gb300 import synth
-    if name == "cu131k":
+    if name in ("cu131k", "cu32k"):
         return synth.copper_fcc(8, 0), synth.copper_weights(1001)
     return synth.water_box(256, 0), synth.water_weights(1001)
 
@@ -350,7 +356,7 @@ def e2e(m, s, stream, nsteps):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--workload", default="cu131k", choices=sorted(WORKLOADS))
@@ -362,7 +368,7 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if args.precision is None:
-        args.precision = os.environ.get("DP_BENCH_PRECISION", "fp32")
+        args.precision = os.environ.get("DP_BENCH_PRECISION", "mix_fp16")
     world, rank, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, world, rank)
