@@ -659,8 +659,11 @@ __global__ void __launch_bounds__(kRows, 2) k_mix_embed_bwd(MixArgs a) {
         }
       }
     }
-    // chain rule through the normalisation and the environment row
-    double g3[3] = {0.0, 0.0, 0.0};
+    // chain rule through the normalisation and the environment row.  Per-row terms
+    // and the per-warp partial sums stay FP32 (FP64 arithmetic runs at a small
+    // fraction of the FP32 rate on this GPU); only the accumulation into the
+    // force and virial arrays is FP64.
+    float g3[3] = {0.f, 0.f, 0.f};
     if (valid) {
       dR[0] += ds;
 #pragma unroll
@@ -672,18 +675,18 @@ __global__ void __launch_bounds__(kRows, 2) k_mix_embed_bwd(MixArgs a) {
       const float proj = dR[1] * f.d[0] + dR[2] * f.d[1] + dR[3] * f.d[2];
       const float common = (dR[0] * dsr + dq * proj) * rinv;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) g3[c] = (double)(common * f.d[c] + qv * dR[1 + c]);
+      for (int c = 0; c < 3; ++c) g3[c] = common * f.d[c] + qv * dR[1 + c];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) atomicAdd(&a.force[3 * (size_t)f.j + c], -g3[c]);
+      for (int c = 0; c < 3; ++c) atomicAdd(&a.force[3 * (size_t)f.j + c], (double)(-g3[c]));
     }
     // centre force and per-atom virial: warp-segmented sums over rows of the same atom
-    double vals[12];
+    float vals[12];
 #pragma unroll
     for (int c = 0; c < 3; ++c) vals[c] = g3[c];
 #pragma unroll
     for (int p = 0; p < 3; ++p)
 #pragma unroll
-      for (int q = 0; q < 3; ++q) vals[3 + 3 * p + q] = -g3[p] * (double)f.d[q];
+      for (int q = 0; q < 3; ++q) vals[3 + 3 * p + q] = -g3[p] * f.d[q];
     const int my = valid ? f.la : -1;
     unsigned todo = __ballot_sync(0xffffffffu, valid);
     while (todo) {
@@ -693,13 +696,13 @@ __global__ void __launch_bounds__(kRows, 2) k_mix_embed_bwd(MixArgs a) {
       const unsigned mask = __ballot_sync(0xffffffffu, in);
 #pragma unroll
       for (int q = 0; q < 12; ++q) {
-        double v = in ? vals[q] : 0.0;
+        float v = in ? vals[q] : 0.f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == leader) {
           const size_t atom = (size_t)ti.a0 + seg;
-          if (q < 3) atomicAdd(&a.force[3 * atom + q], v);
-          else atomicAdd(&a.vir_atom[9 * atom + q - 3], v);
+          if (q < 3) atomicAdd(&a.force[3 * atom + q], (double)v);
+          else atomicAdd(&a.vir_atom[9 * atom + q - 3], (double)v);
         }
       }
       todo &= ~mask;
@@ -798,28 +801,56 @@ __global__ void k_mix_descriptor(int N, int ntypes, float invS, const float* __r
 }
 
 // dT[c][a] = (1/S) (sum_b dD[a][b] T[c][b] + [a < 16] sum_a' dD[a'][a] T[c][a']), stored [N][100] float4.
-__global__ void k_mix_dT(int N, float invS, const float* __restrict__ Tm, const float* __restrict__ dD,
-                         float4* dT) {
-  __shared__ float sT[400];
-  __shared__ float sD[kKD];
-  for (int i = blockIdx.x; i < N; i += gridDim.x) {
-    for (int q = threadIdx.x; q < 400; q += blockDim.x) sT[q] = Tm[(size_t)i * 400 + q];
-    for (int q = threadIdx.x; q < kKD; q += blockDim.x) sD[q] = dD[(size_t)i * kKD + q];
-    __syncthreads();
-    for (int q = threadIdx.x; q < kN3; q += blockDim.x) {
+// One warp per atom: T (4 x 100) and dD (100 x 16, rows padded to 17 floats so that a
+// warp reading one column hits 32 banks) staged in shared memory; the second term's 64
+// outputs (c, a < 16) are split over the 32 lanes, two each.
+constexpr int kDtWarps = 4;
+constexpr int kDtRow = kM2 + 1;
+
+__global__ void __launch_bounds__(32 * kDtWarps) k_mix_dT(int N, float invS, const float* __restrict__ Tm,
+                                                         const float* __restrict__ dD, float4* __restrict__ dT) {
+  __shared__ __align__(16) float sT[kDtWarps][400];
+  __shared__ float sD[kDtWarps][kN3 * kDtRow];
+  __shared__ float s2[kDtWarps][4 * kM2];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float* T = sT[w];
+  float* D = sD[w];
+  float* t2 = s2[w];
+  for (int i = blockIdx.x * kDtWarps + w; i < N; i += gridDim.x * kDtWarps) {
+    const float4* Ti = reinterpret_cast<const float4*>(Tm + (size_t)i * 400);
+    for (int q = lane; q < 100; q += 32) reinterpret_cast<float4*>(T)[q] = Ti[q];
+    const float4* Di = reinterpret_cast<const float4*>(dD + (size_t)i * kKD);
+    for (int q = lane; q < kKD / 4; q += 32) {
+      const float4 v = Di[q];
+      float* d = D + (q >> 2) * kDtRow + (q & 3) * 4;
+      d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+    }
+    __syncwarp();
+    {  // second term: lane -> a = lane % 16, c = lane / 16 and c + 2
+      const int a = lane & 15, c = lane >> 4;
+      float u0 = 0.f, u1 = 0.f;
+      for (int a2 = 0; a2 < kN3; ++a2) {
+        const float d = D[a2 * kDtRow + a];
+        u0 = fmaf(d, T[c * kN3 + a2], u0);
+        u1 = fmaf(d, T[(c + 2) * kN3 + a2], u1);
+      }
+      t2[c * kM2 + a] = u0;
+      t2[(c + 2) * kM2 + a] = u1;
+    }
+    __syncwarp();
+    for (int a = lane; a < kN3; a += 32) {
       float v[4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        float s = 0.f;
+      for (int c = 0; c < 4; ++c) v[c] = (a < kM2) ? t2[c * kM2 + a] : 0.f;
 #pragma unroll
-        for (int b = 0; b < kM2; ++b) s = fmaf(sD[q * kM2 + b], sT[c * kN3 + b], s);
-        if (q < kM2)
-          for (int a2 = 0; a2 < kN3; ++a2) s = fmaf(sD[a2 * kM2 + q], sT[c * kN3 + a2], s);
-        v[c] = s * invS;
+      for (int b = 0; b < kM2; ++b) {
+        const float d = D[a * kDtRow + b];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = fmaf(d, T[c * kN3 + b], v[c]);
       }
-      dT[(size_t)i * kN3 + q] = make_float4(v[0], v[1], v[2], v[3]);
+      dT[(size_t)i * kN3 + a] = make_float4(v[0] * invS, v[1] * invS, v[2] * invS, v[3] * invS);
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
@@ -865,7 +896,8 @@ dp_status launch_mix_descriptor(Model* m, int N) {
 }
 
 dp_status launch_mix_embed_backward(Model* m, int N) {
-  k_mix_dT<<<std::min(N, 4 * num_sms()), 128, 0, m->stream>>>(N, 1.f / (float)m->S, static_cast<const float*>(m->Tm),
+  const int dt_grid = std::max(1, std::min((N + kDtWarps - 1) / kDtWarps, 5 * num_sms()));
+  k_mix_dT<<<dt_grid, 32 * kDtWarps, 0, m->stream>>>(N, 1.f / (float)m->S, static_cast<const float*>(m->Tm),
                                                               static_cast<const float*>(m->dD),
                                                               static_cast<float4*>(m->dTm));
   DP_CUDA_TRY(m, cudaMemsetAsync(m->vir_atom, 0, sizeof(double) * 9 * (size_t)N, m->stream));

@@ -302,8 +302,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
       }
       tc::mma_commit(&accb[0]);
     }
+    __syncwarp();  // lanes 1..31 of warp 0 wait here, not in a polling loop beside the issuer
     wait_acc(0);
     if (t == 0) is.load_split(0, 0);  // prefetch under the epilogue
+    __syncwarp();
     // f1/f2 factors of this row are fetched ahead of the TMEM loop below
 #pragma unroll 1
     for (int c = c_beg; c < c_end; ++c) {
@@ -330,8 +332,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
 
     // ---- L2: h2 = h1 + tanh(h1 W2 + b2)
     if (t == 0) issue_split(0);
+    __syncwarp();
     wait_acc(0);
     if (t == 0) is.load_split(1, 0);
+    __syncwarp();
 #pragma unroll 1
     for (int c = c_beg; c < c_end; ++c) {
       float z[16], r[16], f[16];
@@ -353,8 +357,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
 
     // ---- L3: h3 = h2 + tanh(h2 W3 + b3), E_i, dz3
     if (t == 0) issue_split(1);
+    __syncwarp();
     wait_acc(0);
     if (t == 0) is.load_split(2, 0);
+    __syncwarp();
     float e = 0.f;
 #pragma unroll 1
     for (int c = c_beg; c < c_end; ++c) {
@@ -378,6 +384,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
 
     // ---- B3: dh2 = w4 + dz3 W3^T ; dz2 = dh2 (1 - t2^2)
     if (t == 0) issue_split(2);
+    __syncwarp();
     {  // fetch this row's 1 - t2^2 factors while the MMAs run
       uint4 fq[16];
 #pragma unroll
@@ -393,6 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
       }
       wait_acc(0);
       if (t == 0) is.load_split(3, 0);
+      __syncwarp();
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int cc = c_beg + c;
@@ -416,6 +424,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
 
     // ---- B2: dh1 = dh2 + dz2 W2^T ; dz1 = dh1 (1 - h1^2)
     if (t == 0) issue_split(3);
+    __syncwarp();
     {
       uint4 fq[16];
 #pragma unroll
@@ -434,6 +443,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
       // its weights stream in under this epilogue
       if (t == 0)
         for (int j = 0; j < kB1Slots - 1; ++j) is.load_b1(j);
+      __syncwarp();
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int cc = c_beg + c;
@@ -472,6 +482,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
       issue_b1_chunk(0);
       issue_b1_chunk(1);
     }
+    __syncwarp();
     for (int n = 0; n < nch; ++n) {
       const int rg = n & 1;
       wait_acc(rg);
@@ -491,6 +502,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
       __syncthreads();
       tc::tc_fence_after();
       if (t == 0 && n + 2 < nch && ok) issue_b1_chunk(n + 2);
+      __syncwarp();
     }
   }
   tc::tc_fence_before();
