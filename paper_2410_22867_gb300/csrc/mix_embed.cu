@@ -3,7 +3,7 @@
 // Blackwell: the 25->50 and 50->100 layers of the embedding net (and their
 // backward) are MMAs with 16-bit operands and FP32 accumulation in TMEM; the
 // environment matrix, the 1->25 layer, all tanh (on the SFU) and residuals stay
-// FP32 on the CUDA cores.  The reduction T = R_hat^T G (Eq. 4) is a third MMA
+// FP32 on the CUDA cores.  The reduction T = R_hat^T G of the descriptor (Section II-A) is a third MMA
 // per tile with fp16 operands: G^T [feature][row] against a block-sparse R_hat^T
 // whose column (atom slot, c) is non-zero only on that atom's rows, so one
 // 128x32x128 product yields the partial T of every atom in the tile.
