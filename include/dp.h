@@ -206,6 +206,31 @@ long long dp_kernel_launches(const dp_model* m);
  */
 dp_status dp_selftest(int which, double* result);
 
+/*
+ * dp_selftest_noalloc -- the checks of dp_selftest for several cases in one call,
+ * without allocating memory.  The paper has no counterpart: this is a device
+ * health check of the library for callers that cannot allocate (a process whose
+ * device memory already belongs to its own pool, or a monitor that must not
+ * trigger the device-wide wait of cudaFree, which dp_selftest calls).
+ *   which[ncases]      host: case numbers 0..4, as for dp_selftest.
+ *   ncases             0..DP_SELFTEST_NOALLOC_MAX_CASES; 0 performs only the set-up.
+ *   results[2*ncases]  host, caller-owned: per case max |error| and max |value|.
+ * Scratch: 16 bytes per case in a fixed 256-byte device array inside the library
+ * (one copy per device).  Every call zeroes the slots it uses before its kernels
+ * run, so nothing has to be cleared by the caller.  The first call on a device
+ * does the set-up (looks up that array's address, sets kernel attributes); make
+ * it before any stream capture on that device.  Calls that overlap in time on
+ * one device (other host threads or streams) share the array and race: the
+ * caller must serialise them.  Work runs on the legacy default stream; the call
+ * returns when the results are on the host.
+ * Errors: DP_ERR_CAPACITY if ncases > DP_SELFTEST_NOALLOC_MAX_CASES (nothing runs);
+ * DP_ERR_ARG for ncases < 0, a null array with ncases > 0, or a case outside 0..4;
+ * DP_ERR_UNSUPPORTED on a device without tcgen05; DP_ERR_CUDA if the set-up, a
+ * launch or the copy failed; DP_ERR_WAIT_TIMEOUT if an MMA wait gave up.
+ */
+#define DP_SELFTEST_NOALLOC_MAX_CASES 16
+dp_status dp_selftest_noalloc(const int* which, int ncases, double* results);
+
 /* Wait for the model's stream; return and clear the sticky device error (DP_OK if none). */
 dp_status dp_sync(dp_model* m);
 

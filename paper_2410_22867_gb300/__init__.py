@@ -31,7 +31,7 @@ STATUS = {0: "DP_OK", 1: "DP_ERR_ARG", 2: "DP_ERR_CUDA", 3: "DP_ERR_OOM", 4: "DP
 # exported symbols of include/dp.h
 EXPORTS = ("dp_create", "dp_compute", "dp_compute_batch", "dp_verlet_step", "dp_md_run_batch", "dp_param_grad",
            "dp_ntheta", "dp_get_nlist", "dp_phase_times", "dp_kernel_launches", "dp_sync", "dp_last_error",
-           "dp_destroy", "dp_version", "dp_selftest")
+           "dp_destroy", "dp_version", "dp_selftest", "dp_selftest_noalloc")
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -84,8 +84,10 @@ def lib():
             L.dp_kernel_launches.argtypes = [_P]
             L.dp_kernel_launches.restype = ctypes.c_longlong
             L.dp_selftest.argtypes = [_I, _P]
+            L.dp_selftest_noalloc.argtypes = [_P, _I, _P]
             for name in ("dp_create", "dp_compute", "dp_compute_batch", "dp_verlet_step", "dp_md_run_batch",
-                         "dp_param_grad", "dp_get_nlist", "dp_phase_times", "dp_sync", "dp_selftest"):
+                         "dp_param_grad", "dp_get_nlist", "dp_phase_times", "dp_sync", "dp_selftest",
+                         "dp_selftest_noalloc"):
                 getattr(L, name).restype = _I
             _lib = L
     return _lib
@@ -108,6 +110,22 @@ def selftest(which: int):
     if st != 0:
         raise DPError(st, "dp_selftest failed")
     return out[0], out[1]
+
+
+SELFTEST_NOALLOC_MAX_CASES = 16
+
+
+def selftest_noalloc(cases):
+    """dp_selftest_noalloc: the self check for each case in ``cases`` with no
+    allocation (fixed scratch inside the library); returns [(max error, max value)]."""
+    cases = [int(c) for c in cases]
+    n = len(cases)
+    which = (ctypes.c_int * max(n, 1))(*cases)
+    out = (ctypes.c_double * max(2 * n, 2))()
+    st = lib().dp_selftest_noalloc(ctypes.cast(which, _P), n, ctypes.cast(out, _P))
+    if st != 0:
+        raise DPError(st, "dp_selftest_noalloc failed")
+    return [(out[2 * i], out[2 * i + 1]) for i in range(n)]
 
 
 class DPModel:

@@ -138,3 +138,108 @@ extern "C" dp_status dp_selftest(int which, double* result) {
   result[1] = h[1];
   return DP_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the self check.
+//
+// dp_selftest above takes its 32 bytes of device scratch from cudaMalloc and
+// hands them back with cudaFree on every call.  Some callers cannot do that: a
+// serving process that has already given the whole device to its own memory
+// pool gets an out-of-memory error exactly when it wants to re-check a device,
+// and a health monitor running beside live work must not pay for cudaFree,
+// which waits for the whole device.  This variant keeps its scratch in a fixed
+// array compiled into the library, so a call allocates nothing.
+
+#include <cstring>
+#include <mutex>
+
+namespace dpg {
+namespace {
+
+// Per case 16 bytes: two floats that the kernel raises with atomicMax (max
+// |error|, max |value|; both must start at 0) and the wait-timeout word (must
+// start at 0), padded to 16 bytes.  Every call zeroes the slots it uses.
+constexpr int kNoAllocCases = DP_SELFTEST_NOALLOC_MAX_CASES;
+static __device__ __align__(256) unsigned int g_selftest_scratch[kNoAllocCases * 4];
+
+constexpr int kNoAllocDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned int* g_noalloc_scratch[kNoAllocDevices] = {nullptr};
+
+template <int N, int KB>
+constexpr size_t selftest_smem() { return (size_t)KB * 128 * 128 + (size_t)KB * N * 128 + 1024; }
+
+template <int N, int KB, bool F16>
+cudaError_t noalloc_prepare() {
+  return cudaFuncSetAttribute(reinterpret_cast<const void*>(k_mma_selftest<N, KB, F16>),
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)selftest_smem<N, KB>());
+}
+
+template <int N, int KB, bool F16>
+cudaError_t noalloc_launch(unsigned int* slot) {
+  k_mma_selftest<N, KB, F16><<<1, 128, selftest_smem<N, KB>()>>>(reinterpret_cast<float*>(slot),
+                                                                 reinterpret_cast<int*>(slot + 2));
+  return cudaGetLastError();
+}
+
+// Once per device: the device address of the scratch array (the module holding it
+// is loaded on first use) and the shared-memory limits of the five kernels.
+dp_status noalloc_setup(unsigned int** scratch) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return DP_ERR_CUDA;
+  if (dev < 0 || dev >= kNoAllocDevices) return DP_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_scratch[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_selftest_scratch) != cudaSuccess || !p) return DP_ERR_CUDA;
+    if (noalloc_prepare<64, 1, false>() != cudaSuccess || noalloc_prepare<112, 1, false>() != cudaSuccess ||
+        noalloc_prepare<240, 4, false>() != cudaSuccess || noalloc_prepare<32, 1, true>() != cudaSuccess ||
+        noalloc_prepare<160, 4, true>() != cudaSuccess)
+      return DP_ERR_CUDA;
+    g_noalloc_scratch[dev] = static_cast<unsigned int*>(p);
+  }
+  *scratch = g_noalloc_scratch[dev];
+  return DP_OK;
+}
+
+}  // namespace
+}  // namespace dpg
+
+extern "C" dp_status dp_selftest_noalloc(const int* which, int ncases, double* results) {
+  if (ncases < 0) return DP_ERR_ARG;
+  if (ncases > kNoAllocCases) return DP_ERR_CAPACITY;
+  if (ncases > 0 && (!which || !results)) return DP_ERR_ARG;
+  for (int i = 0; i < ncases; ++i)
+    if (which[i] < 0 || which[i] > 4) return DP_ERR_ARG;
+  if (!tc_available(nullptr)) return DP_ERR_UNSUPPORTED;
+  unsigned int* scratch = nullptr;
+  dp_status st = noalloc_setup(&scratch);
+  if (st != DP_OK || ncases == 0) return st;
+
+  // legacy default stream: the zeroing, the launches and the read-back are ordered
+  if (cudaMemsetAsync(scratch, 0, (size_t)ncases * 16, 0) != cudaSuccess) return DP_ERR_CUDA;
+  for (int i = 0; i < ncases; ++i) {
+    unsigned int* slot = scratch + 4 * i;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (which[i]) {
+      case 0: e = noalloc_launch<64, 1, false>(slot); break;
+      case 1: e = noalloc_launch<112, 1, false>(slot); break;
+      case 2: e = noalloc_launch<240, 4, false>(slot); break;
+      case 3: e = noalloc_launch<32, 1, true>(slot); break;
+      case 4: e = noalloc_launch<160, 4, true>(slot); break;
+      default: break;
+    }
+    if (e != cudaSuccess) return DP_ERR_CUDA;
+  }
+  unsigned int host[kNoAllocCases * 4];
+  if (cudaMemcpy(host, scratch, (size_t)ncases * 16, cudaMemcpyDeviceToHost) != cudaSuccess) return DP_ERR_CUDA;
+  st = DP_OK;
+  for (int i = 0; i < ncases; ++i) {
+    float v[2];
+    memcpy(v, host + 4 * i, sizeof(v));
+    results[2 * i] = v[0];
+    results[2 * i + 1] = v[1];
+    if (host[4 * i + 2] != 0) st = DP_ERR_WAIT_TIMEOUT;
+  }
+  return st;
+}
