@@ -441,6 +441,12 @@ dp_status dp_create(dp_model** out, int ntypes, const char* const* type_map, dou
     A_(dTm, 16 * N * kN3);
     A_(tc_weights, mix_fit_weight_bytes(nt));
   }
+  m->pg_cap = std::min(max_atoms, kPgAtoms);
+  m->pg_roff_cap = 2 * (size_t)nt * N + 64;
+  A_(pg_ws, param_grad_workspace_bytes(m->pg_cap, prec == DP_FP64));
+  A_(pg_roff, 4 * m->pg_roff_cap);
+  A_(pg_w, 24 * N);
+  A_(pg_scal, 64);
 #undef A_
   if (halloc(m, &m->geom_host, sizeof(RepGeom) * R + sizeof(int) * (R + 1) + 64) != DP_OK) return fail(DP_ERR_OOM, m->last_error);
   if (halloc(m, &m->err_host, 64) != DP_OK) return fail(DP_ERR_OOM, m->last_error);
@@ -602,9 +608,18 @@ void dp_destroy(dp_model* h) {
 extern "C" dp_status dp_param_grad(dp_model* h, int natoms, const double* coords, const int* types,
                                    const double* box, double E0, const double* F0, double cE, double cF,
                                    double* grad, double* loss) {
-  (void)natoms; (void)coords; (void)types; (void)box; (void)E0; (void)F0; (void)cE; (void)cF; (void)grad;
-  (void)loss;
   if (!h) return DP_ERR_ARG;
-  h->m.last_error = "dp_param_grad: not available in this build";
-  return DP_ERR_UNSUPPORTED;
+  Model* m = &h->m;
+  if (!coords || !types || !box || !F0 || !grad) { m->last_error = "null argument"; return DP_ERR_ARG; }
+  if (natoms < 1) { m->last_error = "natoms < 1"; return DP_ERR_ARG; }
+  if (natoms > m->max_atoms) { m->last_error = "natoms out of range"; return DP_ERR_CAPACITY; }
+  const int offs[2] = {0, natoms};
+  m->md_valid = false;
+  DP_TRY(setup_replicas(m, 1, offs, box, natoms));
+  m->natoms = natoms;
+  DP_TRY(launch_type_sort(m, types, natoms));
+  DP_TRY(launch_load_positions(m, coords, natoms));
+  DP_TRY(launch_rebuild(m, natoms));
+  DP_TRY(force_eval(m, natoms));
+  return launch_param_grad(m, natoms, F0, E0, cE, cF, grad, loss);
 }

@@ -21,6 +21,8 @@ constexpr int kKD = kN3 * kM2;  // 1600, descriptor length
 constexpr int kEmbParams = kN1 + kN1 + kN1 * kN2 + kN2 + kN2 * kN3 + kN3;       // 6450
 constexpr int kFitParams = kKD * kF + kF + kF * kF + kF + kF * kF + kF + kF + 1;  // 500161
 constexpr int kMaxTypes = 4;
+// parameter gradient: centre atoms per chunk, neighbour rows per chunk of the embedding reverse
+constexpr int kPgAtoms = 2048, kPgRows = 16384;
 
 // offsets inside one embedding block
 constexpr int kEW1 = 0, kEb1 = kN1, kEW2 = 2 * kN1, kEb2 = kEW2 + kN1 * kN2, kEW3 = kEb2 + kN2,
@@ -142,6 +144,13 @@ struct Model {
   int* scan_blk = nullptr;    // [nt][N / 1024 + 1]
   float* Tseg = nullptr;      // [nt][N][400] partial T per neighbour type
   void* dTm = nullptr;        // [N][100] float4
+  // parameter gradient
+  void* pg_ws = nullptr;      // per-chunk activations and adjoints (FP64 or FP32)
+  int pg_cap = 0;             // centre atoms per chunk
+  int* pg_roff = nullptr;     // row offsets of every row chunk of one call
+  size_t pg_roff_cap = 0;
+  double* pg_w = nullptr;     // [N][3] tangent direction 2 cF (F - F0), internal order
+  double* pg_scal = nullptr;  // alpha, loss, E
 
   // MD bookkeeping
   int natoms = 0;             // atoms of the current call
@@ -247,6 +256,10 @@ dp_status launch_mix_embed_backward(Model* m, int N);
 dp_status mix_fit_setup(Model* m);
 size_t mix_fit_weight_bytes(int ntypes);
 dp_status launch_mix_fitting(Model* m, int N);
+// parameter gradient (pgrad.cu)
+size_t param_grad_workspace_bytes(int cap, bool fp64);
+dp_status launch_param_grad(Model* m, int N, const double* F0, double E0, double cE, double cF, double* grad,
+                            double* loss);
 inline bool is_mixed(const Model* m) { return m->prec == DP_MIX_BF16 || m->prec == DP_MIX_FP16; }
 // md.cu
 dp_status launch_outputs(Model* m, int N, double* energy_rep, double* atom_energy, double* forces,
