@@ -192,6 +192,65 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# Algorithmic tanh per real neighbour row of the embedding net (25 + 50 + 100); the backward
+# recomputes the forward, and tanh' = 1 - t^2 needs no further tanh.
+TANH_PER_NEIGHBOUR = 175
+SFU_PER_CLK_PER_SM = 16   # MUFU results per clock per SM (documented rate of recent NVIDIA GPUs)
+N_SMS = 152
+
+# DRAM bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# 32,000-atom copper capture, per real neighbour row; scaled to a launch by the row count.
+# Only valid while the kernel is unchanged since the capture (see profiles/).
+TRAFFIC_PER_ROW = {
+    ("embedding_backward", "mix_fp16"): (173.6896e6 + 5.020160e6) / 5726060,  # profiles/k_mix_embed_bwd_cu32k.md
+    ("embedding_forward", "mix_fp16"): (95.655424e6 + 20.975872e6) / 5726060,  # profiles/k_mix_embed_fwd_cu32k.md
+}
+
+
+def kernel_times(ph):
+    return {"format": ph[0], "embedding_forward": ph[5], "descriptor": max(0.0, ph[1] - ph[5]),
+            "fitting": ph[2], "dE_dT": max(0.0, ph[3] - ph[6]), "embedding_backward": ph[6]}
+
+
+def roofline(prec, kernel, ms, N, n_neigh):
+    pk, src = peaks()
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    t = ms * 1e-3
+    mixed = prec.startswith("mix")
+    traffic = TRAFFIC_PER_ROW.get((kernel, prec))
+    out = {"kernel": kernel, "kernel_ms": ms,
+           "traffic": traffic * n_neigh if traffic is not None else None}
+    if kernel in ("embedding_forward", "embedding_backward"):
+        flop = n_neigh * (EMB_FWD_FLOP_PER_NEIGHBOUR if kernel == "embedding_forward" else EMB_BWD_FLOP_PER_NEIGHBOUR)
+        tanh = n_neigh * TANH_PER_NEIGHBOUR
+        if mixed:
+            # bound = max(tensor, SFU); at 175 tanh vs ~2e4 flop per row the SFU term is the larger
+            sfu = N_SMS * SFU_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
+            tens = pk.get("bf16_tflops_sustained", 1700.0)
+            out.update({"bound": "alu", "achieved": tanh / t / 1e12, "peak": sfu, "unit": "Ttanh/s",
+                        "frac": tanh / t / 1e12 / sfu,
+                        "peak_source": f"derived: {N_SMS} SMs x {SFU_PER_CLK_PER_SM} MUFU/clk x {sm_mhz:.0f} MHz",
+                        "tensor": {"achieved": flop / t / 1e12, "peak": tens, "unit": "TFLOP/s",
+                                   "frac": flop / t / 1e12 / tens, "peak_source": f"{src} bf16 sustained"}})
+            return out
+        work = flop
+    elif kernel == "fitting":
+        work = N * FIT_FLOP_PER_ATOM
+        if mixed:
+            tens = pk.get("bf16_tflops_sustained", 1700.0)
+            out.update({"bound": "tensor", "achieved": work / t / 1e12, "peak": tens, "unit": "TFLOP/s",
+                        "frac": work / t / 1e12 / tens, "peak_source": f"{src} bf16 sustained"})
+            return out
+    else:
+        work = 0
+    lanes = {"fp64": 2, "fp32": 128}.get(prec, 128)  # FMA lanes per SM per clock
+    peak = N_SMS * lanes * 2 * sm_mhz * 1e6 / 1e12
+    ach = work / t / 1e12 if work else 0.0
+    out.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "peak_source": f"derived: {N_SMS} SMs x {lanes} FMA lanes x 2 x {sm_mhz:.0f} MHz"})
+    return out
+
+
 def neighbour_count(m):
     nl, _ = m.get_nlist()
     return int((nl >= 0).sum().item())
@@ -231,34 +290,16 @@ def run_mine(args, world, rank, local):
         launches = m.kernel_launches() - launches0
         ms_step = t_ms / args.steps
         value = world * N * args.steps / (t_ms * 1e-3)
-        phases = m.phase_times(3)  # [format, descriptor, fitting, embed backward, total]
+        # [format, descriptor phase, fitting, embedding-backward phase, total, embedding forward
+        #  kernel, embedding backward kernel] from events on the model's stream
+        phases = m.phase_times(args.phase_repeats)
 
     extra = {}
     if rank == 0:
-        # dominant kernel and its roofline
-        names = ["format", "descriptor", "fitting", "embedding_backward"]
-        k = int(np.argmax(phases[:4]))
-        pk, src = peaks()
-        if prec in ("fp32", "fp64"):
-            sm_mhz = pk.get("sm_max_mhz", 2070.0)
-            lanes = 128 if prec == "fp32" else 2  # FP32 FMA lanes per SM; FP64 ~ 1.25 TF/s per GPU
-            peak_tf = 152 * lanes * 2 * sm_mhz * 1e6 / 1e12
-            flops = {1: n_neigh * EMB_FWD_FLOP_PER_NEIGHBOUR, 2: N * FIT_FLOP_PER_ATOM,
-                     3: n_neigh * EMB_BWD_FLOP_PER_NEIGHBOUR}.get(k, 0)
-            achieved = flops / (phases[k] * 1e-3) / 1e12 if phases[k] > 0 and flops else 0.0
-            roof = {"bound": "alu", "kernel": names[k], "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                    "frac": achieved / peak_tf, "traffic": None,
-                    "peak_source": f"derived: 152 SMs x {lanes} {prec} FMA lanes x 2 x {sm_mhz:.0f} MHz"}
-        else:
-            flops = {1: n_neigh * EMB_FWD_FLOP_PER_NEIGHBOUR, 2: N * FIT_FLOP_PER_ATOM,
-                     3: n_neigh * EMB_BWD_FLOP_PER_NEIGHBOUR}.get(k, 0)
-            achieved = flops / (phases[k] * 1e-3) / 1e12 if phases[k] > 0 and flops else 0.0
-            peak_tf = pk.get("bf16_tflops_sustained", 1700.0)
-            roof = {"bound": "tensor", "kernel": names[k], "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                    "frac": achieved / peak_tf, "traffic": None,
-                    "peak_source": f"{src} bf16 sustained"}
-        extra["roofline"] = roof
-        extra["phases_ms"] = dict(zip(names + ["evaluation"], [round(p, 4) for p in phases]))
+        kern = kernel_times(phases)
+        dominant = max(kern, key=kern.get)
+        extra["roofline"] = roofline(prec, dominant, kern[dominant], N, n_neigh)
+        extra["kernels_ms"] = {k: round(v, 4) for k, v in kern.items()}
         # FP64 comparison (speed and error) on the same configuration
         if not args.no_fp64 and prec != "fp64":
             extra["fp64"] = fp64_compare(args, s, w, v0, m, stream)
@@ -363,6 +404,7 @@ def main():
     ap.add_argument("--precision", default=None, choices=["mix_bf16", "mix_fp16", "fp32", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--phase-repeats", type=int, default=10)
     ap.add_argument("--no-fp64", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

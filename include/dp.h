@@ -188,7 +188,9 @@ dp_status dp_get_nlist(dp_model* m, int* nlist, int* images);
  * CUDA events on the model's stream around each phase, and write the mean
  * milliseconds per phase to ms[8]: [0] list format, [1] descriptor (environment
  * matrix, embedding, T, D), [2] fitting forward+backward, [3] embedding backward
- * with force and virial scatter, [4] whole evaluation, [5..7] reserved (0).
+ * with force and virial scatter, [4] whole evaluation, [5] the embedding
+ * forward kernel alone (mixed precision; else = [1]), [6] the embedding backward
+ * kernel alone (mixed precision: without the dE/dT kernel; else = [3]), [7] 0.
  * Synchronous.  Leaves forces/energies of the last evaluation in place.
  */
 dp_status dp_phase_times(dp_model* m, int repeats, float* ms);

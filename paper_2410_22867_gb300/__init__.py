@@ -260,10 +260,11 @@ class DPModel:
 
     # ------------------------------------------------------------------ measurement
     def phase_times(self, repeats: int = 3):
-        """Mean ms of [format, descriptor, fitting, embedding backward, whole evaluation]."""
+        """Mean ms of [format, descriptor, fitting, embedding backward, whole evaluation,
+        embedding forward kernel, embedding backward kernel] (dp_phase_times)."""
         ms = (ctypes.c_float * 8)()
         self._check(lib().dp_phase_times(self.h, int(repeats), ctypes.cast(ms, _P)))
-        return list(ms)[:5]
+        return list(ms)[:7]
 
     def kernel_launches(self) -> int:
         return int(lib().dp_kernel_launches(self.h))

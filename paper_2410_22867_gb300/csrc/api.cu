@@ -563,7 +563,10 @@ dp_status dp_phase_times(dp_model* h, int repeats, float* ms) {
   const int N = m->natoms;
   cudaEvent_t ev[5];
   for (auto& e : ev) DP_CUDA_TRY(m, cudaEventCreate(&e));
-  double acc[5] = {0, 0, 0, 0, 0};
+  const bool split = is_mixed(m);  // the mixed launchers record the kernel-level split
+  if (split)
+    for (auto& e : m->sub_ev) DP_CUDA_TRY(m, cudaEventCreate(&e));
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
   dp_status st = DP_OK;
   for (int r = 0; r < repeats && st == DP_OK; ++r) {
     cudaEventRecord(ev[0], m->stream);
@@ -585,9 +588,19 @@ dp_status dp_phase_times(dp_model* h, int repeats, float* ms) {
     float tot = 0;
     cudaEventElapsedTime(&tot, ev[0], ev[4]);
     acc[4] += tot;
+    if (split && st == DP_OK) {
+      float f = 0, b = 0;
+      cudaEventElapsedTime(&f, ev[1], m->sub_ev[0]);
+      cudaEventElapsedTime(&b, m->sub_ev[1], ev[4]);
+      acc[5] += f;
+      acc[6] += b;
+    }
   }
   for (auto& e : ev) cudaEventDestroy(e);
-  for (int q = 0; q < 8; ++q) ms[q] = q < 5 ? (float)(acc[q] / repeats) : 0.f;
+  if (split)
+    for (auto& e : m->sub_ev) { cudaEventDestroy(e); e = nullptr; }
+  if (!split) { acc[5] = acc[1]; acc[6] = acc[3]; }
+  for (int q = 0; q < 8; ++q) ms[q] = q < 7 ? (float)(acc[q] / repeats) : 0.f;
   return st;
 }
 

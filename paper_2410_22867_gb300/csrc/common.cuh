@@ -157,6 +157,7 @@ struct Model {
   bool lists_valid = false;
   bool md_valid = false;      // internal x, v, F, lists belong to the last MD call
   long long launches = 0;     // kernels launched (graph replays add their kernel count)
+  cudaEvent_t sub_ev[2] = {nullptr, nullptr};  // set only inside dp_phase_times: kernel-level split
   cudaGraphExec_t graph_exec = nullptr;
   int graph_key[4] = {0, 0, 0, 0};
 };

@@ -884,6 +884,7 @@ dp_status launch_mix_descriptor(Model* m, int N) {
   const int grid = num_sms() * blocks_per_sm(fn, kRows, kFwdSmem, kTmemCols);
   if (f16) k_mix_embed_fwd<true><<<grid, kRows, kFwdSmem, m->stream>>>(a);
   else k_mix_embed_fwd<false><<<grid, kRows, kFwdSmem, m->stream>>>(a);
+  if (m->sub_ev[0]) DP_CUDA_TRY(m, cudaEventRecord(m->sub_ev[0], m->stream));
   if (f16)
     k_mix_descriptor<true><<<std::min(N, 4 * num_sms()), 128, 0, m->stream>>>(
         N, m->ntypes, 1.f / (float)m->S, m->Tseg, static_cast<float*>(m->Tm), static_cast<unsigned short*>(m->Dm));
@@ -901,6 +902,7 @@ dp_status launch_mix_embed_backward(Model* m, int N) {
                                                               static_cast<const float*>(m->dD),
                                                               static_cast<float4*>(m->dTm));
   DP_CUDA_TRY(m, cudaMemsetAsync(m->vir_atom, 0, sizeof(double) * 9 * (size_t)N, m->stream));
+  if (m->sub_ev[1]) DP_CUDA_TRY(m, cudaEventRecord(m->sub_ev[1], m->stream));
   MixArgs a = make_mix_args(m, N);
   const bool f16 = m->prec == DP_MIX_FP16;
   const void* fn = f16 ? reinterpret_cast<const void*>(k_mix_embed_bwd<true>)
