@@ -303,6 +303,9 @@ def run_mine(args, world, rank, local):
         # FP64 comparison (speed and error) on the same configuration
         if not args.no_fp64 and prec != "fp64":
             extra["fp64"] = fp64_compare(args, s, w, v0, m, stream)
+        # batched replicas (dp_md_run_batch)
+        if args.batch_steps > 0:
+            extra["batch"] = batch_leg(args, stream)
         # end-to-end through the public API with host buffers
         extra["e2e"] = e2e(m, s, stream, args.e2e_steps)
         # CPU oracle baseline
@@ -328,6 +331,40 @@ def run_mine(args, world, rank, local):
                 "gpu_launches": launches, "clocks": ck}
         line.update(extra)
         print(json.dumps(line), flush=True)
+
+
+def batch_leg(args, stream):
+    """256 water replicas of 32..2048 molecules (96..6,144 atoms each) advanced together by
+    dp_md_run_batch: one launch per phase for all boxes, replayed from a CUDA graph."""
+    import torch
+    import paper_2410_22867_gb300 as dp
+    from paper_2410_22867_gb300 import synth
+    reps = synth.water_replicas(256, 4)
+    w = synth.water_weights(1001)
+    coords, types, offs, boxes = synth.concat(reps)
+    v0 = np.concatenate([synth.maxwell_boltzmann(s.masses()[s.types], 300.0, 1000 + r) for r, s in enumerate(reps)])
+    N = len(types)
+    with torch.cuda.stream(stream):
+        m = dp.DPModel(w, args.precision, max_atoms=N, max_replicas=len(reps), skin=2.0, stream=stream)
+        x = torch.tensor(coords, device="cuda")
+        v = torch.tensor(v0, device="cuda")
+        t = torch.tensor(types, device="cuda")
+        st = m.md_state(x, v, t, boxes, reps[0].masses(), atom_offsets=offs, rebuild_every=REBUILD)
+        m.md_run_batch(st, DT_FS, 3)
+        st.resume = 1
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        m.md_run_batch(st, DT_FS, args.batch_steps, sync=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        m.sync()
+        ms = ev0.elapsed_time(ev1) / args.batch_steps
+        m.close()
+    return {"workload": f"256 H2O replicas, 32..2048 molecules each ({N} atoms), r_c 6 A, sel 46/92, "
+                        f"NVE dt 0.5 fs, rebuild every {REBUILD} steps",
+            "value": N / (ms * 1e-3), "unit": "atom-steps/s", "ms_per_step": ms, "steps": args.batch_steps,
+            "replicas": len(reps), "natoms": N}
 
 
 def fp64_compare(args, s, w, v0, m_mixed, stream):
@@ -405,6 +442,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--phase-repeats", type=int, default=10)
+    ap.add_argument("--batch-steps", type=int, default=22)  # + 3 warm-up: before the first collapse (step ~35)
     ap.add_argument("--no-fp64", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -146,9 +146,12 @@ typedef struct {
 dp_status dp_verlet_step(dp_model* m, dp_md_state* st, double dt_fs, int nsteps, int capture_graph);
 
 /*
- * dp_md_run_batch -- dp_verlet_step for many replicas of uneven size in one
- * launch per phase (persistent kernels over (replica, atom) work), always under
- * a captured CUDA graph, with tile shapes chosen by the autotuner on first use.
+ * dp_md_run_batch -- dp_verlet_step for many replicas of uneven size (st->nrep
+ * boxes, atoms concatenated by st->atom_offsets).  Every phase is one launch over
+ * the atoms and neighbour rows of all replicas (the kernels walk the concatenated
+ * arrays; the grids follow from the kernels' occupancy), and the steps between
+ * neighbour rebuilds always run as a captured CUDA graph.  Energies, kinetic
+ * energies and virials are reported per replica.
  */
 dp_status dp_md_run_batch(dp_model* m, dp_md_state* st, double dt_fs, int nsteps);
 
