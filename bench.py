@@ -149,13 +149,21 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """The largest of the ranks' values (timed regions: the slowest rank sets the time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_rate(world, natoms_per_rank, steps, t_ms):
+    """Whole-job atom-steps/s: every rank advances its own replica of natoms_per_rank atoms
+    for `steps` steps; t_ms is the max over ranks of the timed region."""
+    return world * natoms_per_rank * steps / (t_ms * 1e-3)
 
 
 def oracle_rate(name, seconds_target=None, nsteps=1):
@@ -289,7 +297,7 @@ def run_mine(args, world, rank, local):
         t_ms = max_over_ranks(ev0.elapsed_time(ev1), world)
         launches = m.kernel_launches() - launches0
         ms_step = t_ms / args.steps
-        value = world * N * args.steps / (t_ms * 1e-3)
+        value = aggregate_rate(world, N, args.steps, t_ms)
         # [format, descriptor phase, fitting, embedding-backward phase, total, embedding forward
         #  kernel, embedding backward kernel] from events on the model's stream
         phases = m.phase_times(args.phase_repeats)
