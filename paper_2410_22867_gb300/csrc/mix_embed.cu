@@ -765,38 +765,48 @@ __global__ void k_scan_fix(int N, int nblk, int* rowoff, const int* blk) {
   if (i < N) rowoff[(size_t)tj * (N + 1) + i] += off;
 }
 
-// T = sum over neighbour types of the partial sums, scaled by 1/S; D = T^T T[:, :16]
-// (fp32 copy for the fitting net).
+// T = sum over neighbour types of the partial sums, scaled by 1/S (kept in FP32 for the
+// dE/dT kernel); D = T^T T[:, :16] in 16 bits for the fitting net.  One warp per atom: T
+// (float4 loads) in shared memory, then lane -> rows a = lane, lane + 32, ... of D (16
+// values, two 16-byte stores).
+constexpr int kDescWarps = 8;
+
 template <bool F16>
-__global__ void k_mix_descriptor(int N, int ntypes, float invS, const float* __restrict__ Tseg, float* Tm,
-                                 unsigned short* Dm) {
-  __shared__ float sT[400];
-  for (int i = blockIdx.x; i < N; i += gridDim.x) {
-    for (int q = threadIdx.x; q < 400; q += blockDim.x) {
-      float v = 0.f;
-      for (int tj = 0; tj < ntypes; ++tj) v += Tseg[((size_t)tj * N + i) * 400 + q];
-      v *= invS;
-      sT[q] = v;
-      Tm[(size_t)i * 400 + q] = v;
+__global__ void __launch_bounds__(32 * kDescWarps) k_mix_descriptor(int N, int ntypes, float invS,
+                                                                   const float* __restrict__ Tseg, float* Tm,
+                                                                   unsigned short* Dm) {
+  __shared__ __align__(16) float sT[kDescWarps][400];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float* T = sT[w];
+  for (int i = blockIdx.x * kDescWarps + w; i < N; i += gridDim.x * kDescWarps) {
+    for (int q = lane; q < 100; q += 32) {
+      float4 v = reinterpret_cast<const float4*>(Tseg + (size_t)i * 400)[q];
+      for (int tj = 1; tj < ntypes; ++tj) {
+        const float4 u = reinterpret_cast<const float4*>(Tseg + ((size_t)tj * N + i) * 400)[q];
+        v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
+      }
+      v.x *= invS; v.y *= invS; v.z *= invS; v.w *= invS;
+      reinterpret_cast<float4*>(T)[q] = v;
+      reinterpret_cast<float4*>(Tm + (size_t)i * 400)[q] = v;
     }
-    __syncthreads();
-    for (int q = threadIdx.x; q < kN3; q += blockDim.x) {
+    __syncwarp();
+    for (int aa = lane; aa < kN3; aa += 32) {
       float out[kM2];
 #pragma unroll
       for (int b = 0; b < kM2; ++b) {
         float v = 0.f;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) v = fmaf(sT[c * kN3 + q], sT[c * kN3 + b], v);
+        for (int c = 0; c < 4; ++c) v = fmaf(T[c * kN3 + aa], T[c * kN3 + b], v);
         out[b] = v;
       }
       uint32_t pk[8];
 #pragma unroll
       for (int h = 0; h < 8; ++h) pk[h] = tc::pack2<F16>(out[2 * h], out[2 * h + 1]);
-      uint4* dst = reinterpret_cast<uint4*>(Dm + (size_t)i * kKD + q * kM2);
+      uint4* dst = reinterpret_cast<uint4*>(Dm + (size_t)i * kKD + aa * kM2);
       dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
       dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
@@ -885,11 +895,12 @@ dp_status launch_mix_descriptor(Model* m, int N) {
   if (f16) k_mix_embed_fwd<true><<<grid, kRows, kFwdSmem, m->stream>>>(a);
   else k_mix_embed_fwd<false><<<grid, kRows, kFwdSmem, m->stream>>>(a);
   if (m->sub_ev[0]) DP_CUDA_TRY(m, cudaEventRecord(m->sub_ev[0], m->stream));
+  const int dgrid = std::max(1, std::min((N + kDescWarps - 1) / kDescWarps, 8 * num_sms()));
   if (f16)
-    k_mix_descriptor<true><<<std::min(N, 4 * num_sms()), 128, 0, m->stream>>>(
+    k_mix_descriptor<true><<<dgrid, 32 * kDescWarps, 0, m->stream>>>(
         N, m->ntypes, 1.f / (float)m->S, m->Tseg, static_cast<float*>(m->Tm), static_cast<unsigned short*>(m->Dm));
   else
-    k_mix_descriptor<false><<<std::min(N, 4 * num_sms()), 128, 0, m->stream>>>(
+    k_mix_descriptor<false><<<dgrid, 32 * kDescWarps, 0, m->stream>>>(
         N, m->ntypes, 1.f / (float)m->S, m->Tseg, static_cast<float*>(m->Tm), static_cast<unsigned short*>(m->Dm));
   m->launches += 4;
   DP_LAUNCH_CHECK(m);

@@ -132,8 +132,10 @@ __global__ void k_load_positions(const double* __restrict__ coords, const int* _
 }
 
 // ------------------------------------------------------------------ cells
-__global__ void k_wrap_bin(int N, const int* __restrict__ irep, const RepGeom* __restrict__ geom, dvec4* x,
-                           dvec4* xref, float4* xf, float4* delta, int* cell_of, int* cell_count) {
+// xf.w carries the atom's type (bit pattern), read by the Verlet-list gather.
+__global__ void k_wrap_bin(int N, const int* __restrict__ irep, const int* __restrict__ itype,
+                           const RepGeom* __restrict__ geom, dvec4* x, dvec4* xref, float4* xf, float4* delta,
+                           int* cell_of, int* cell_count) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
   const RepGeom& g = geom[irep[k]];
@@ -142,7 +144,7 @@ __global__ void k_wrap_bin(int N, const int* __restrict__ irep, const RepGeom* _
   dvec4 q = make_dvec4(w[0], w[1], w[2], 0.0);
   x[k] = q;
   xref[k] = q;
-  xf[k] = make_float4((float)w[0], (float)w[1], (float)w[2], 0.f);
+  xf[k] = make_float4((float)w[0], (float)w[1], (float)w[2], __int_as_float(itype[k]));
   delta[k] = make_float4(0.f, 0.f, 0.f, 0.f);
   int c[3];
   for (int a = 0; a < 3; ++a) {
@@ -211,9 +213,26 @@ struct VerletArgs {
 
 constexpr int kVerletWarps = 4;
 
+// d = (x_j + n L) - x_i in FP64, round to nearest (no FMA).
+__device__ __forceinline__ void pair_vec64(const dvec4& xi, const dvec4& xj, int nx, int ny, int nz, const double* L,
+                                           double* d) {
+  d[0] = __dsub_rn(__dadd_rn(xj.x, __dmul_rn((double)nx, L[0])), xi.x);
+  d[1] = __dsub_rn(__dadd_rn(xj.y, __dmul_rn((double)ny, L[1])), xi.y);
+  d[2] = __dsub_rn(__dadd_rn(xj.z, __dmul_rn((double)nz, L[2])), xi.z);
+}
+
+// Verlet list of atom i (one warp per atom).  The list only has to contain every pair
+// within r_c + skin (the per-step format keeps exactly the pairs within r_c, with an exact
+// FP64 test near the cutoff), so a pair is taken when its FP32 r^2 is below (r_c + skin)^2
+// plus a band wider than the FP32 rounding error: no FP64 in the candidate loop.  The
+// stencil's cells are taken 32 at a time; their candidates form one flat range that the
+// lanes walk two at a time (independent gathers in flight).  Keys (j, image) are sorted per
+// neighbour type in shared memory, which gives the canonical order.
 __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
   extern __shared__ unsigned long long keys_all[];
   __shared__ int cnt[kVerletWarps][kMaxTypes];
+  __shared__ int s_beg[kVerletWarps][32], s_off[kVerletWarps][32], s_img[kVerletWarps][32];
+  __shared__ float s_sh[kVerletWarps][32][3];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int i = blockIdx.x * kVerletWarps + w;
   if (i >= a.N) return;
@@ -224,56 +243,89 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
   const dvec4 xi = a.x[i];
   const float4 xfi = a.xf[i];
   const int cid = a.cell_of[i];
-  int rel = cid - g.cell_off;
-  int ci[3] = {rel / (g.nc[1] * g.nc[2]), (rel / g.nc[2]) % g.nc[1], rel % g.nc[2]};
+  const int rel = cid - g.cell_off;
+  const int ci[3] = {rel / (g.nc[1] * g.nc[2]), (rel / g.nc[2]) % g.nc[1], rel % g.nc[2]};
   const unsigned lt = (1u << lane) - 1u;
-  for (int ox = -g.m[0]; ox <= g.m[0]; ++ox)
-    for (int oy = -g.m[1]; oy <= g.m[1]; ++oy)
-      for (int oz = -g.m[2]; oz <= g.m[2]; ++oz) {
-        int v[3] = {ci[0] + ox, ci[1] + oy, ci[2] + oz}, n[3], cc[3];
-        for (int q = 0; q < 3; ++q) {
-          n[q] = floor_div(v[q], g.nc[q]);
-          cc[q] = v[q] - n[q] * g.nc[q];
-        }
-        int c = g.cell_off + (cc[0] * g.nc[1] + cc[1]) * g.nc[2] + cc[2];
-        float sh[3] = {(float)n[0] * g.Lf[0], (float)n[1] * g.Lf[1], (float)n[2] * g.Lf[2]};
-        bool self_img = (n[0] == 0 && n[1] == 0 && n[2] == 0);
-        int beg = a.cell_start[c], end = a.cell_start[c + 1];
-        for (int base = beg; base < end; base += 32) {
-          int idx = base + lane;
-          bool acc = false;
-          int j = -1, tj = 0;
-          if (idx < end) {
-            j = a.cell_atoms[idx];
-            if (!(self_img && j == i)) {
-              float4 xfj = a.xf[j];
-              float dx = (xfj.x + sh[0]) - xfi.x, dy = (xfj.y + sh[1]) - xfi.y, dz = (xfj.z + sh[2]) - xfi.z;
-              float r2f = dx * dx + dy * dy + dz * dz;
-              if (r2f < a.rcs2_hi) {
-                double d[3];
-                double r2 = exact_r2(xi, a.x[j], n[0], n[1], n[2], g.L, d);
-                acc = r2 < a.rcs2;
-              }
-              tj = a.itype[j];
-            }
-          }
-          for (int t = 0; t < a.ntypes; ++t) {
-            unsigned mask = __ballot_sync(0xffffffffu, acc && tj == t);
-            if (mask == 0u) continue;
-            int start = cnt[w][t];
-            if (acc && tj == t) {
-              int pos = start + __popc(mask & lt);
-              int capP = a.buf_off[t + 1] - a.buf_off[t];
-              if (pos < capP)
-                keys[a.buf_off[t] + pos] = ((unsigned long long)(unsigned)j << 32) |
-                                           (unsigned)pack_img(n[0], n[1], n[2]);
-            }
-            __syncwarp();
-            if (lane == 0) cnt[w][t] = start + __popc(mask);
-            __syncwarp();
-          }
-        }
+  const int sy = 2 * g.m[1] + 1, sz = 2 * g.m[2] + 1;
+  const int ncell = (2 * g.m[0] + 1) * sy * sz;
+  const int self_code = pack_img(0, 0, 0);
+
+  auto fetch = [&](int q, int total, int nb, bool& acc, int& j, int& tj, int& code) {
+    acc = false; j = -1; tj = 0; code = 0;
+    if (q >= total) return;
+    int lo = 0, hi = nb - 1;  // the batch cell holding flat index q
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_off[w][mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    j = a.cell_atoms[s_beg[w][lo] + q - s_off[w][lo]];
+    code = s_img[w][lo];
+    if (j == i && code == self_code) return;
+    const float4 xfj = a.xf[j];
+    const float dx = (xfj.x + s_sh[w][lo][0]) - xfi.x;
+    const float dy = (xfj.y + s_sh[w][lo][1]) - xfi.y;
+    const float dz = (xfj.z + s_sh[w][lo][2]) - xfi.z;
+    acc = dx * dx + dy * dy + dz * dz < a.rcs2_hi;
+    tj = __float_as_int(xfj.w);
+  };
+  auto append = [&](bool acc, int j, int tj, int code) {
+    for (int t = 0; t < a.ntypes; ++t) {
+      const unsigned mask = __ballot_sync(0xffffffffu, acc && tj == t);
+      if (mask == 0u) continue;
+      const int start = cnt[w][t];
+      if (acc && tj == t) {
+        const int pos = start + __popc(mask & lt);
+        if (pos < a.buf_off[t + 1] - a.buf_off[t])
+          keys[a.buf_off[t] + pos] = ((unsigned long long)(unsigned)j << 32) | (unsigned)code;
       }
+      __syncwarp();
+      if (lane == 0) cnt[w][t] = start + __popc(mask);
+      __syncwarp();
+    }
+  };
+
+  for (int cb = 0; cb < ncell; cb += 32) {
+    const int k = cb + lane;
+    int beg = 0, num = 0, code = 0;
+    float sh[3] = {0.f, 0.f, 0.f};
+    if (k < ncell) {
+      const int o[3] = {k / (sy * sz) - g.m[0], (k / sz) % sy - g.m[1], k % sz - g.m[2]};
+      int n[3], cc[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int v = ci[q] + o[q];
+        n[q] = floor_div(v, g.nc[q]);
+        cc[q] = v - n[q] * g.nc[q];
+        sh[q] = (float)n[q] * g.Lf[q];
+      }
+      const int c = g.cell_off + (cc[0] * g.nc[1] + cc[1]) * g.nc[2] + cc[2];
+      beg = a.cell_start[c];
+      num = a.cell_start[c + 1] - beg;
+      code = pack_img(n[0], n[1], n[2]);
+    }
+    int incl = num;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    s_beg[w][lane] = beg;
+    s_off[w][lane] = incl - num;
+    s_img[w][lane] = code;
+    s_sh[w][lane][0] = sh[0]; s_sh[w][lane][1] = sh[1]; s_sh[w][lane][2] = sh[2];
+    __syncwarp();
+    const int nb = min(32, ncell - cb);
+    for (int base = 0; base < total; base += 64) {
+      bool acc0, acc1;
+      int j0, j1, t0, t1, c0, c1;
+      fetch(base + lane, total, nb, acc0, j0, t0, c0);
+      fetch(base + 32 + lane, total, nb, acc1, j1, t1, c1);
+      append(acc0, j0, t0, c0);
+      append(acc1, j1, t1, c1);
+    }
+    __syncwarp();
+  }
   __syncwarp();
   for (int t = 0; t < a.ntypes; ++t) {
     int nt_ = cnt[w][t];
@@ -310,7 +362,7 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
       int n0, n1, n2;
       unpack_img(code, n0, n1, n2);
       double d[3];
-      exact_r2(xi, a.x[j], n0, n1, n2, g.L, d);
+      pair_vec64(xi, a.x[j], n0, n1, n2, g.L, d);
       a.vl_j[ebase + q] = j;
       a.vl_img[ebase + q] = code;
       a.vl_d0[ebase + q] = make_float4((float)d[0], (float)d[1], (float)d[2], 0.f);
@@ -464,8 +516,8 @@ dp_status launch_rebuild(Model* m, int N) {
   cudaStream_t s = m->stream;
   DP_CUDA_TRY(m, cudaMemsetAsync(m->cell_count, 0, sizeof(int) * m->ncells, s));
   DP_CUDA_TRY(m, cudaMemsetAsync(m->cell_fill, 0, sizeof(int) * m->ncells, s));
-  k_wrap_bin<<<cdiv(N, 256), 256, 0, s>>>(N, m->irep, m->geom, m->x, m->xref, m->xf, m->delta, m->cell_of,
-                                          m->cell_count);
+  k_wrap_bin<<<cdiv(N, 256), 256, 0, s>>>(N, m->irep, m->itype, m->geom, m->x, m->xref, m->xf, m->delta,
+                                          m->cell_of, m->cell_count);
   k_scan_cells<<<1, 1024, 0, s>>>(m->ncells, m->cell_count, m->cell_start);
   k_fill_cells<<<cdiv(N, 256), 256, 0, s>>>(N, m->cell_of, m->cell_start, m->cell_fill, m->cell_atoms);
   VerletArgs a;
