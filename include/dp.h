@@ -205,7 +205,9 @@ long long dp_kernel_launches(const dp_model* m);
 /*
  * dp_selftest -- built-in check of the tensor-core operand layouts on the current
  * device: runs one tcgen05 MMA of a known small-integer problem (case `which`:
- * 0..4 = shapes N 64/112/240/32/160, bf16 or fp16 operands) and writes
+ * 0..4 = shapes N 64/112/240/32/160, bf16 or fp16 operands, both K-major;
+ * 5..7 = K 64 with an MN-major B (N 64), an MN-major A (N 64), or both MN-major
+ * (N 128)) and writes
  * result[0] = max |error| against the exact product, result[1] = max |value|.
  * Returns DP_ERR_UNSUPPORTED on a device without tcgen05.
  */
@@ -217,7 +219,7 @@ dp_status dp_selftest(int which, double* result);
  * health check of the library for callers that cannot allocate (a process whose
  * device memory already belongs to its own pool, or a monitor that must not
  * trigger the device-wide wait of cudaFree, which dp_selftest calls).
- *   which[ncases]      host: case numbers 0..4, as for dp_selftest.
+ *   which[ncases]      host: case numbers 0..4 (the K-major cases of dp_selftest).
  *   ncases             0..DP_SELFTEST_NOALLOC_MAX_CASES; 0 performs only the set-up.
  *   results[2*ncases]  host, caller-owned: per case max |error| and max |value|.
  * Scratch: 16 bytes per case in a fixed 256-byte device array inside the library

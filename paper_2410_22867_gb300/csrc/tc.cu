@@ -90,6 +90,94 @@ __global__ void __launch_bounds__(128) k_mma_selftest(float* out, int* err) {
   if (w == 0) tc::tmem_dealloc(tmem, 256);
 }
 
+// As k_mma_selftest with K = 64 and either operand stored MN-major (rows = K, 64-wide
+// MN blocks 8 KB apart), read through the MN-major descriptor and the transpose bits.
+template <int N, bool F16, bool AMN, bool BMN>
+__global__ void __launch_bounds__(128) k_mma_selftest_mn(float* out, int* err) {
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
+  unsigned char* sm = sm_raw + ((1024u - (tc::smem_u32(sm_raw) & 1023u)) & 1023u);
+  unsigned char* A = sm;              // 16 KB
+  unsigned char* B = sm + 16384;      // up to 16 KB
+  constexpr uint32_t kLbo = 8192;     // 64 K-rows x 128 B per 64-wide MN block
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tslot;
+  const int t = threadIdx.x, w = t >> 5;
+  auto aval = [](int r, int k) { return (float)(((r * 7 + k * 3) % 17) - 8) * 0.125f; };
+  auto bval = [](int n, int k) { return (float)(((n * 5 + k * 11) % 13) - 6) * 0.25f; };
+  for (int k = 0; k < 64; ++k) {
+    const float v = aval(t, k);
+    const uint32_t bits = tc::pack2<F16>(v, 0.f) & 0xFFFFu;
+    const uint32_t off = AMN ? tc::sw128_mn_off(t, k, kLbo) : tc::sw128_off(t, k & ~7) + (k & 7) * 2;
+    *reinterpret_cast<unsigned short*>(A + off) = (unsigned short)bits;
+  }
+  for (int n = t; n < N; n += 128)
+    for (int k = 0; k < 64; ++k) {
+      const uint32_t bits = tc::pack2<F16>(bval(n, k), 0.f) & 0xFFFFu;
+      const uint32_t off = BMN ? tc::sw128_mn_off(n, k, kLbo) : tc::sw128_off(n, k & ~7) + (k & 7) * 2;
+      *reinterpret_cast<unsigned short*>(B + off) = (unsigned short)bits;
+    }
+  if (t == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::mbar_fence_init();
+  }
+  if (w == 0) {
+    tc::tmem_alloc(&tslot, 128);
+    tc::tmem_relinquish();
+  }
+  tc::fence_async_smem();
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tslot;
+  if (t == 0) {
+    constexpr uint32_t idesc = tc::idesc_mn(tc::idesc_f16(128, N, F16), AMN, BMN);
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t as = tc::smem_u32(A) + (AMN ? 2048u * k : 32u * k);
+      const uint32_t bs = tc::smem_u32(B) + (BMN ? 2048u * k : 32u * k);
+      const uint64_t ad = AMN ? tc::sdesc_sw128_mn(as, kLbo) : tc::sdesc_sw128(as);
+      const uint64_t bd = BMN ? tc::sdesc_sw128_mn(bs, kLbo) : tc::sdesc_sw128(bs);
+      tc::mma_f16(tmem, ad, bd, idesc, k > 0 ? 1u : 0u);
+    }
+    tc::mma_commit(&bar);
+  }
+  bool ok = tc::mbar_wait(&bar, 0, err);
+  tc::tc_fence_after();
+  float emax = 0.f, rmax = 0.f;
+  if (ok) {
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(32 * w) << 16) + c0, v);
+      tc::tmem_wait_ld();
+      for (int u = 0; u < 16; ++u) {
+        float ref = 0.f;
+        for (int k = 0; k < 64; ++k) ref += aval(t, k) * bval(c0 + u, k);
+        emax = fmaxf(emax, fabsf(v[u] - ref));
+        rmax = fmaxf(rmax, fabsf(ref));
+      }
+    }
+  } else {
+    emax = 1e30f;
+  }
+  atomicMax(reinterpret_cast<int*>(out), __float_as_int(emax));
+  atomicMax(reinterpret_cast<int*>(out + 1), __float_as_int(rmax));
+  tc::tc_fence_before();
+  __syncthreads();
+  if (w == 0) tc::tmem_dealloc(tmem, 128);
+}
+
+template <int N, bool F16, bool AMN, bool BMN>
+dp_status run_selftest_mn(float* dout, int* derr, float* host) {
+  // operands need 32 KB; the window is sized so that any misread stride stays inside it
+  const size_t smem = 64 * 1024 + 1024;
+  const void* fn = reinterpret_cast<const void*>(k_mma_selftest_mn<N, F16, AMN, BMN>);
+  if (ensure_smem(fn, smem) != cudaSuccess) return DP_ERR_CUDA;
+  if (cudaMemset(dout, 0, 8) != cudaSuccess) return DP_ERR_CUDA;
+  k_mma_selftest_mn<N, F16, AMN, BMN><<<1, 128, smem>>>(dout, derr);
+  if (cudaDeviceSynchronize() != cudaSuccess) return DP_ERR_CUDA;
+  if (cudaMemcpy(host, dout, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return DP_ERR_CUDA;
+  return DP_OK;
+}
+
 template <int N, int KB, bool F16>
 dp_status run_selftest(float* dout, int* derr, float* host) {
   size_t smem = (size_t)KB * 128 * 128 + (size_t)KB * N * 128 + 1024;
@@ -126,6 +214,9 @@ extern "C" dp_status dp_selftest(int which, double* result) {
     case 2: st = run_selftest<240, 4, false>(d, e, h); break;
     case 3: st = run_selftest<32, 1, true>(d, e, h); break;
     case 4: st = run_selftest<160, 4, true>(d, e, h); break;
+    case 5: st = run_selftest_mn<64, false, false, true>(d, e, h); break;
+    case 6: st = run_selftest_mn<64, true, true, false>(d, e, h); break;
+    case 7: st = run_selftest_mn<128, true, true, true>(d, e, h); break;
     default: break;
   }
   int eh = 0;

@@ -107,14 +107,38 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   return d;
 }
 
+// Shared-memory matrix descriptor for an MN-major operand, 128-byte swizzle: rows are K
+// (8-row groups SBO = 1024 B apart), each 128-byte row holds 64 consecutive M (or N)
+// elements; further 64-element MN blocks lie `lbo` bytes apart.  One K step of 16 is two
+// row groups (2048 B).
+__device__ __forceinline__ uint64_t sdesc_sw128_mn(uint32_t saddr, uint32_t lbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;        // leading byte offset: next 64-wide MN block
+  d |= (uint64_t)(1024 >> 4) << 32;                   // stride byte offset: 8 K-rows x 128 B
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Byte offset of element (mn, k) of an MN-major SW128 operand (64-wide MN blocks `lbo` apart).
+__host__ __device__ __forceinline__ uint32_t sw128_mn_off(int mn, int k, uint32_t lbo) {
+  return (uint32_t)(mn >> 6) * lbo + (uint32_t)(k >> 3) * 1024u + (uint32_t)(k & 7) * 128u +
+         (uint32_t)((((mn & 63) >> 3) ^ (k & 7)) << 4) + (uint32_t)(mn & 7) * 2u;
+}
+
 // Instruction descriptor, kind::f16: D fp32, A/B bf16 (ab_f16 = false) or fp16,
-// both K-major, shape M x N.
+// both K-major, shape M x N.  idesc_mn() sets the MN-major (transposed) bits.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool ab_f16) {
   return (1u << 4)                                   // D format F32
          | ((ab_f16 ? 0u : 1u) << 7)                 // A format: 0 F16, 1 BF16
          | ((ab_f16 ? 0u : 1u) << 10)                // B format
          | ((uint32_t)(N >> 3) << 17)                // N / 8
          | ((uint32_t)(M >> 4) << 24);               // M / 16
+}
+
+__host__ __device__ constexpr uint32_t idesc_mn(uint32_t idesc, bool a_mn, bool b_mn) {
+  return idesc | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16);
 }
 
 // D[tmem] (+)= A[smem] * B[smem]^T, one instruction (K = 16).  Issued by one thread.

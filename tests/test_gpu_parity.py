@@ -272,8 +272,9 @@ def test_md_skin_exceeded_is_reported(dp):
 
 
 # ------------------------------------------------------------------ mixed precision (tensor cores)
-@pytest.mark.parametrize("which", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("which", [0, 1, 2, 3, 4, 5, 6, 7])
 def test_tensor_core_layout_selftest(dp, which):
+    # 0-4: K-major operands of several shapes; 5-7: MN-major B, MN-major A, both MN-major
     err, vmax = dp.selftest(which)
     assert vmax > 1.0
     assert err == 0.0
