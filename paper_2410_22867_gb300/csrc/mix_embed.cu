@@ -178,37 +178,6 @@ __device__ void load_fwd_weights(const float* __restrict__ W, unsigned char* sB2
   }
 }
 
-// Backward operand blocks: W3 as [64 (m) x 112 (a)] in two K blocks, W2 as [32 (k) x 64 (m)].
-template <bool F16>
-__device__ void load_bwd_weights(const float* __restrict__ W, unsigned char* sB3b, unsigned char* sB2b) {
-  const int t = threadIdx.x;
-  for (int q = t; q < 2 * 64 * 8; q += kRows) {
-    int kb = q / 512, rem = q % 512;
-    int m = rem >> 3, k0 = (rem & 7) * 8;
-    uint32_t p[4];
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      int a0 = kb * 64 + k0 + 2 * h;
-      float x0 = (m < kN2 && a0 < kN3) ? W[kEW3 + m * kN3 + a0] : 0.f;
-      float x1 = (m < kN2 && a0 + 1 < kN3) ? W[kEW3 + m * kN3 + a0 + 1] : 0.f;
-      p[h] = tc::pack2<F16>(x0, x1);
-    }
-    tc::st_chunk(sB3b + kb * 64 * 128, m, k0, make_uint4(p[0], p[1], p[2], p[3]));
-  }
-  for (int q = t; q < 32 * 8; q += kRows) {
-    int k = q >> 3, m0 = (q & 7) * 8;
-    uint32_t p[4];
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      int m = m0 + 2 * h;
-      float x0 = (k < kN1 && m < kN2) ? W[kEW2 + k * kN2 + m] : 0.f;
-      float x1 = (k < kN1 && m + 1 < kN2) ? W[kEW2 + k * kN2 + m + 1] : 0.f;
-      p[h] = tc::pack2<F16>(x0, x1);
-    }
-    tc::st_chunk(sB2b, k, m0, make_uint4(p[0], p[1], p[2], p[3]));
-  }
-}
-
 // Per-row front end shared by forward and backward: environment row and layer 1.
 struct RowFront {
   float d[3], R[4], r, sw, dsw;
@@ -484,17 +453,70 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
 }
 
 // ------------------------------------------------------------------ backward
+// Layer-3 column order of the backward: feature q < 50 at column q, q >= 50 at column q + 14,
+// so that the two features q = m and q = m + 50 that share the residual h2[m] sit 64 columns
+// apart (16-column aligned TMEM loads, N = 128 with zero padding).
+__device__ __forceinline__ int bwd_q_of(int n) {
+  return n < kN2 ? n : (n >= 64 && n < 64 + kN2 ? n - 14 : -1);
+}
+
+// Backward operand blocks of pair (ti, tj): B2 as in the forward ([64 x 64], rows = layer-2
+// unit, K = layer-1 unit) and B3 with 128 rows in the column order above (K = layer-2
+// unit).  The transposed products dz3 W3^T and dz2 W2^T read the same two blocks as MN-major
+// operands.  small: W1, b1, b2, b3 (b3 by feature index).
 template <bool F16>
-__global__ void __launch_bounds__(kRows, 2) k_mix_embed_bwd(MixArgs a) {
+__device__ void load_bwd_ops(const float* __restrict__ W, unsigned char* sB2, unsigned char* sB3, float* small) {
+  const int t = threadIdx.x;
+  for (int q = t; q < 64 * 8; q += kRows) {
+    const int n = q >> 3, k0 = (q & 7) * 8;
+    uint32_t p[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int k = k0 + 2 * h;
+      const float x0 = (n < kN2 && k < kN1) ? W[kEW2 + k * kN2 + n] : 0.f;
+      const float x1 = (n < kN2 && k + 1 < kN1) ? W[kEW2 + (k + 1) * kN2 + n] : 0.f;
+      p[h] = tc::pack2<F16>(x0, x1);
+    }
+    tc::st_chunk(sB2, n, k0, make_uint4(p[0], p[1], p[2], p[3]));
+  }
+  for (int q = t; q < 128 * 8; q += kRows) {
+    const int n = q >> 3, k0 = (q & 7) * 8;
+    const int f = bwd_q_of(n);
+    uint32_t p[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int k = k0 + 2 * h;
+      const float x0 = (f >= 0 && k < kN2) ? W[kEW3 + k * kN3 + f] : 0.f;
+      const float x1 = (f >= 0 && k + 1 < kN2) ? W[kEW3 + (k + 1) * kN3 + f] : 0.f;
+      p[h] = tc::pack2<F16>(x0, x1);
+    }
+    tc::st_chunk(sB3, n, k0, make_uint4(p[0], p[1], p[2], p[3]));
+  }
+  for (int q = t; q < 200; q += kRows) {
+    float v;
+    if (q < 25) v = W[kEW1 + q];
+    else if (q < 50) v = W[kEb1 + q - 25];
+    else if (q < 100) v = W[kEb2 + q - 50];
+    else v = W[kEb3 + q - 100];
+    small[q] = v;
+  }
+}
+
+// Embedding backward with recompute, prod_force and per-atom virial.  One row per thread and
+// TMEM lane; per tile four tensor-core products (z2 = h1 W2, z3 = h2 W3, dh2' = dz3 W3^T,
+// dh1' = dz2 W2^T; the last two read B3 / B2 MN-major).  The layer-3 epilogue takes the
+// features m and m + 50 together, so the residual part dG[m] + dG[m + 50] of dE/dh2 is final
+// when formed; it is parked in the TMEM columns of z3 just read, and added back after the
+// dh2' product.  dR_hat and dG use dE/dT and G in FP32 on the CUDA cores.
+template <bool F16>
+__global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
   extern __shared__ unsigned char sraw[];
   unsigned char* sm = align1024(sraw);
-  unsigned char* sA = sm;                          // 32 KB: h1 / h2 (block 0), dz3 (blocks 0-1), dz2 (block 0)
+  unsigned char* sA = sm;                          // 32 KB: h1 / h2 (blk 0), dz3 (blks 0-1), dz2 (blk 0)
   unsigned char* sB2 = sm + 32768;                 // 8 KB
-  unsigned char* sB3 = sB2 + 8192;                 // 14 KB
-  unsigned char* sB3b = sB3 + 14336;               // 16 KB (two K blocks of 64 rows)
-  unsigned char* sB2b = sB3b + 16384;              // 4 KB
-  float4* sdT = reinterpret_cast<float4*>(sB2b + 4096);  // [kMaxAtoms][100]
-  float* small = reinterpret_cast<float*>(sdT + kMaxAtoms * kN3);  // 200
+  unsigned char* sB3 = sB2 + 8192;                 // 16 KB (128 rows, backward column order)
+  float4* sdT = reinterpret_cast<float4*>(sB3 + 16384);              // [kMaxAtoms][100]
+  float* small = reinterpret_cast<float*>(sdT + kMaxAtoms * kN3);    // 200
   int* sRow = reinterpret_cast<int*>(small + 200);
   __shared__ uint64_t bar;
   __shared__ uint32_t tslot;
@@ -520,6 +542,10 @@ __global__ void __launch_bounds__(kRows, 2) k_mix_embed_bwd(MixArgs a) {
   walk_tables(a, s_tot, s_tiend);
   __syncthreads();
   Walk wk{0, 0, -1};
+  const uint32_t id64 = tc::idesc_f16(128, 64, F16);
+  const uint32_t id128 = tc::idesc_f16(128, 128, F16);
+  const uint32_t idH2 = tc::idesc_mn(tc::idesc_f16(128, 64, F16), false, true);
+  const uint32_t idH1 = tc::idesc_mn(tc::idesc_f16(128, 32, F16), false, true);
 
   for (int cur = c0; cur < c1 && ok;) {
     if (w == 0) locate_tile(a, cur, c0, c1, wk, s_tot, s_tiend, &sti, sRow);
@@ -527,9 +553,7 @@ __global__ void __launch_bounds__(kRows, 2) k_mix_embed_bwd(MixArgs a) {
     const TileInfo ti = sti;
     const int np = ti.ti * a.ntypes + ti.tj;
     if (np != pair) {
-      const float* W = a.w + (size_t)np * kEmbParams;
-      load_fwd_weights<F16>(W, sB2, sB3, small);
-      load_bwd_weights<F16>(W, sB3b, sB2b);
+      load_bwd_ops<F16>(a.w + (size_t)np * kEmbParams, sB2, sB3, small);
       pair = np;
     }
     const int natoms_tile = local_atom(sRow, ti.p + ti.nrows - 1) + 1;
@@ -548,107 +572,120 @@ __global__ void __launch_bounds__(kRows, 2) k_mix_embed_bwd(MixArgs a) {
     layer1<F16>(small, f.R[0], h1, sA, t);
     operand_barrier();
     if (t == 0) {
-      tc::mma_kblock(tmem, tc::smem_u32(sA), tc::smem_u32(sB2), tc::idesc_f16(128, 64, F16), false, 2);
+      tc::mma_kblock(tmem, tc::smem_u32(sA), tc::smem_u32(sB2), id64, false, 2);
       tc::mma_commit(&bar);
     }
+    __syncwarp();
     mma_sync_wait(&bar, phase, a.err, ok);
     layer2_epi<F16>(tl, small, h1, h2, sA, t);
     operand_barrier();
     if (t == 0) {
-      tc::mma_kblock(tmem, tc::smem_u32(sA), tc::smem_u32(sB3), tc::idesc_f16(128, 112, F16), false, 4);
+      tc::mma_kblock(tmem, tc::smem_u32(sA), tc::smem_u32(sB3), id128, false, 4);
       tc::mma_commit(&bar);
     }
+    __syncwarp();
     mma_sync_wait(&bar, phase, a.err, ok);
-    // layer-3 epilogue (backward): G, dR_hat, dG, dz3 = dG (1 - t3^2) into A (two K blocks)
+
+    // layer-3 epilogue over the feature pairs (m, m + 50): G, dR_hat, dG, dz3 -> sA (blk 0:
+    // column m, blk 1: column m + 64), residual dG[m] + dG[m + 50] -> TMEM column 64 + m
     float dR[4] = {0.f, 0.f, 0.f, 0.f};
-    float dh2[kN2];
-#pragma unroll
-    for (int m = 0; m < kN2; ++m) dh2[m] = 0.f;
     const float4* dTa = sdT + f.la * kN3;
 #pragma unroll
-    for (int c = 0; c < 7; ++c) {
-      float z[16];
-      tc::tmem_ld16(tl + 16 * c, z);
+    for (int c = 0; c < 4; ++c) {
+      float za[16], zb[16];
+      tc::tmem_ld16(tl + 16 * c, za);
+      tc::tmem_ld16(tl + 64 + 16 * c, zb);
       tc::tmem_wait_ld();
-      float dz[16];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int q = 16 * c + u;
-        dz[u] = 0.f;
-        if (q < kN3) {
-          const float t3 = tc::tanh_fast(z[u] + small[100 + q]);
-          const float G = h2[q % kN2] + t3;
-          const float4 d4 = dTa[q];
-          dR[0] = fmaf(d4.x, G, dR[0]);
-          dR[1] = fmaf(d4.y, G, dR[1]);
-          dR[2] = fmaf(d4.z, G, dR[2]);
-          dR[3] = fmaf(d4.w, G, dR[3]);
-          const float dG = f.R[0] * d4.x + f.R[1] * d4.y + f.R[2] * d4.z + f.R[3] * d4.w;
-          dz[u] = dG * (1.f - t3 * t3);
-          dh2[q % kN2] += dG;
+      for (int hh = 0; hh < 2; ++hh) {
+        float da[8], db[8], r[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int m = 16 * c + 8 * hh + u;
+          da[u] = db[u] = r[u] = 0.f;
+          if (m < kN2) {
+            const float ta = tc::tanh_fast(za[8 * hh + u] + small[100 + m]);
+            const float tb = tc::tanh_fast(zb[8 * hh + u] + small[150 + m]);
+            const float Ga = h2[m] + ta, Gb = h2[m] + tb;
+            const float4 pa = dTa[m], pb = dTa[m + kN2];
+            dR[0] = fmaf(pa.x, Ga, fmaf(pb.x, Gb, dR[0]));
+            dR[1] = fmaf(pa.y, Ga, fmaf(pb.y, Gb, dR[1]));
+            dR[2] = fmaf(pa.z, Ga, fmaf(pb.z, Gb, dR[2]));
+            dR[3] = fmaf(pa.w, Ga, fmaf(pb.w, Gb, dR[3]));
+            const float ga = f.R[0] * pa.x + f.R[1] * pa.y + f.R[2] * pa.z + f.R[3] * pa.w;
+            const float gb = f.R[0] * pb.x + f.R[1] * pb.y + f.R[2] * pb.z + f.R[3] * pb.w;
+            da[u] = ga * (1.f - ta * ta);
+            db[u] = gb * (1.f - tb * tb);
+            r[u] = ga + gb;
+          }
         }
-      }
-      // 16 values = two 8-element chunks of K block (16c / 64)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int k0 = 16 * c + 8 * h;
-        uint32_t p[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) p[v] = tc::pack2<F16>(dz[8 * h + 2 * v], dz[8 * h + 2 * v + 1]);
-        tc::st_chunk(sA + (k0 >> 6) * 16384, t, k0 & 63, make_uint4(p[0], p[1], p[2], p[3]));
+        const int k0 = 16 * c + 8 * hh;
+        tc::st_chunk(sA, t, k0, make_uint4(tc::pack2<F16>(da[0], da[1]), tc::pack2<F16>(da[2], da[3]),
+                                           tc::pack2<F16>(da[4], da[5]), tc::pack2<F16>(da[6], da[7])));
+        tc::st_chunk(sA + 16384, t, k0, make_uint4(tc::pack2<F16>(db[0], db[1]), tc::pack2<F16>(db[2], db[3]),
+                                                   tc::pack2<F16>(db[4], db[5]), tc::pack2<F16>(db[6], db[7])));
+        tc::tmem_st8(tl + 64 + k0, r);
       }
     }
+    tc::tmem_wait_st();
     operand_barrier();
-    // dh2 += dz3 W3^T  (N = 64 over m, K = 112 over a: two K blocks, the second with 48 used)
+    // dh2' = dz3 W3^T (B = the rows of B3 read MN-major: K = layer-3 column, N = layer-2 unit)
     if (t == 0) {
-      const uint32_t id = tc::idesc_f16(128, 64, F16);
-      tc::mma_kblock(tmem, tc::smem_u32(sA), tc::smem_u32(sB3b), id, false, 4);
-      tc::mma_kblock(tmem, tc::smem_u32(sA + 16384), tc::smem_u32(sB3b + 8192), id, true, 3);
+      for (int k = 0; k < 8; ++k) {
+        const uint64_t ad = tc::sdesc_sw128(tc::smem_u32(sA + (k >> 2) * 16384) + 32 * (k & 3));
+        const uint64_t bd = tc::sdesc_sw128_mn(tc::smem_u32(sB3) + 2048 * k, 8192);
+        tc::mma_f16(tmem, ad, bd, idH2, k > 0 ? 1u : 0u);
+      }
       tc::mma_commit(&bar);
     }
+    __syncwarp();
     mma_sync_wait(&bar, phase, a.err, ok);
+    // layer-2 backward: g2 = dh2' + residual, dz2 = g2 (1 - t2^2) -> sA; h2's residual into dh1
     float dh1[kN1];
 #pragma unroll
     for (int k = 0; k < kN1; ++k) dh1[k] = 0.f;
-    {
-      float dz2[64];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        float z[16];
-        tc::tmem_ld16(tl + 16 * c, z);
-        tc::tmem_wait_ld();
+    for (int c = 0; c < 4; ++c) {
+      float z[16], rr[16];
+      tc::tmem_ld16(tl + 16 * c, z);
+      tc::tmem_ld16(tl + 64 + 16 * c, rr);
+      tc::tmem_wait_ld();
+      float d2[16];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int m = 16 * c + u;
-          dz2[m] = 0.f;
-          if (m < kN2) {
-            const float g2 = z[u] + dh2[m];
-            const float t2 = h2[m] - h1[m % kN1];
-            dz2[m] = g2 * (1.f - t2 * t2);
-            dh1[m % kN1] += g2;
-          }
+      for (int u = 0; u < 16; ++u) {
+        const int m = 16 * c + u;
+        d2[u] = 0.f;
+        if (m < kN2) {
+          const float g2 = z[u] + rr[u];
+          const float t2 = h2[m] - h1[m % kN1];
+          d2[u] = g2 * (1.f - t2 * t2);
+          dh1[m % kN1] += g2;
         }
       }
 #pragma unroll
-      for (int k0 = 0; k0 < 64; k0 += 8) {
-        uint32_t p[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) p[v] = tc::pack2<F16>(dz2[k0 + 2 * v], dz2[k0 + 2 * v + 1]);
-        tc::st_chunk(sA, t, k0, make_uint4(p[0], p[1], p[2], p[3]));
-      }
+      for (int hh = 0; hh < 2; ++hh)
+        tc::st_chunk(sA, t, 16 * c + 8 * hh,
+                     make_uint4(tc::pack2<F16>(d2[8 * hh], d2[8 * hh + 1]), tc::pack2<F16>(d2[8 * hh + 2], d2[8 * hh + 3]),
+                                tc::pack2<F16>(d2[8 * hh + 4], d2[8 * hh + 5]),
+                                tc::pack2<F16>(d2[8 * hh + 6], d2[8 * hh + 7])));
     }
     operand_barrier();
-    // dh1 += dz2 W2^T  (N = 32 over k, K = 64 over m)
+    // dh1' = dz2 W2^T (B = the rows of B2 read MN-major: K = layer-2 unit, N = layer-1 unit)
     if (t == 0) {
-      tc::mma_kblock(tmem + 64, tc::smem_u32(sA), tc::smem_u32(sB2b), tc::idesc_f16(128, 32, F16), false, 4);
+      for (int k = 0; k < 4; ++k) {
+        const uint64_t ad = tc::sdesc_sw128(tc::smem_u32(sA) + 32 * k);
+        const uint64_t bd = tc::sdesc_sw128_mn(tc::smem_u32(sB2) + 2048 * k, 8192);
+        tc::mma_f16(tmem, ad, bd, idH1, k > 0 ? 1u : 0u);
+      }
       tc::mma_commit(&bar);
     }
+    __syncwarp();
     mma_sync_wait(&bar, phase, a.err, ok);
     float ds = 0.f;
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       float z[16];
-      tc::tmem_ld16(tl + 64 + 16 * c, z);
+      tc::tmem_ld16(tl + 16 * c, z);
       tc::tmem_wait_ld();
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
@@ -877,7 +914,7 @@ MixArgs make_mix_args(Model* m, int N) {
 }
 
 constexpr size_t kFwdSmem = 32768 + 8192 + 8192 + 14336 + 200 * 4 + 64 + 1024;
-constexpr size_t kBwdSmem = 32768 + 8192 + 14336 + 16384 + 4096 + kMaxAtoms * kN3 * 16 + 200 * 4 + 64 + 1024;
+constexpr size_t kBwdSmem = 32768 + 8192 + 16384 + kMaxAtoms * kN3 * 16 + 200 * 4 + 64 + 1024;
 
 }  // namespace
 
