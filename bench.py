@@ -210,7 +210,6 @@ N_SMS = 152
 # 32,000-atom copper capture, per real neighbour row; scaled to a launch by the row count.
 # Only valid while the kernel is unchanged since the capture (see profiles/).
 TRAFFIC_PER_ROW = {
-    ("embedding_backward", "mix_fp16"): (173.6896e6 + 5.020160e6) / 5726060,  # profiles/k_mix_embed_bwd_cu32k.md
     ("embedding_forward", "mix_fp16"): (95.655424e6 + 20.975872e6) / 5726060,  # profiles/k_mix_embed_fwd_cu32k.md
 }
 

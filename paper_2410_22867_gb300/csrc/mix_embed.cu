@@ -847,7 +847,8 @@ __global__ void __launch_bounds__(32 * kDescWarps) k_mix_descriptor(int N, int n
   }
 }
 
-// dT[c][a] = (1/S) (sum_b dD[a][b] T[c][b] + [a < 16] sum_a' dD[a'][a] T[c][a']), stored [N][100] float4.
+// dT[c][a] = (1/S) (sum_b dD[a][b] T[c][b] + [a < 16] sum_a' dD[a'][a] T[c][a']), stored [N][100] float4;
+// dD (dE/dD from the fitting kernel) is fp16.
 // One warp per atom: T (4 x 100) and dD (100 x 16, rows padded to 17 floats so that a
 // warp reading one column hits 32 banks) staged in shared memory; the second term's 64
 // outputs (c, a < 16) are split over the 32 lanes, two each.
@@ -855,7 +856,8 @@ constexpr int kDtWarps = 4;
 constexpr int kDtRow = kM2 + 1;
 
 __global__ void __launch_bounds__(32 * kDtWarps) k_mix_dT(int N, float invS, const float* __restrict__ Tm,
-                                                         const float* __restrict__ dD, float4* __restrict__ dT) {
+                                                         const unsigned short* __restrict__ dD,
+                                                         float4* __restrict__ dT) {
   __shared__ __align__(16) float sT[kDtWarps][400];
   __shared__ float sD[kDtWarps][kN3 * kDtRow];
   __shared__ float s2[kDtWarps][4 * kM2];
@@ -866,11 +868,17 @@ __global__ void __launch_bounds__(32 * kDtWarps) k_mix_dT(int N, float invS, con
   for (int i = blockIdx.x * kDtWarps + w; i < N; i += gridDim.x * kDtWarps) {
     const float4* Ti = reinterpret_cast<const float4*>(Tm + (size_t)i * 400);
     for (int q = lane; q < 100; q += 32) reinterpret_cast<float4*>(T)[q] = Ti[q];
-    const float4* Di = reinterpret_cast<const float4*>(dD + (size_t)i * kKD);
-    for (int q = lane; q < kKD / 4; q += 32) {
-      const float4 v = Di[q];
-      float* d = D + (q >> 2) * kDtRow + (q & 3) * 4;
-      d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+    const uint4* Di = reinterpret_cast<const uint4*>(dD + (size_t)i * kKD);  // fp16, 8 per load
+    for (int q = lane; q < kKD / 8; q += 32) {
+      const uint4 v = Di[q];
+      const uint32_t p[4] = {v.x, v.y, v.z, v.w};
+      float* d = D + (q >> 1) * kDtRow + (q & 1) * 8;
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const float2 f2 = __half22float2(*reinterpret_cast<const __half2*>(&p[h]));
+        d[2 * h] = f2.x;
+        d[2 * h + 1] = f2.y;
+      }
     }
     __syncwarp();
     {  // second term: lane -> a = lane % 16, c = lane / 16 and c + 2
@@ -947,7 +955,7 @@ dp_status launch_mix_descriptor(Model* m, int N) {
 dp_status launch_mix_embed_backward(Model* m, int N) {
   const int dt_grid = std::max(1, std::min((N + kDtWarps - 1) / kDtWarps, 5 * num_sms()));
   k_mix_dT<<<dt_grid, 32 * kDtWarps, 0, m->stream>>>(N, 1.f / (float)m->S, static_cast<const float*>(m->Tm),
-                                                              static_cast<const float*>(m->dD),
+                                                              static_cast<const unsigned short*>(m->dD),
                                                               static_cast<float4*>(m->dTm));
   DP_CUDA_TRY(m, cudaMemsetAsync(m->vir_atom, 0, sizeof(double) * 9 * (size_t)N, m->stream));
   if (m->sub_ev[1]) DP_CUDA_TRY(m, cudaEventRecord(m->sub_ev[1], m->stream));

@@ -15,6 +15,7 @@
 // "Split": x = x_hi + x_lo with both halves 16-bit, x*w ~ x_hi w_hi + x_hi w_lo +
 // x_lo w_hi, which keeps ~16 mantissa bits; rounding the 240 x 240 layers to plain
 // 16 bits biases E_i by ~1e-3 eV (bf16), above the 1e-4 eV/atom target.
+// dE/dD is written in fp16 for the dE/dT kernel.
 // The activation operand X (hi and lo) lives in shared memory, the FP32 residual
 // stream (h1, h2, dh2) in TMEM columns 256..495, the factors 1 - h1^2 and 1 - t2^2
 // in a small global scratch between forward and backward.  TMA loads run several
@@ -34,13 +35,16 @@ constexpr uint32_t kBlk = 16384;          // one [128 x 64] 16-bit operand block
 constexpr uint32_t kWB = 240 * 128;       // one [240 x 64] 16-bit weight block (30 KB)
 constexpr uint32_t kXHi = 0;              // X_hi: 4 blocks
 constexpr uint32_t kXLo = 4 * kBlk;       // X_lo: 4 blocks
-constexpr uint32_t kSt = 8 * kBlk;        // 60 KB: split weight hi + lo
-constexpr uint32_t kPrm = kSt + 2 * kWB;  // b1, b2, b3, w4
+constexpr uint32_t kSt = 8 * kBlk;        // 64 KB: four split staging slots
+constexpr uint32_t kSSlot = 128 * 128;    // split job: [128 x 64] 16-bit weight block (16 KB)
+constexpr int kSSlots = 4;
+constexpr uint32_t kPrm = kSt + kSSlots * kSSlot;  // b1, b2, b3, w4
 constexpr uint32_t kL1Slot = kBlk + kWB;  // L1 job: A block + W1T block (46 KB), slots over [0, kPrm)
 constexpr int kL1Slots = 4;
 constexpr uint32_t kB1Slot = kBChunk * 128;  // B1 job: W1 block [160 x 64] (20 KB), slots over [kXLo, kPrm)
 constexpr int kB1Slots = 6;
-constexpr int kSplitSlot = 6;             // barrier index of the split staging slot
+constexpr int kSplitSlot = 6;             // barrier index of the first split staging slot (6..9)
+constexpr int kSplitJobs = 16;            // per split GEMM: 4 K blocks x 2 N halves x {hi, lo}
 constexpr int kL1Jobs = kKD / 64;         // 25
 constexpr int kB1Jobs = 4 * (kKD / kBChunk);  // 40
 
@@ -60,16 +64,16 @@ struct FitArgs {
   long ebias_off;
   unsigned short* f1;      // [N][240] 16-bit: 1 - h1^2
   unsigned short* f2;      // [N][240] 16-bit: 1 - t2^2
-  float* dD;               // [N][1600]
+  unsigned short* dD;      // [N][1600] fp16
   double* e_atom;
   int* err;
 };
 
 // Staging slots: one full/empty mbarrier pair each; `uses` counts completed jobs per slot.
 struct Slots {
-  uint64_t* full;   // [8]: L1 0..3, B1 0..5, split hi 6, split lo 7
-  uint64_t* empty;  // [8]
-  uint32_t uses[8];
+  uint64_t* full;   // [10]: L1 0..3, B1 0..5, split 6..9
+  uint64_t* empty;  // [10]
+  uint32_t uses[10];
 };
 
 __device__ __forceinline__ unsigned char* align1k(unsigned char* p) {
@@ -167,13 +171,19 @@ struct Issuer {
     tc::mbar_arrive_expect_tx(&s->full[k], kB1Slot);
     tc::tma_load_2d(sm + kXLo + k * kB1Slot, &mp->W1[ty], &s->full[k], 64 * (j & 3), kBChunk * b1_chunk(j >> 2));
   }
-  // split job i of GEMM g: weight half (i & 1: 0 = hi, 1 = lo) of K block split_block(i / 2),
-  // into split slot i & 1 (hi slot at kSt, lo slot at kSt + kWB)
+  // split job i of GEMM g: weight half i & 1 (0 = hi, 1 = lo), N half (i >> 1) & 1 (rows 0..127
+  // or 128..255; rows past 240 are zero-filled by the TMA) of K block split_block(i >> 2),
+  // into split slot i & 3
   __device__ void load_split(int g, int i) {
-    const int k = kSplitSlot + (i & 1);
+    const int k = kSplitSlot + (i & 3);
     slot_acquire(*s, k, s->uses[k], err, *ok);
-    tc::mbar_arrive_expect_tx(&s->full[k], kWB);
-    tc::tma_load_2d(sm + kSt + (i & 1) * kWB, &mp->S[ty][g][i & 1], &s->full[k], 64 * split_block(i >> 1), 0);
+    tc::mbar_arrive_expect_tx(&s->full[k], kSSlot);
+    tc::tma_load_2d(sm + kSt + (i & 3) * kSSlot, &mp->S[ty][g][i & 1], &s->full[k], 64 * split_block(i >> 2),
+                    128 * ((i >> 1) & 1));
+  }
+  // the first three jobs of split GEMM g (issued under the preceding epilogue)
+  __device__ void prefetch_split(int g) {
+    for (int i = 0; i < kSSlots - 1; ++i) load_split(g, i);
   }
   // wait for the data of the oldest outstanding job in slot k and mark it consumed after the MMAs
   __device__ void consume_begin(int k) {
@@ -191,7 +201,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
   extern __shared__ unsigned char sraw[];
   unsigned char* sm = align1k(sraw);
   float* prm = reinterpret_cast<float*>(sm + kPrm);  // b1, b2, b3, w4 [4][240]
-  __shared__ uint64_t full[8], empty[8], accb[2];
+  __shared__ uint64_t full[10], empty[10], accb[2];
   __shared__ uint32_t tslot;
   __shared__ int s_tiles[kMaxTypes + 1];
   __shared__ float sE[kFR];
@@ -199,7 +209,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
   const int row = t & (kFR - 1), half = t >> 7;  // TMEM lane / atom, column half
 
   if (t == 0) {
-    for (int q = 0; q < 8; ++q) { tc::mbar_init(&full[q], 1); tc::mbar_init(&empty[q], 1); }
+    for (int q = 0; q < 10; ++q) { tc::mbar_init(&full[q], 1); tc::mbar_init(&empty[q], 1); }
     for (int q = 0; q < 2; ++q) tc::mbar_init(&accb[q], 1);
     tc::mbar_fence_init();
     int acc = 0;
@@ -217,12 +227,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
   const uint32_t resid = acc1;
   Slots sl;
   sl.full = full; sl.empty = empty;
-  for (int q = 0; q < 8; ++q) sl.uses[q] = 0;
+  for (int q = 0; q < 10; ++q) sl.uses[q] = 0;
   uint32_t aph[2] = {0, 0};
   bool ok = true;
   int cur_type = -1;
   const int ntiles = s_tiles[a.ntypes];
   const uint32_t id240 = tc::idesc_f16(128, 240, F16), id160 = tc::idesc_f16(128, kBChunk, F16);
+  const uint32_t id128 = tc::idesc_f16(128, 128, F16);
   // columns of this thread's half: 16-column chunks [c_beg, c_end) of 15 (240 columns)
   const int c_beg = half ? 8 : 0, c_end = half ? 15 : 8;
   Issuer is;
@@ -242,24 +253,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
     aph[r] ^= 1u;
     tc::tc_fence_after();
   };
-  // thread 0: the MMAs of split GEMM g (its first job, the hi block of K block 0, was
-  // prefetched).  Jobs alternate hi / lo halves; after issuing job i the slot of job i - 1
-  // is refilled, so the tensor pipe always has the MMAs of job i queued while it waits.
+  // thread 0: the MMAs of split GEMM g (its first three jobs were prefetched).  Each job is
+  // one N half (128 output columns) of one K block, hi or lo weights; after issuing job i the
+  // slot of job i - 1 is refilled, so three loads stay in flight behind the MMAs.
   auto issue_split = [&](int g) {
-    for (int i = 0; i < 8 && ok; ++i) {
-      const int k = kSplitSlot + (i & 1);
+    for (int i = 0; i < kSplitJobs && ok; ++i) {
+      const int k = kSplitSlot + (i & 3);
       is.consume_begin(k);
-      const int kx = is.split_block(i >> 1);
+      const int kx = is.split_block(i >> 2);
+      const uint32_t d = tmem + 128u * (uint32_t)((i >> 1) & 1);
       const uint32_t xh = tc::smem_u32(sm + kXHi + kx * kBlk), xl = tc::smem_u32(sm + kXLo + kx * kBlk);
-      const uint32_t wv = tc::smem_u32(sm + kSt + (i & 1) * kWB);
+      const uint32_t wv = tc::smem_u32(sm + kSt + (i & 3) * kSSlot);
       if ((i & 1) == 0) {  // hi weights: x_hi w_hi + x_lo w_hi
-        tc::mma_kblock(tmem, xh, wv, id240, i > 0, 4);
-        tc::mma_kblock(tmem, xl, wv, id240, true, 4);
+        tc::mma_kblock(d, xh, wv, id128, i >= 4, 4);
+        tc::mma_kblock(d, xl, wv, id128, true, 4);
       } else {             // lo weights: x_hi w_lo
-        tc::mma_kblock(tmem, xh, wv, id240, true, 4);
+        tc::mma_kblock(d, xh, wv, id128, true, 4);
       }
       is.consume_end(k);
-      if (i + 1 < 8) is.load_split(g, i + 1);
+      if (i + kSSlots - 1 < kSplitJobs) is.load_split(g, i + kSSlots - 1);
     }
     tc::mma_commit(&accb[0]);
   };
@@ -304,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
     }
     __syncwarp();  // lanes 1..31 of warp 0 wait here, not in a polling loop beside the issuer
     wait_acc(0);
-    if (t == 0) is.load_split(0, 0);  // prefetch under the epilogue
+    if (t == 0) is.prefetch_split(0);  // prefetch under the epilogue
     __syncwarp();
     // f1/f2 factors of this row are fetched ahead of the TMEM loop below
 #pragma unroll 1
@@ -334,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
     if (t == 0) issue_split(0);
     __syncwarp();
     wait_acc(0);
-    if (t == 0) is.load_split(1, 0);
+    if (t == 0) is.prefetch_split(1);
     __syncwarp();
 #pragma unroll 1
     for (int c = c_beg; c < c_end; ++c) {
@@ -359,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
     if (t == 0) issue_split(1);
     __syncwarp();
     wait_acc(0);
-    if (t == 0) is.load_split(2, 0);
+    if (t == 0) is.prefetch_split(2);
     __syncwarp();
     float e = 0.f;
 #pragma unroll 1
@@ -399,7 +411,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
         }
       }
       wait_acc(0);
-      if (t == 0) is.load_split(3, 0);
+      if (t == 0) is.prefetch_split(3);
       __syncwarp();
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
@@ -492,11 +504,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
         float z[16];
         tc::tmem_ld16(src + 16 * c, z);
         tc::tmem_wait_ld();
-        if (valid) {
-          float4* d = reinterpret_cast<float4*>(a.dD + grow * kKD + kBChunk * is.b1_chunk(n) + 16 * c);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) d[u] = make_float4(z[4 * u], z[4 * u + 1], z[4 * u + 2], z[4 * u + 3]);
-        }
+        if (valid) store_g16<true>(a.dD + grow * kKD + kBChunk * is.b1_chunk(n) + 16 * c, z);
       }
       tc::tc_fence_before();
       __syncthreads();
@@ -622,7 +630,7 @@ dp_status mix_fit_setup(Model* m) {
     ok = ok && make_map(&fm->W1[ty], W1, f16, kF, kKD, kBChunk);
     for (int g = 0; g < 4; ++g)
       for (int h = 0; h < 2; ++h)
-        ok = ok && make_map(&fm->S[ty][g][h], S + (size_t)(2 * g + h) * kF * kF, f16, kF, kF, kF);
+        ok = ok && make_map(&fm->S[ty][g][h], S + (size_t)(2 * g + h) * kF * kF, f16, kF, kF, 128);
   }
   if (!ok) {
     m->last_error = "cuTensorMapEncodeTiled failed";
@@ -640,7 +648,7 @@ dp_status launch_mix_fitting(Model* m, int N) {
   a.ebias_off = a.fit_base + (long)m->ntypes * kFitParams;
   a.f1 = static_cast<unsigned short*>(m->act[0]);
   a.f2 = static_cast<unsigned short*>(m->act[1]);
-  a.dD = static_cast<float*>(m->dD);
+  a.dD = static_cast<unsigned short*>(m->dD);
   a.e_atom = m->e_atom;
   a.err = m->err;
   const bool f16 = m->prec == DP_MIX_FP16;
