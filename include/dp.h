@@ -63,7 +63,8 @@ typedef enum {
   DP_FP32 = 1,     /* R, networks and per-pair force terms in FP32; positions,
                       Verlet update, force accumulation, energy and virial sums in FP64 */
   DP_MIX_BF16 = 2, /* as DP_FP32, with the embedding and fitting GEMM operands in BF16
-                      on the tensor cores, FP32 accumulation */
+                      on the tensor cores, FP32 accumulation; forces accumulated in FP32
+                      (then added to the FP64 force array) */
   DP_MIX_FP16 = 3  /* as DP_MIX_BF16 with FP16 operands */
 } dp_precision;
 

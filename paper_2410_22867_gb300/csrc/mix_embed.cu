@@ -41,6 +41,7 @@ struct MixArgs {
   float* Tseg;           // [nt][N][400] partial T per neighbour type
   const float4* dT;      // [N][100]: dE/dT[c][a] * (1/S), c in x..w
   double* force;         // [N][3]
+  float* force32;        // [N][3] FP32 accumulator (folded into force after the backward)
   double* vir_atom;      // [N][9]
   int* err;
 };
@@ -696,10 +697,10 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
         }
       }
     }
-    // chain rule through the normalisation and the environment row.  Per-row terms
-    // and the per-warp partial sums stay FP32 (FP64 arithmetic runs at a small
-    // fraction of the FP32 rate on this GPU); only the accumulation into the
-    // force and virial arrays is FP64.
+    // chain rule through the normalisation and the environment row.  Per-row terms,
+    // the per-warp partial sums and the force accumulation are FP32 (FP64 arithmetic
+    // runs at a small fraction of the FP32 rate on this GPU; ~180 terms per atom add
+    // ~1e-6 relative rounding); the per-atom virial is accumulated in FP64.
     float g3[3] = {0.f, 0.f, 0.f};
     if (valid) {
       dR[0] += ds;
@@ -714,7 +715,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) g3[c] = common * f.d[c] + qv * dR[1 + c];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) atomicAdd(&a.force[3 * (size_t)f.j + c], (double)(-g3[c]));
+      for (int c = 0; c < 3; ++c) atomicAdd(&a.force32[3 * (size_t)f.j + c], -g3[c]);
     }
     // centre force and per-atom virial: warp-segmented sums over rows of the same atom
     float vals[12];
@@ -738,7 +739,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == leader) {
           const size_t atom = (size_t)ti.a0 + seg;
-          if (q < 3) atomicAdd(&a.force[3 * atom + q], (double)v);
+          if (q < 3) atomicAdd(&a.force32[3 * atom + q], v);
           else atomicAdd(&a.vir_atom[9 * atom + q - 3], (double)v);
         }
       }
@@ -909,6 +910,12 @@ __global__ void __launch_bounds__(32 * kDtWarps) k_mix_dT(int N, float invS, con
   }
 }
 
+// force (FP64) += force32 (the mixed backward's FP32 accumulation).
+__global__ void k_fold_force32(int n3, const float* __restrict__ f32, double* __restrict__ force) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n3) force[k] += (double)f32[k];
+}
+
 MixArgs make_mix_args(Model* m, int N) {
   MixArgs a{};
   a.N = N; a.ntypes = m->ntypes; a.S = m->S;
@@ -917,7 +924,7 @@ MixArgs make_mix_args(Model* m, int N) {
   a.w = m->w32; a.stat = m->stat32; a.itype = m->itype; a.type_off = m->type_off; a.rowoff = m->rowoff;
   a.nl_j = m->nl_j; a.nl_d = static_cast<const float4*>(m->nl_d);
   a.Tseg = m->Tseg; a.dT = static_cast<const float4*>(m->dTm);
-  a.force = m->force; a.vir_atom = m->vir_atom; a.err = m->err;
+  a.force = m->force; a.force32 = m->force32; a.vir_atom = m->vir_atom; a.err = m->err;
   return a;
 }
 
@@ -958,6 +965,7 @@ dp_status launch_mix_embed_backward(Model* m, int N) {
                                                               static_cast<const unsigned short*>(m->dD),
                                                               static_cast<float4*>(m->dTm));
   DP_CUDA_TRY(m, cudaMemsetAsync(m->vir_atom, 0, sizeof(double) * 9 * (size_t)N, m->stream));
+  DP_CUDA_TRY(m, cudaMemsetAsync(m->force32, 0, sizeof(float) * 3 * (size_t)N, m->stream));
   if (m->sub_ev[1]) DP_CUDA_TRY(m, cudaEventRecord(m->sub_ev[1], m->stream));
   MixArgs a = make_mix_args(m, N);
   const bool f16 = m->prec == DP_MIX_FP16;
@@ -967,7 +975,8 @@ dp_status launch_mix_embed_backward(Model* m, int N) {
   const int grid = num_sms() * blocks_per_sm(fn, kRows, kBwdSmem, kTmemCols);
   if (f16) k_mix_embed_bwd<true><<<grid, kRows, kBwdSmem, m->stream>>>(a);
   else k_mix_embed_bwd<false><<<grid, kRows, kBwdSmem, m->stream>>>(a);
-  m->launches += 2;
+  k_fold_force32<<<cdiv(3L * N, 256), 256, 0, m->stream>>>(3 * N, m->force32, m->force);
+  m->launches += 3;
   DP_LAUNCH_CHECK(m);
   return DP_OK;
 }
