@@ -193,7 +193,6 @@ __global__ void k_fill_cells(int N, const int* __restrict__ cell_of, const int* 
 struct VerletArgs {
   int N, ntypes, VS;
   int vcap[kMaxTypes], vcap_off[kMaxTypes + 1];
-  int buf_off[kMaxTypes + 1];  // per-warp smem key buffer offsets (in keys)
   double rcs2;
   float rcs2_hi;               // fp32 prefilter bound (rcs2 + band)
   const int* itype;
@@ -224,19 +223,20 @@ __device__ __forceinline__ void pair_vec64(const dvec4& xi, const dvec4& xj, int
 // Verlet list of atom i (one warp per atom).  The list only has to contain every pair
 // within r_c + skin (the per-step format keeps exactly the pairs within r_c, with an exact
 // FP64 test near the cutoff), so a pair is taken when its FP32 r^2 is below (r_c + skin)^2
-// plus a band wider than the FP32 rounding error: no FP64 in the candidate loop.  The
+// plus a band wider than the FP32 rounding error: no FP64 in the candidate test.  The
 // stencil's cells are taken 32 at a time; their candidates form one flat range that the
-// lanes walk two at a time (independent gathers in flight).  Keys (j, image) are sorted per
-// neighbour type in shared memory, which gives the canonical order.
+// lanes walk two at a time (independent gathers in flight).  Accepted pairs go straight to
+// the list, grouped by neighbour type, in the order found: every consumer is independent
+// of the order within a type (the descriptor is a sum over neighbours; the format is a
+// compaction), and dp_get_nlist sorts a copy into the canonical order.  The pair vector at
+// rebuild is formed in FP64 from the positions and stored in FP32.
 __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
-  extern __shared__ unsigned long long keys_all[];
   __shared__ int cnt[kVerletWarps][kMaxTypes];
   __shared__ int s_beg[kVerletWarps][32], s_off[kVerletWarps][32], s_img[kVerletWarps][32];
   __shared__ float s_sh[kVerletWarps][32][3];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int i = blockIdx.x * kVerletWarps + w;
   if (i >= a.N) return;
-  unsigned long long* keys = keys_all + (size_t)w * a.buf_off[a.ntypes];
   if (lane < kMaxTypes) cnt[w][lane] = 0;
   __syncwarp();
   const RepGeom& g = a.geom[a.irep[i]];
@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
   const int sy = 2 * g.m[1] + 1, sz = 2 * g.m[2] + 1;
   const int ncell = (2 * g.m[0] + 1) * sy * sz;
   const int self_code = pack_img(0, 0, 0);
+  const size_t ebase = (size_t)i * a.VS;
 
   auto fetch = [&](int q, int total, int nb, bool& acc, int& j, int& tj, int& code) {
     acc = false; j = -1; tj = 0; code = 0;
@@ -275,8 +276,16 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
       const int start = cnt[w][t];
       if (acc && tj == t) {
         const int pos = start + __popc(mask & lt);
-        if (pos < a.buf_off[t + 1] - a.buf_off[t])
-          keys[a.buf_off[t] + pos] = ((unsigned long long)(unsigned)j << 32) | (unsigned)code;
+        if (pos < a.vcap[t]) {
+          int n0, n1, n2;
+          unpack_img(code, n0, n1, n2);
+          double d[3];
+          pair_vec64(xi, a.x[j], n0, n1, n2, g.L, d);
+          const size_t e = ebase + a.vcap_off[t] + pos;
+          a.vl_j[e] = j;
+          a.vl_img[e] = code;
+          a.vl_d0[e] = make_float4((float)d[0], (float)d[1], (float)d[2], 0.f);
+        }
       }
       __syncwarp();
       if (lane == 0) cnt[w][t] = start + __popc(mask);
@@ -327,48 +336,13 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
     __syncwarp();
   }
   __syncwarp();
-  for (int t = 0; t < a.ntypes; ++t) {
-    int nt_ = cnt[w][t];
-    int capP = a.buf_off[t + 1] - a.buf_off[t];
-    if (nt_ > a.vcap[t]) {
-      if (lane == 0) set_err(a.err, ERR_VCAP);
-      nt_ = a.vcap[t];
+  if (lane < a.ntypes) {
+    int nt_ = cnt[w][lane];
+    if (nt_ > a.vcap[lane]) {
+      set_err(a.err, ERR_VCAP);
+      nt_ = a.vcap[lane];
     }
-    unsigned long long* kb = keys + a.buf_off[t];
-    int P = 1;
-    while (P < nt_) P <<= 1;
-    if (P > capP) P = capP;
-    for (int q = nt_ + lane; q < P; q += 32) kb[q] = ~0ull;
-    __syncwarp();
-    // bitonic sort of kb[0, P)
-    for (int k = 2; k <= P; k <<= 1) {
-      for (int jj = k >> 1; jj > 0; jj >>= 1) {
-        for (int q = lane; q < P; q += 32) {
-          int p = q ^ jj;
-          if (p > q) {
-            unsigned long long u0 = kb[q], u1 = kb[p];
-            bool up = (q & k) == 0;
-            if ((u0 > u1) == up) { kb[q] = u1; kb[p] = u0; }
-          }
-        }
-        __syncwarp();
-      }
-    }
-    size_t ebase = (size_t)i * a.VS + a.vcap_off[t];
-    for (int q = lane; q < nt_; q += 32) {
-      unsigned long long key = kb[q];
-      int j = (int)(key >> 32);
-      int code = (int)(key & 0xffffffffu);
-      int n0, n1, n2;
-      unpack_img(code, n0, n1, n2);
-      double d[3];
-      pair_vec64(xi, a.x[j], n0, n1, n2, g.L, d);
-      a.vl_j[ebase + q] = j;
-      a.vl_img[ebase + q] = code;
-      a.vl_d0[ebase + q] = make_float4((float)d[0], (float)d[1], (float)d[2], 0.f);
-    }
-    if (lane == 0) a.vcount[(size_t)i * a.ntypes + t] = nt_;
-    __syncwarp();
+    a.vcount[(size_t)i * a.ntypes + lane] = nt_;
   }
 }
 
@@ -468,19 +442,43 @@ __global__ void __launch_bounds__(128) k_format(FormatArgs a) {
   }
 }
 
+// Canonical copy of the formatted list for the caller: rows in the caller's atom order, each
+// neighbour-type segment sorted by (caller index j, image nx, ny, nz), padded with -1 / 0.
+// One CTA per atom; keys sorted in shared memory (bitonic).  A test hook, not on the MD path.
 __global__ void k_get_nlist(int N, int ntypes, int S, const int* sel, const int* sel_off, const int* inv,
                             const int* perm, const int* nl_j, const int* nl_img, const int* nl_count,
                             int* out_nl, int* out_img) {
-  int u = blockIdx.x;
+  extern __shared__ unsigned long long keys[];
+  const int u = blockIdx.x;
   if (u >= N) return;
-  int i = inv[u];
+  const int i = inv[u];
   for (int t = 0; t < ntypes; ++t) {
-    int c = nl_count[(size_t)i * ntypes + t];
-    for (int q = threadIdx.x; q < sel[t]; q += blockDim.x) {
-      size_t src = (size_t)i * S + sel_off[t] + q, dst = (size_t)u * S + sel_off[t] + q;
-      out_nl[dst] = (q < c) ? perm[nl_j[src]] : -1;
-      out_img[dst] = (q < c) ? nl_img[src] : 0;
+    const int c = nl_count[(size_t)i * ntypes + t];
+    int P = 1;
+    while (P < c) P <<= 1;
+    for (int q = threadIdx.x; q < P; q += blockDim.x) {
+      const size_t src = (size_t)i * S + sel_off[t] + q;
+      keys[q] = (q < c) ? (((unsigned long long)(unsigned)perm[nl_j[src]] << 32) | (unsigned)nl_img[src])
+                        : ~0ull;
     }
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1)
+      for (int jj = k >> 1; jj > 0; jj >>= 1) {
+        for (int q = threadIdx.x; q < P; q += blockDim.x) {
+          const int p = q ^ jj;
+          if (p > q) {
+            const unsigned long long k0 = keys[q], k1 = keys[p];
+            if ((k0 > k1) == ((q & k) == 0)) { keys[q] = k1; keys[p] = k0; }
+          }
+        }
+        __syncthreads();
+      }
+    for (int q = threadIdx.x; q < sel[t]; q += blockDim.x) {
+      const size_t dst = (size_t)u * S + sel_off[t] + q;
+      out_nl[dst] = (q < c) ? (int)(keys[q] >> 32) : -1;
+      out_img[dst] = (q < c) ? (int)(keys[q] & 0xffffffffu) : 0;
+    }
+    __syncthreads();
   }
 }
 
@@ -522,13 +520,9 @@ dp_status launch_rebuild(Model* m, int N) {
   k_fill_cells<<<cdiv(N, 256), 256, 0, s>>>(N, m->cell_of, m->cell_start, m->cell_fill, m->cell_atoms);
   VerletArgs a;
   a.N = N; a.ntypes = m->ntypes; a.VS = m->VS;
-  a.buf_off[0] = 0;
   for (int t = 0; t < m->ntypes; ++t) {
     a.vcap[t] = m->vcap[t];
     a.vcap_off[t] = m->vcap_off[t];
-    int P = 1;
-    while (P < m->vcap[t]) P <<= 1;
-    a.buf_off[t + 1] = a.buf_off[t] + P;
   }
   a.vcap_off[m->ntypes] = m->vcap_off[m->ntypes];
   const double rcs = m->rc + m->skin;
@@ -539,9 +533,7 @@ dp_status launch_rebuild(Model* m, int N) {
   a.itype = m->itype; a.irep = m->irep; a.geom = m->geom; a.x = m->x; a.xf = m->xf;
   a.cell_of = m->cell_of; a.cell_start = m->cell_start; a.cell_atoms = m->cell_atoms;
   a.vl_j = m->vl_j; a.vl_img = m->vl_img; a.vl_d0 = m->vl_d0; a.vcount = m->vcount; a.err = m->err;
-  size_t smem = sizeof(unsigned long long) * (size_t)a.buf_off[m->ntypes] * kVerletWarps;
-  DP_CUDA_TRY(m, ensure_smem(reinterpret_cast<const void*>(k_verlet), smem));
-  k_verlet<<<cdiv(N, kVerletWarps), 32 * kVerletWarps, smem, s>>>(a);
+  k_verlet<<<cdiv(N, kVerletWarps), 32 * kVerletWarps, 0, s>>>(a);
   m->launches += 4;
   DP_LAUNCH_CHECK(m);
   return DP_OK;
@@ -582,8 +574,13 @@ dp_status launch_get_nlist(Model* m, int N, int* nlist, int* images) {
   for (int t = 0; t < m->ntypes; ++t) hsel[t] = m->sel[t];
   for (int t = 0; t <= m->ntypes; ++t) hsel[kMaxTypes + t] = m->sel_off[t];
   DP_CUDA_TRY(m, cudaMemcpyAsync(dsel, hsel, sizeof(hsel), cudaMemcpyHostToDevice, m->stream));
-  k_get_nlist<<<N, 128, 0, m->stream>>>(N, m->ntypes, m->S, dsel, dsel + kMaxTypes, m->inv, m->perm, m->nl_j,
-                                        m->nl_img, m->nl_count, nlist, images);
+  int Pmax = 1;
+  for (int t = 0; t < m->ntypes; ++t)
+    while (Pmax < m->sel[t]) Pmax <<= 1;
+  const size_t ksm = sizeof(unsigned long long) * (size_t)Pmax;
+  DP_CUDA_TRY(m, ensure_smem(reinterpret_cast<const void*>(k_get_nlist), ksm));
+  k_get_nlist<<<N, 128, ksm, m->stream>>>(N, m->ntypes, m->S, dsel, dsel + kMaxTypes, m->inv, m->perm, m->nl_j,
+                                          m->nl_img, m->nl_count, nlist, images);
   m->launches += 1;
   DP_LAUNCH_CHECK(m);
   return DP_OK;
