@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
   extern __shared__ unsigned char sraw[];
   unsigned char* sm = align1024(sraw);
   unsigned char* sA = sm;                          // 16 KB operand block (h1, then h2)
-  unsigned char* sGt = sm;                         // 32 KB: G^T [feature][row] fp16, aliases sA after MMA 2
+  unsigned char* sGt = sm;                         // 32 KB: G^T fp16 (MN-major: [row][feature]), aliases sA after MMA 2
   unsigned char* sRs = sm + 32768;                 // 8 KB: block-sparse R_hat^T [(atom, c)][row] fp16
   unsigned char* sB2 = sRs + 8192;                 // 8 KB
   unsigned char* sB3 = sB2 + 8192;                 // 14 KB
@@ -360,23 +360,30 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     // layer-3 epilogue: G = [h2, h2] + tanh(z3 + b3); G^T and this row's R_hat column go to
     // the fp16 operands of the T product T_slot[c][a] = sum_rows R_hat[row][c] G[row][a]
     {
-      const uint32_t kb = (uint32_t)(t >> 6) * 16384u, kr = (uint32_t)(t & 63);
-      unsigned char* gcol = sGt + kb + (kr & 7) * 2;
+      // G^T is the A operand stored MN-major: row = tile row (K), 64 features per 128-byte
+      // row, features 64..127 in a second block 16 KB on; each thread writes its own row
 #pragma unroll
       for (int c = 0; c < 7; ++c) {
         float z[16];
         tc::tmem_ld16(tl + 16 * c, z);
         tc::tmem_wait_ld();
+        float g[16];
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
           const int q = 16 * c + u;
-          if (q < kN3) {
-            const float g = h2[q % kN2] + tc::tanh_fast(z[u] + small[100 + q]);
-            *reinterpret_cast<__half*>(gcol + q * 128 + (((kr >> 3) ^ (q & 7)) << 4)) = __float2half_rn(g);
-          }
+          g[u] = (q < kN3) ? h2[q % kN2] + tc::tanh_fast(z[u] + small[100 + q]) : 0.f;
+        }
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const int q0 = 16 * c + 8 * hh;
+          if (q0 < kN3)  // features 104.. only feed output rows that are never read
+            *reinterpret_cast<uint4*>(sGt + tc::sw128_mn_off(q0, t, 16384)) =
+                make_uint4(tc::pack2<true>(g[8 * hh], g[8 * hh + 1]), tc::pack2<true>(g[8 * hh + 2], g[8 * hh + 3]),
+                           tc::pack2<true>(g[8 * hh + 4], g[8 * hh + 5]), tc::pack2<true>(g[8 * hh + 6], g[8 * hh + 7]));
         }
       }
       if (valid) {
+        const uint32_t kr = (uint32_t)(t & 63);
         unsigned char* rcol = sRs + (uint32_t)(t >> 6) * 4096u + (kr & 7) * 2;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -386,11 +393,15 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
       }
     }
     operand_barrier();
-    // T product on the tensor core: D[feature][(slot, c)] over the 128 rows (two K blocks)
+    // T product on the tensor core: D[feature][(slot, c)] over the 128 rows (8 K steps;
+    // A = G^T read MN-major, B = R_hat^T K-major)
     if (t == 0) {
-      const uint32_t id = tc::idesc_f16(128, 32, true);
-      tc::mma_kblock(tmem, tc::smem_u32(sGt), tc::smem_u32(sRs), id, false, 4);
-      tc::mma_kblock(tmem, tc::smem_u32(sGt + 16384), tc::smem_u32(sRs + 4096), id, true, 4);
+      const uint32_t id = tc::idesc_mn(tc::idesc_f16(128, 32, true), true, false);
+      for (int k = 0; k < 8; ++k) {
+        const uint64_t ad = tc::sdesc_sw128_mn(tc::smem_u32(sGt) + 2048 * k, 16384);
+        const uint64_t bd = tc::sdesc_sw128(tc::smem_u32(sRs + (k >> 2) * 4096) + 32 * (k & 3));
+        tc::mma_f16(tmem, ad, bd, id, k > 0 ? 1u : 0u);
+      }
       tc::mma_commit(&bar);
     }
     mma_sync_wait(&bar, phase, a.err, ok);
