@@ -192,14 +192,19 @@ __device__ __forceinline__ int local_atom(const int* sRow, int row) {
   return la;
 }
 
-__device__ __forceinline__ void row_front(const MixArgs& a, const TileInfo& ti, const int* sRow, int t,
+// Load half: the row's slot, atom, neighbour index and pair vector (issued early so the
+// global loads overlap other work); row_compute forms the environment row from them.
+__device__ __forceinline__ float4 row_load(const MixArgs& a, const TileInfo& ti, const int* sRow, int t,
                                           bool want_j, RowFront& f) {
   const int row = ti.p + t;
   f.la = local_atom(sRow, row);
   f.atom = ti.a0 + f.la;
   const size_t e = (size_t)f.atom * a.S + a.sel_off[ti.tj] + (row - sRow[f.la]);
-  float4 dv = a.nl_d[e];
   f.j = want_j ? a.nl_j[e] : 0;
+  return a.nl_d[e];
+}
+
+__device__ __forceinline__ void row_compute(const MixArgs& a, const TileInfo& ti, float4 dv, RowFront& f) {
   f.d[0] = dv.x; f.d[1] = dv.y; f.d[2] = dv.z;
   f.r = sqrtf(dv.x * dv.x + dv.y * dv.y + dv.z * dv.z);
   switch_fn<float>(f.r, a.rs, a.rc, a.switch_kind, f.sw, f.dsw);
@@ -207,6 +212,11 @@ __device__ __forceinline__ void row_front(const MixArgs& a, const TileInfo& ti, 
   f.R[0] = s; f.R[1] = s * dv.x / f.r; f.R[2] = s * dv.y / f.r; f.R[3] = s * dv.z / f.r;
 #pragma unroll
   for (int c = 0; c < 4; ++c) f.R[c] = (f.R[c] - a.stat[ti.ti * 4 + c]) * a.stat[(a.ntypes + ti.ti) * 4 + c];
+}
+
+__device__ __forceinline__ void row_front(const MixArgs& a, const TileInfo& ti, const int* sRow, int t,
+                                          bool want_j, RowFront& f) {
+  row_compute(a, ti, row_load(a, ti, sRow, t, want_j, f), f);
 }
 
 // h1 = tanh(s_hat W1 + b1) and its 16-bit copy into the A block (K = 32 used).
@@ -568,15 +578,18 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
       load_bwd_ops<F16>(a.w + (size_t)np * kEmbParams, sB2, sB3, small);
       pair = np;
     }
+    // this row's neighbour data is requested before the dE/dT staging and its barrier
+    RowFront f;
+    const bool valid = t < ti.nrows;
+    float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) dv = row_load(a, ti, sRow, t, true, f);
     const int natoms_tile = local_atom(sRow, ti.p + ti.nrows - 1) + 1;
     for (int q = t; q < natoms_tile * kN3; q += kRows) sdT[q] = a.dT[(size_t)ti.a0 * kN3 + q];
     __syncthreads();
 
     float h1[kN1], h2[kN2];
-    RowFront f;
-    const bool valid = t < ti.nrows;
     if (valid) {
-      row_front(a, ti, sRow, t, true, f);
+      row_compute(a, ti, dv, f);
     } else {
       f.R[0] = f.R[1] = f.R[2] = f.R[3] = 0.f;
       f.la = 0; f.j = 0; f.atom = ti.a0;
