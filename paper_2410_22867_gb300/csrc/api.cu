@@ -142,6 +142,7 @@ dp_status setup_replicas(Model* m, int nrep, const int* offs, const double* boxe
       if (!(L > 0.0) || !std::isfinite(L)) { m->last_error = "box length must be positive"; return DP_ERR_ARG; }
       g.L[a] = L;
       g.Lf[a] = (float)L;
+      g.Lq[a] = std::llrint(L * 4294967296.0);
       int nc = (int)std::floor(L / eff);
       if (nc < 1) nc = 1;
       if (nc > 1024) nc = 1024;
@@ -149,6 +150,7 @@ dp_status setup_replicas(Model* m, int nrep, const int* offs, const double* boxe
       g.edge[a] = L / nc;
       g.m[a] = (int)std::ceil(eff / g.edge[a]);
       if (g.m[a] > 200) { m->last_error = "box too small for the cutoff"; return DP_ERR_UNSUPPORTED; }
+      if (L >= 2147483648.0) { m->last_error = "box length too large"; return DP_ERR_UNSUPPORTED; }
       ncr *= nc;
     }
     g.cell_off = cells;
@@ -417,7 +419,7 @@ dp_status dp_create(dp_model** out, int ntypes, const char* const* type_map, dou
   A_(perm, 4 * N); A_(inv, 4 * N); A_(itype, 4 * N); A_(irep, 4 * N);
   A_(type_count, 4 * (kMaxTypes + 1)); A_(type_off, 4 * (kMaxTypes + 1));
   A_(blk_count, 4 * (size_t)kMaxTypes * (N / 1024 + 2));
-  A_(x, 32 * N); A_(xref, 32 * N); A_(v, 32 * N); A_(delta, 16 * N); A_(xf, 16 * N);
+  A_(x, 32 * N); A_(xref, 32 * N); A_(v, 32 * N); A_(delta, 16 * N); A_(xf, 16 * N); A_(xq, 32 * N);
   A_(force, 24 * N); A_(mass, 8 * N);
   A_(geom, sizeof(RepGeom) * R);
   A_(cell_of, 4 * N);

@@ -44,9 +44,15 @@ __host__ __device__ __forceinline__ dvec4 make_dvec4(double x, double y, double 
   return r;
 }
 
+// Fixed-point position (x * 2^32, rounded) for exact pair vectors without FP64 arithmetic.
+struct __align__(32) qvec4 {
+  long long x, y, z, w;
+};
+
 // Per-replica geometry (orthorhombic box and cell grid).
 struct RepGeom {
   double L[3];      // box lengths
+  long long Lq[3];  // box lengths in fixed point (L * 2^32, rounded)
   float Lf[3];      // box lengths in fp32
   int nc[3];        // cells per axis
   int m[3];         // stencil half width per axis
@@ -96,6 +102,7 @@ struct Model {
   dvec4* v = nullptr;       // velocities
   float4* delta = nullptr;    // x - xref in fp32
   float4* xf = nullptr;       // wrapped positions in fp32 (rebuild prefilter)
+  qvec4* xq = nullptr;        // wrapped positions at rebuild in fixed point (x * 2^32)
   double* force = nullptr;    // [N*3]
   double* mass = nullptr;     // [N] per internal atom
 

@@ -132,10 +132,11 @@ __global__ void k_load_positions(const double* __restrict__ coords, const int* _
 }
 
 // ------------------------------------------------------------------ cells
-// xf.w carries the atom's type (bit pattern), read by the Verlet-list gather.
+// xf.w carries the atom's type (bit pattern), read by the Verlet-list gather; xq holds the
+// wrapped position in fixed point for exact pair vectors.
 __global__ void k_wrap_bin(int N, const int* __restrict__ irep, const int* __restrict__ itype,
-                           const RepGeom* __restrict__ geom, dvec4* x, dvec4* xref, float4* xf, float4* delta,
-                           int* cell_of, int* cell_count) {
+                           const RepGeom* __restrict__ geom, dvec4* x, dvec4* xref, float4* xf, qvec4* xq,
+                           float4* delta, int* cell_of, int* cell_count) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
   const RepGeom& g = geom[irep[k]];
@@ -145,6 +146,10 @@ __global__ void k_wrap_bin(int N, const int* __restrict__ irep, const int* __res
   x[k] = q;
   xref[k] = q;
   xf[k] = make_float4((float)w[0], (float)w[1], (float)w[2], __int_as_float(itype[k]));
+  qvec4 qk;
+  qk.x = llrint(w[0] * 4294967296.0); qk.y = llrint(w[1] * 4294967296.0); qk.z = llrint(w[2] * 4294967296.0);
+  qk.w = 0;
+  xq[k] = qk;
   delta[k] = make_float4(0.f, 0.f, 0.f, 0.f);
   int c[3];
   for (int a = 0; a < 3; ++a) {
@@ -200,6 +205,7 @@ struct VerletArgs {
   const RepGeom* geom;
   const dvec4* x;
   const float4* xf;
+  const qvec4* xq;
   const int* cell_of;
   const int* cell_start;
   const int* cell_atoms;
@@ -212,12 +218,15 @@ struct VerletArgs {
 
 constexpr int kVerletWarps = 4;
 
-// d = (x_j + n L) - x_i in FP64, round to nearest (no FMA).
-__device__ __forceinline__ void pair_vec64(const dvec4& xi, const dvec4& xj, int nx, int ny, int nz, const double* L,
-                                           double* d) {
-  d[0] = __dsub_rn(__dadd_rn(xj.x, __dmul_rn((double)nx, L[0])), xi.x);
-  d[1] = __dsub_rn(__dadd_rn(xj.y, __dmul_rn((double)ny, L[1])), xi.y);
-  d[2] = __dsub_rn(__dadd_rn(xj.z, __dmul_rn((double)nz, L[2])), xi.z);
+// One component of d = x_j + n L - x_i from fixed-point positions (units of 2^-32 A): the
+// integer difference D = hi * 2^32 + lo (lo in [0, 2^32)) is exact; the float result is
+// hi + lo * 2^-32 with one final rounding (within one ulp of d).  Integer work only: FP64
+// runs at a small fraction of the FP32 rate on this GPU.
+__device__ __forceinline__ float fixed_diff(long long qj, long long qi, int n, long long Lq) {
+  const long long D = qj + (long long)n * Lq - qi;
+  const int hi = (int)(D >> 32);
+  const unsigned lo = (unsigned)(D & 0xffffffffll);
+  return fmaf((float)lo, 2.3283064365386963e-10f, (float)hi);
 }
 
 // Verlet list of atom i (one warp per atom).  The list only has to contain every pair
@@ -229,7 +238,7 @@ __device__ __forceinline__ void pair_vec64(const dvec4& xi, const dvec4& xj, int
 // the list, grouped by neighbour type, in the order found: every consumer is independent
 // of the order within a type (the descriptor is a sum over neighbours; the format is a
 // compaction), and dp_get_nlist sorts a copy into the canonical order.  The pair vector at
-// rebuild is formed in FP64 from the positions and stored in FP32.
+// rebuild is formed exactly from fixed-point positions and stored in FP32.
 __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
   __shared__ int cnt[kVerletWarps][kMaxTypes];
   __shared__ int s_beg[kVerletWarps][32], s_off[kVerletWarps][32], s_img[kVerletWarps][32];
@@ -240,7 +249,7 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
   if (lane < kMaxTypes) cnt[w][lane] = 0;
   __syncwarp();
   const RepGeom& g = a.geom[a.irep[i]];
-  const dvec4 xi = a.x[i];
+  const qvec4 qi = a.xq[i];
   const float4 xfi = a.xf[i];
   const int cid = a.cell_of[i];
   const int rel = cid - g.cell_off;
@@ -279,12 +288,12 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
         if (pos < a.vcap[t]) {
           int n0, n1, n2;
           unpack_img(code, n0, n1, n2);
-          double d[3];
-          pair_vec64(xi, a.x[j], n0, n1, n2, g.L, d);
+          const qvec4 qj = a.xq[j];
           const size_t e = ebase + a.vcap_off[t] + pos;
           a.vl_j[e] = j;
           a.vl_img[e] = code;
-          a.vl_d0[e] = make_float4((float)d[0], (float)d[1], (float)d[2], 0.f);
+          a.vl_d0[e] = make_float4(fixed_diff(qj.x, qi.x, n0, g.Lq[0]), fixed_diff(qj.y, qi.y, n1, g.Lq[1]),
+                                   fixed_diff(qj.z, qi.z, n2, g.Lq[2]), 0.f);
         }
       }
       __syncwarp();
@@ -514,8 +523,8 @@ dp_status launch_rebuild(Model* m, int N) {
   cudaStream_t s = m->stream;
   DP_CUDA_TRY(m, cudaMemsetAsync(m->cell_count, 0, sizeof(int) * m->ncells, s));
   DP_CUDA_TRY(m, cudaMemsetAsync(m->cell_fill, 0, sizeof(int) * m->ncells, s));
-  k_wrap_bin<<<cdiv(N, 256), 256, 0, s>>>(N, m->irep, m->itype, m->geom, m->x, m->xref, m->xf, m->delta,
-                                          m->cell_of, m->cell_count);
+  k_wrap_bin<<<cdiv(N, 256), 256, 0, s>>>(N, m->irep, m->itype, m->geom, m->x, m->xref, m->xf, m->xq,
+                                          m->delta, m->cell_of, m->cell_count);
   k_scan_cells<<<1, 1024, 0, s>>>(m->ncells, m->cell_count, m->cell_start);
   k_fill_cells<<<cdiv(N, 256), 256, 0, s>>>(N, m->cell_of, m->cell_start, m->cell_fill, m->cell_atoms);
   VerletArgs a;
@@ -530,7 +539,7 @@ dp_status launch_rebuild(Model* m, int N) {
   // worst-case FP32 error of the prefilter's r^2 is ~1.3e-6 * rcs * Lmax; use 10x that
   double band = 1.25e-5 * rcs * (max_box_length(m) + rcs) + 1e-3;
   a.rcs2_hi = (float)(a.rcs2 + band);
-  a.itype = m->itype; a.irep = m->irep; a.geom = m->geom; a.x = m->x; a.xf = m->xf;
+  a.itype = m->itype; a.irep = m->irep; a.geom = m->geom; a.x = m->x; a.xf = m->xf; a.xq = m->xq;
   a.cell_of = m->cell_of; a.cell_start = m->cell_start; a.cell_atoms = m->cell_atoms;
   a.vl_j = m->vl_j; a.vl_img = m->vl_img; a.vl_d0 = m->vl_d0; a.vcount = m->vcount; a.err = m->err;
   k_verlet<<<cdiv(N, kVerletWarps), 32 * kVerletWarps, 0, s>>>(a);
