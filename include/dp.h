@@ -177,6 +177,17 @@ dp_status dp_param_grad(dp_model* m, int natoms, const double* coords, const int
 long long dp_ntheta(const dp_model* m);
 
 /*
+ * dp_set_params -- replace the model's network parameters (training step).  theta
+ * [ntheta] host FP64 in the layout of the weight blob's parameter block (embedding
+ * nets per (ti, tj), fitting nets per type, e_bias); ntheta must equal dp_ntheta(m).
+ * All derived device copies (FP32, transposed fitting weights, 16-bit tensor-core
+ * copies) are rebuilt.  Waits for the model's stream first; synchronous.  Captured
+ * MD graphs stay valid (the device buffers do not move).
+ * Errors: DP_ERR_ARG (null, wrong size), DP_ERR_WEIGHTS (non-finite value), DP_ERR_CUDA.
+ */
+dp_status dp_set_params(dp_model* m, const double* theta, long long ntheta);
+
+/*
  * dp_get_nlist -- copy the formatted neighbour list of the last dp_compute /
  * MD step: nlist [natoms*S] and images [natoms*S] device int32 in caller order,
  * S = sum(sel).  Row i holds, per neighbour type t in order, the neighbours of

@@ -31,7 +31,7 @@ STATUS = {0: "DP_OK", 1: "DP_ERR_ARG", 2: "DP_ERR_CUDA", 3: "DP_ERR_OOM", 4: "DP
 # exported symbols of include/dp.h
 EXPORTS = ("dp_create", "dp_compute", "dp_compute_batch", "dp_verlet_step", "dp_md_run_batch", "dp_param_grad",
            "dp_ntheta", "dp_get_nlist", "dp_phase_times", "dp_kernel_launches", "dp_sync", "dp_last_error",
-           "dp_destroy", "dp_version", "dp_selftest", "dp_selftest_noalloc")
+           "dp_destroy", "dp_version", "dp_selftest", "dp_selftest_noalloc", "dp_set_params")
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -85,9 +85,10 @@ def lib():
             L.dp_kernel_launches.restype = ctypes.c_longlong
             L.dp_selftest.argtypes = [_I, _P]
             L.dp_selftest_noalloc.argtypes = [_P, _I, _P]
+            L.dp_set_params.argtypes = [_P, _P, ctypes.c_longlong]
             for name in ("dp_create", "dp_compute", "dp_compute_batch", "dp_verlet_step", "dp_md_run_batch",
                          "dp_param_grad", "dp_get_nlist", "dp_phase_times", "dp_sync", "dp_selftest",
-                         "dp_selftest_noalloc"):
+                         "dp_selftest_noalloc", "dp_set_params"):
                 getattr(L, name).restype = _I
             _lib = L
     return _lib
@@ -273,6 +274,14 @@ class DPModel:
     def ntheta(self) -> int:
         return int(lib().dp_ntheta(self.h))
 
+    def set_params(self, theta):
+        """Replace the network parameters (dp_set_params): theta [ntheta] float64 in the weight
+        blob's parameter order (numpy array or torch tensor on any device)."""
+        if hasattr(theta, "detach"):
+            theta = theta.detach().to("cpu").numpy()
+        th = np.ascontiguousarray(theta, dtype=np.float64).ravel()
+        self._check(lib().dp_set_params(self.h, th.ctypes.data_as(_P), int(th.size)))
+
     def param_grad(self, coords, types, box, E0, F0, cE=1.0, cF=1.0, sync: bool = True):
         import torch
         N = int(types.shape[0])
@@ -295,3 +304,34 @@ def _remember_n(fn):
 
 DPModel.compute = _remember_n(DPModel.compute)
 DPModel.compute_batch = _remember_n(DPModel.compute_batch)
+
+
+def _make_param_loss():
+    import torch
+
+    class ParamLoss(torch.autograd.Function):
+        """L(theta) = cE (E - E0)^2 + cF sum_k |F_k - F0_k|^2 of one box as a differentiable
+        function of the network parameters theta (float64 tensor [ntheta]).  The forward
+        loads theta into `model` (dp_set_params) and runs dp_param_grad, which returns the
+        loss and its full gradient; the backward scales that gradient.  coords, types, F0
+        are device tensors in the caller's atom order, box a host 3x3."""
+
+        @staticmethod
+        def forward(ctx, theta, model, coords, types, box, E0, F0, cE=1.0, cF=1.0):
+            model.set_params(theta)
+            g, loss = model.param_grad(coords, types, box, float(E0), F0, float(cE), float(cF))
+            ctx.save_for_backward(g.to(theta.device, theta.dtype))
+            return loss.to(theta.device, theta.dtype).reshape(())
+
+        @staticmethod
+        def backward(ctx, gout):
+            (g,) = ctx.saved_tensors
+            return gout * g, None, None, None, None, None, None, None, None
+
+    return ParamLoss
+
+
+try:
+    ParamLoss = _make_param_loss()
+except ImportError:  # torch is needed only for the autograd wrapper
+    ParamLoss = None

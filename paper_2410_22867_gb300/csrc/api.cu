@@ -338,6 +338,43 @@ extern "C" {
 
 const char* dp_version(void) { return "dpgb300 0.1"; }
 
+// Device copies of the parameters from m->theta_host (and davg / dstd): theta in FP64 and
+// FP32, transposed fitting weights, normalisation statistics, and for the mixed precisions
+// the 16-bit tensor-core operand copies.  Synchronous.
+dp_status upload_weights(Model* m) {
+  const int nt = m->ntypes;
+  const std::vector<double>& theta = m->theta_host;
+  const size_t tsz = (size_t)kF * kKD + 2 * (size_t)kF * kF;
+  std::vector<float> t32(theta.begin(), theta.end());
+  std::vector<double> wT(tsz * nt);
+  const size_t emb_total = (size_t)nt * nt * kEmbParams;
+  for (int t = 0; t < nt; ++t) {
+    const double* Pf = theta.data() + emb_total + (size_t)t * kFitParams;
+    double* dst = wT.data() + t * tsz;
+    for (int k = 0; k < kKD; ++k)
+      for (int o = 0; o < kF; ++o) dst[(size_t)o * kKD + k] = Pf[kFW1 + (size_t)k * kF + o];
+    double* d2 = dst + (size_t)kF * kKD;
+    double* d3 = d2 + (size_t)kF * kF;
+    for (int k = 0; k < kF; ++k)
+      for (int o = 0; o < kF; ++o) {
+        d2[(size_t)o * kF + k] = Pf[kFW2 + (size_t)k * kF + o];
+        d3[(size_t)o * kF + k] = Pf[kFW3 + (size_t)k * kF + o];
+      }
+  }
+  std::vector<float> wT32(wT.begin(), wT.end());
+  std::vector<double> stat(8 * nt);
+  for (int q = 0; q < 4 * nt; ++q) { stat[q] = m->davg_host[q]; stat[4 * nt + q] = 1.0 / m->dstd_host[q]; }
+  std::vector<float> stat32(stat.begin(), stat.end());
+  DP_CUDA_TRY(m, cudaMemcpy(m->w64, theta.data(), 8 * theta.size(), cudaMemcpyHostToDevice));
+  DP_CUDA_TRY(m, cudaMemcpy(m->w32, t32.data(), 4 * t32.size(), cudaMemcpyHostToDevice));
+  DP_CUDA_TRY(m, cudaMemcpy(m->fitT64, wT.data(), 8 * wT.size(), cudaMemcpyHostToDevice));
+  DP_CUDA_TRY(m, cudaMemcpy(m->fitT32, wT32.data(), 4 * wT32.size(), cudaMemcpyHostToDevice));
+  DP_CUDA_TRY(m, cudaMemcpy(m->stat64, stat.data(), 8 * stat.size(), cudaMemcpyHostToDevice));
+  DP_CUDA_TRY(m, cudaMemcpy(m->stat32, stat32.data(), 4 * stat32.size(), cudaMemcpyHostToDevice));
+  if (m->prec == DP_MIX_BF16 || m->prec == DP_MIX_FP16) DP_TRY(launch_tc_setup(m));
+  return DP_OK;
+}
+
 dp_status dp_create(dp_model** out, int ntypes, const char* const* type_map, double rcut, double rcut_smth,
                     const int* sel, const char* weight_path, const void* weight_blob, size_t blob_bytes,
                     dp_precision prec, int max_atoms, int max_replicas, double skin, void* cuda_stream) {
@@ -454,39 +491,11 @@ dp_status dp_create(dp_model** out, int ntypes, const char* const* type_map, dou
   if (halloc(m, &m->geom_host, sizeof(RepGeom) * R + sizeof(int) * (R + 1) + 64) != DP_OK) return fail(DP_ERR_OOM, m->last_error);
   if (halloc(m, &m->err_host, 64) != DP_OK) return fail(DP_ERR_OOM, m->last_error);
 
-  // weights: theta in FP64 and FP32, transposed fitting weights, normalisation stats
-  std::vector<float> t32(P.theta.begin(), P.theta.end());
-  std::vector<double> wT(tsz * nt);
-  const size_t emb_total = (size_t)nt * nt * kEmbParams;
-  for (int t = 0; t < nt; ++t) {
-    const double* Pf = P.theta.data() + emb_total + (size_t)t * kFitParams;
-    double* dst = wT.data() + t * tsz;
-    for (int k = 0; k < kKD; ++k)
-      for (int o = 0; o < kF; ++o) dst[(size_t)o * kKD + k] = Pf[kFW1 + (size_t)k * kF + o];
-    double* d2 = dst + (size_t)kF * kKD;
-    double* d3 = d2 + (size_t)kF * kF;
-    for (int k = 0; k < kF; ++k)
-      for (int o = 0; o < kF; ++o) {
-        d2[(size_t)o * kF + k] = Pf[kFW2 + (size_t)k * kF + o];
-        d3[(size_t)o * kF + k] = Pf[kFW3 + (size_t)k * kF + o];
-      }
+  {
+    dp_status s1 = upload_weights(m);
+    if (s1 != DP_OK) return fail(s1, m->last_error);
   }
-  std::vector<float> wT32(wT.begin(), wT.end());
-  std::vector<double> stat(8 * nt);
-  for (int q = 0; q < 4 * nt; ++q) { stat[q] = P.davg[q]; stat[4 * nt + q] = 1.0 / P.dstd[q]; }
-  std::vector<float> stat32(stat.begin(), stat.end());
-  auto up = [&](void* dst, const void* src, size_t bytes) {
-    return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
-  };
-  if (!up(m->w64, P.theta.data(), 8 * P.theta.size()) || !up(m->w32, t32.data(), 4 * t32.size()) ||
-      !up(m->fitT64, wT.data(), 8 * wT.size()) || !up(m->fitT32, wT32.data(), 4 * wT32.size()) ||
-      !up(m->stat64, stat.data(), 8 * stat.size()) || !up(m->stat32, stat32.data(), 4 * stat32.size()))
-    return fail(DP_ERR_CUDA, "weight upload failed");
   if (cudaMemset(m->err, 0, 16) != cudaSuccess) return fail(DP_ERR_CUDA, "memset failed");
-  if (prec == DP_MIX_BF16 || prec == DP_MIX_FP16) {
-    dp_status s2 = launch_tc_setup(m);
-    if (s2 != DP_OK) return fail(s2, m->last_error);
-  }
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(DP_ERR_CUDA, "device sync after create failed");
   *out = h;
   return DP_OK;
@@ -532,6 +541,20 @@ dp_status dp_verlet_step(dp_model* h, dp_md_state* st, double dt_fs, int nsteps,
 dp_status dp_md_run_batch(dp_model* h, dp_md_state* st, double dt_fs, int nsteps) {
   if (!h) return DP_ERR_ARG;
   return run_md(&h->m, st, dt_fs, nsteps, 1);
+}
+
+dp_status dp_set_params(dp_model* h, const double* theta, long long ntheta) {
+  if (!h) return DP_ERR_ARG;
+  Model* m = &h->m;
+  if (!theta) { m->last_error = "null theta"; return DP_ERR_ARG; }
+  if (ntheta != m->ntheta) { m->last_error = "ntheta does not match the model"; return DP_ERR_ARG; }
+  for (long long q = 0; q < ntheta; ++q)
+    if (!std::isfinite(theta[q])) { m->last_error = "non-finite parameter"; return DP_ERR_WEIGHTS; }
+  DP_CUDA_TRY(m, cudaStreamSynchronize(m->stream));
+  m->theta_host.assign(theta, theta + ntheta);
+  DP_TRY(upload_weights(m));
+  DP_CUDA_TRY(m, cudaDeviceSynchronize());
+  return DP_OK;
 }
 
 long long dp_ntheta(const dp_model* h) { return h ? h->m.ntheta : 0; }
