@@ -210,7 +210,8 @@ N_SMS = 152
 # 32,000-atom copper capture, per real neighbour row; scaled to a launch by the row count.
 # Only valid while the kernel is unchanged since the capture (see profiles/).
 TRAFFIC_PER_ROW = {
-    ("embedding_forward", "mix_fp16"): (95.655424e6 + 20.975872e6) / 5726060,  # profiles/k_mix_embed_fwd_cu32k.md
+    ("embedding_backward", "mix_fp16"): (174.184192e6 + 5.281792e6) / 5726060,  # profiles/k_mix_embed_bwd_cu32k.md
+    ("embedding_forward", "mix_fp16"): (95.653888e6 + 20.996608e6) / 5726060,  # profiles/k_mix_embed_fwd_cu32k.md
 }
 
 
@@ -367,11 +368,13 @@ def batch_leg(args, stream):
         torch.cuda.synchronize()
         m.sync()
         ms = ev0.elapsed_time(ev1) / args.batch_steps
+        grids = m.autotune(0)  # launch grids the autotuner chose on the first call
         m.close()
     return {"workload": f"256 H2O replicas, 32..2048 molecules each ({N} atoms), r_c 6 A, sel 46/92, "
                         f"NVE dt 0.5 fs, rebuild every {REBUILD} steps",
             "value": N / (ms * 1e-3), "unit": "atom-steps/s", "ms_per_step": ms, "steps": args.batch_steps,
-            "replicas": len(reps), "natoms": N}
+            "replicas": len(reps), "natoms": N,
+            "autotuned_grids": dict(zip(["embedding_forward", "embedding_backward", "dE_dT", "descriptor"], grids))}
 
 
 def fp64_compare(args, s, w, v0, m_mixed, stream):

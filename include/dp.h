@@ -150,11 +150,25 @@ dp_status dp_verlet_step(dp_model* m, dp_md_state* st, double dt_fs, int nsteps,
  * dp_md_run_batch -- dp_verlet_step for many replicas of uneven size (st->nrep
  * boxes, atoms concatenated by st->atom_offsets).  Every phase is one launch over
  * the atoms and neighbour rows of all replicas (the kernels walk the concatenated
- * arrays; the grids follow from the kernels' occupancy), and the steps between
- * neighbour rebuilds always run as a captured CUDA graph.  Energies, kinetic
- * energies and virials are reported per replica.
+ * arrays), and the steps between neighbour rebuilds always run as a captured CUDA
+ * graph.  On the first call for a configuration (precision, atoms, replicas) the
+ * launch grids are chosen by the autotuner (dp_autotune; choices cached per process)
+ * before the graph is captured.  Energies, kinetic energies and virials are reported
+ * per replica.
  */
 dp_status dp_md_run_batch(dp_model* m, dp_md_state* st, double dt_fs, int nsteps);
+
+/*
+ * dp_autotune -- time the candidate launch grids of the mixed-precision kernels whose
+ * shape is a choice (embedding forward and backward: 1, 2, 3 or 6 CTAs per SM; the
+ * dE/dT and descriptor kernels) over `repeats` full force evaluations each, on the
+ * model's current state (after dp_compute or an MD call), and keep the fastest.
+ * grids[4] (host, nullable) receives the chosen grids (embedding forward, embedding
+ * backward, dE/dT, descriptor; 0 = not tuned, as for FP64 / FP32 models).  Drops the
+ * model's captured MD graphs; leaves the forces of the chosen configuration; synchronous.
+ * repeats = 0 only reports the current choices.
+ */
+dp_status dp_autotune(dp_model* m, int repeats, int* grids);
 
 /*
  * dp_param_grad -- gradient of the loss

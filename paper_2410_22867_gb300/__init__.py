@@ -31,7 +31,7 @@ STATUS = {0: "DP_OK", 1: "DP_ERR_ARG", 2: "DP_ERR_CUDA", 3: "DP_ERR_OOM", 4: "DP
 # exported symbols of include/dp.h
 EXPORTS = ("dp_create", "dp_compute", "dp_compute_batch", "dp_verlet_step", "dp_md_run_batch", "dp_param_grad",
            "dp_ntheta", "dp_get_nlist", "dp_phase_times", "dp_kernel_launches", "dp_sync", "dp_last_error",
-           "dp_destroy", "dp_version", "dp_selftest", "dp_selftest_noalloc", "dp_set_params")
+           "dp_destroy", "dp_version", "dp_selftest", "dp_selftest_noalloc", "dp_set_params", "dp_autotune")
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -86,9 +86,10 @@ def lib():
             L.dp_selftest.argtypes = [_I, _P]
             L.dp_selftest_noalloc.argtypes = [_P, _I, _P]
             L.dp_set_params.argtypes = [_P, _P, ctypes.c_longlong]
+            L.dp_autotune.argtypes = [_P, _I, _P]
             for name in ("dp_create", "dp_compute", "dp_compute_batch", "dp_verlet_step", "dp_md_run_batch",
                          "dp_param_grad", "dp_get_nlist", "dp_phase_times", "dp_sync", "dp_selftest",
-                         "dp_selftest_noalloc", "dp_set_params"):
+                         "dp_selftest_noalloc", "dp_set_params", "dp_autotune"):
                 getattr(L, name).restype = _I
             _lib = L
     return _lib
@@ -266,6 +267,14 @@ class DPModel:
         ms = (ctypes.c_float * 8)()
         self._check(lib().dp_phase_times(self.h, int(repeats), ctypes.cast(ms, _P)))
         return list(ms)[:7]
+
+    def autotune(self, repeats: int = 3):
+        """dp_autotune: choose the launch grids of the mixed kernels on the current state;
+        returns [embedding forward, embedding backward, dE/dT, descriptor] (0 = not tuned).
+        repeats = 0 only reports the current choices."""
+        g = (ctypes.c_int * 4)()
+        self._check(lib().dp_autotune(self.h, int(repeats), ctypes.cast(g, _P)))
+        return list(g)
 
     def kernel_launches(self) -> int:
         return int(lib().dp_kernel_launches(self.h))

@@ -5,7 +5,10 @@
 // allocated in the initial phase, no dynamic allocation during the run).
 #include <cmath>
 #include <cstdio>
+#include <array>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -267,7 +270,86 @@ dp_status capture_step(Model* m, int N, double dt, bool rebuild, cudaGraphExec_t
   return DP_OK;
 }
 
-dp_status run_md(Model* m, dp_md_state* st, double dt, int nsteps, int capture) {
+// ---------------------------------------------------------------- autotuner
+// Launch grids of the mixed-precision kernels whose shape is a real choice: the two embedding
+// kernels (CTAs per SM, which also sets the length of each CTA's contiguous row chunk and so
+// the balance between tail effects and atoms split across CTAs), the dE/dT and the descriptor
+// kernels.  Each candidate is timed over full force evaluations on the model's current state
+// (CUDA events on its stream); the fastest is kept.  Choices are cached per process by
+// (precision, atoms, replicas, types, SMs).
+std::mutex g_tune_mu;
+std::map<unsigned long long, std::array<int, 4>> g_tune_cache;
+
+unsigned long long tune_key(const Model* m, int N) {
+  unsigned long long k = 1469598103934665603ull;
+  auto mix = [&](unsigned long long v) { k = (k ^ v) * 1099511628211ull; };
+  mix((unsigned long long)m->prec); mix((unsigned long long)N); mix((unsigned long long)m->nrep);
+  mix((unsigned long long)m->ntypes); mix((unsigned long long)num_sms());
+  return k == 0 ? 1 : k;
+}
+
+dp_status autotune(Model* m, int N, int repeats) {
+  if (!is_mixed(m)) return DP_OK;  // the SIMT paths have no tunable launch shapes
+  const int sms = num_sms();
+  const std::vector<int> cand[4] = {{1 * sms, 2 * sms, 3 * sms, 6 * sms},
+                                    {1 * sms, 2 * sms, 3 * sms, 6 * sms},
+                                    {2 * sms, 4 * sms, 5 * sms, 10 * sms},
+                                    {4 * sms, 8 * sms, 16 * sms}};
+  cudaEvent_t e0, e1;
+  DP_CUDA_TRY(m, cudaEventCreate(&e0));
+  DP_CUDA_TRY(m, cudaEventCreate(&e1));
+  dp_status st = DP_OK;
+  for (int k = 0; k < 4 && st == DP_OK; ++k) {
+    float best = 1e30f;
+    int pick = 0;
+    for (int c : cand[k]) {
+      m->tune_grid[k] = c;
+      if ((st = force_eval(m, N)) != DP_OK) break;  // warm
+      cudaEventRecord(e0, m->stream);
+      for (int r = 0; r < repeats && st == DP_OK; ++r) st = force_eval(m, N);
+      cudaEventRecord(e1, m->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { m->last_error = "autotune timing failed"; st = DP_ERR_CUDA; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (st == DP_OK && ms < best) { best = ms; pick = c; }
+    }
+    m->tune_grid[k] = pick;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == DP_OK) st = force_eval(m, N);  // leave forces of the chosen configuration
+  return st;
+}
+
+// Apply cached choices or tune; returns whether the launch configuration changed.
+dp_status ensure_tuned(Model* m, int N, bool* changed) {
+  *changed = false;
+  if (!is_mixed(m)) return DP_OK;
+  const unsigned long long key = tune_key(m, N);
+  if (m->tuned_key == key) return DP_OK;
+  std::array<int, 4> old{m->tune_grid[0], m->tune_grid[1], m->tune_grid[2], m->tune_grid[3]};
+  bool hit = false;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      for (int k = 0; k < 4; ++k) m->tune_grid[k] = it->second[k];
+      hit = true;
+    }
+  }
+  if (hit) {
+    DP_TRY(force_eval(m, N));
+  } else {
+    DP_TRY(autotune(m, N, 3));
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = {m->tune_grid[0], m->tune_grid[1], m->tune_grid[2], m->tune_grid[3]};
+  }
+  m->tuned_key = key;
+  for (int k = 0; k < 4; ++k) *changed = *changed || (old[k] != m->tune_grid[k]);
+  return DP_OK;
+}
+
+dp_status run_md(Model* m, dp_md_state* st, double dt, int nsteps, int capture, bool tune = false) {
   if (!st || !st->x || !st->v || !st->types || !st->mass_by_type || !st->boxes) {
     m->last_error = "dp_md_state has a null pointer";
     return DP_ERR_ARG;
@@ -298,6 +380,11 @@ dp_status run_md(Model* m, dp_md_state* st, double dt, int nsteps, int capture) 
     DP_TRY(force_eval(m, N));
   }
   GraphCache& gc = gcache(m);
+  if (tune) {
+    bool changed = false;
+    DP_TRY(ensure_tuned(m, N, &changed));
+    if (changed) drop_graphs(m);  // captured graphs hold the old launch shapes
+  }
   if (capture) {
     unsigned long long h = hash_geom(m);
     if (gc.N != N || gc.nrep != nrep || gc.dt != dt || gc.geom_hash != h) {
@@ -540,7 +627,29 @@ dp_status dp_verlet_step(dp_model* h, dp_md_state* st, double dt_fs, int nsteps,
 
 dp_status dp_md_run_batch(dp_model* h, dp_md_state* st, double dt_fs, int nsteps) {
   if (!h) return DP_ERR_ARG;
-  return run_md(&h->m, st, dt_fs, nsteps, 1);
+  return run_md(&h->m, st, dt_fs, nsteps, 1, true);
+}
+
+dp_status dp_autotune(dp_model* h, int repeats, int* grids) {
+  if (!h || repeats < 0) return DP_ERR_ARG;
+  Model* m = &h->m;
+  if (repeats == 0) {  // query only
+    if (grids)
+      for (int k = 0; k < 4; ++k) grids[k] = m->tune_grid[k];
+    return DP_OK;
+  }
+  if (m->natoms < 1) { m->last_error = "no state to tune on"; return DP_ERR_ARG; }
+  drop_graphs(m);
+  DP_TRY(autotune(m, m->natoms, repeats));
+  m->tuned_key = tune_key(m, m->natoms);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[m->tuned_key] = {m->tune_grid[0], m->tune_grid[1], m->tune_grid[2], m->tune_grid[3]};
+  }
+  if (grids)
+    for (int k = 0; k < 4; ++k) grids[k] = m->tune_grid[k];
+  DP_CUDA_TRY(m, cudaStreamSynchronize(m->stream));
+  return DP_OK;
 }
 
 dp_status dp_set_params(dp_model* h, const double* theta, long long ntheta) {

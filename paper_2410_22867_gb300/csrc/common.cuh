@@ -166,6 +166,10 @@ struct Model {
   bool md_valid = false;      // internal x, v, F, lists belong to the last MD call
   long long launches = 0;     // kernels launched (graph replays add their kernel count)
   cudaEvent_t sub_ev[2] = {nullptr, nullptr};  // set only inside dp_phase_times: kernel-level split
+  // launch grids chosen by dp_autotune (0 = occupancy default): embedding forward,
+  // embedding backward, dE/dT, descriptor
+  int tune_grid[4] = {0, 0, 0, 0};
+  unsigned long long tuned_key = 0;
   cudaGraphExec_t graph_exec = nullptr;
   int graph_key[4] = {0, 0, 0, 0};
 };
@@ -265,6 +269,8 @@ dp_status launch_mix_embed_backward(Model* m, int N);
 dp_status mix_fit_setup(Model* m);
 size_t mix_fit_weight_bytes(int ntypes);
 dp_status launch_mix_fitting(Model* m, int N);
+// grid of a tunable mixed kernel: the autotuned value if set, else the default
+inline int tuned_grid(const Model* m, int which, int dflt) { return m->tune_grid[which] > 0 ? m->tune_grid[which] : dflt; }
 // parameter gradient (pgrad.cu)
 size_t param_grad_workspace_bytes(int cap, bool fp64);
 dp_status launch_param_grad(Model* m, int N, const double* F0, double E0, double cE, double cF, double* grad,

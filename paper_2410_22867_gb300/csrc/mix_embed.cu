@@ -967,11 +967,11 @@ dp_status launch_mix_descriptor(Model* m, int N) {
   const void* fn = f16 ? reinterpret_cast<const void*>(k_mix_embed_fwd<true>)
                        : reinterpret_cast<const void*>(k_mix_embed_fwd<false>);
   DP_CUDA_TRY(m, ensure_smem(fn, kFwdSmem));
-  const int grid = num_sms() * blocks_per_sm(fn, kRows, kFwdSmem, kTmemCols);
+  const int grid = tuned_grid(m, 0, num_sms() * blocks_per_sm(fn, kRows, kFwdSmem, kTmemCols));
   if (f16) k_mix_embed_fwd<true><<<grid, kRows, kFwdSmem, m->stream>>>(a);
   else k_mix_embed_fwd<false><<<grid, kRows, kFwdSmem, m->stream>>>(a);
   if (m->sub_ev[0]) DP_CUDA_TRY(m, cudaEventRecord(m->sub_ev[0], m->stream));
-  const int dgrid = std::max(1, std::min((N + kDescWarps - 1) / kDescWarps, 8 * num_sms()));
+  const int dgrid = std::max(1, std::min((N + kDescWarps - 1) / kDescWarps, tuned_grid(m, 3, 8 * num_sms())));
   if (f16)
     k_mix_descriptor<true><<<dgrid, 32 * kDescWarps, 0, m->stream>>>(
         N, m->ntypes, 1.f / (float)m->S, m->Tseg, static_cast<float*>(m->Tm), static_cast<unsigned short*>(m->Dm));
@@ -984,7 +984,7 @@ dp_status launch_mix_descriptor(Model* m, int N) {
 }
 
 dp_status launch_mix_embed_backward(Model* m, int N) {
-  const int dt_grid = std::max(1, std::min((N + kDtWarps - 1) / kDtWarps, 5 * num_sms()));
+  const int dt_grid = std::max(1, std::min((N + kDtWarps - 1) / kDtWarps, tuned_grid(m, 2, 5 * num_sms())));
   k_mix_dT<<<dt_grid, 32 * kDtWarps, 0, m->stream>>>(N, 1.f / (float)m->S, static_cast<const float*>(m->Tm),
                                                               static_cast<const unsigned short*>(m->dD),
                                                               static_cast<float4*>(m->dTm));
@@ -996,7 +996,7 @@ dp_status launch_mix_embed_backward(Model* m, int N) {
   const void* fn = f16 ? reinterpret_cast<const void*>(k_mix_embed_bwd<true>)
                        : reinterpret_cast<const void*>(k_mix_embed_bwd<false>);
   DP_CUDA_TRY(m, ensure_smem(fn, kBwdSmem));
-  const int grid = num_sms() * blocks_per_sm(fn, kRows, kBwdSmem, kTmemCols);
+  const int grid = tuned_grid(m, 1, num_sms() * blocks_per_sm(fn, kRows, kBwdSmem, kTmemCols));
   if (f16) k_mix_embed_bwd<true><<<grid, kRows, kBwdSmem, m->stream>>>(a);
   else k_mix_embed_bwd<false><<<grid, kRows, kBwdSmem, m->stream>>>(a);
   k_fold_force32<<<cdiv(3L * N, 256), 256, 0, m->stream>>>(3 * N, m->force32, m->force);

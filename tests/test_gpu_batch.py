@@ -125,3 +125,34 @@ def test_md_batch_through_close_encounter(dp, water_weights):
     assert e_gpu == pytest.approx(e_ref, rel=1e-9)
     np.testing.assert_allclose(x[offs[0]:offs[1]].cpu().numpy(), ref["x"], atol=1e-8)
     m.close()
+
+
+def test_autotune_choices_and_results(dp, water_weights):
+    reps = synth.water_replicas(16, 21, lo=32, hi=400)
+    coords, types, offs, boxes = synth.concat(reps)
+    m = dp.DPModel(water_weights, "mix_fp16", max_atoms=len(types), max_replicas=len(reps))
+    x = torch.tensor(coords, device="cuda")
+    t = torch.tensor(types, device="cuda")
+    ref = m.compute_batch(x, t, offs, boxes)
+    e_ref = ref["energy"].cpu().numpy()
+    f_ref = ref["forces"].cpu().numpy()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    grids = m.autotune(2)
+    allowed = [{1, 2, 3, 6}, {1, 2, 3, 6}, {2, 4, 5, 10}, {4, 8, 16}]
+    for g, ok in zip(grids, allowed):
+        assert g % sms == 0 and g // sms in ok, grids
+    assert m.autotune(0) == grids
+    # other launch shapes change only the order of FP32 atomic sums, which can flip a 16-bit
+    # rounding downstream (one fp16 ulp ~ 5e-4 relative): compare at the mixed-precision level
+    out = m.compute_batch(x, t, offs, boxes)
+    np.testing.assert_allclose(out["energy"].cpu().numpy(), e_ref, rtol=1e-6)
+    f = out["forces"].cpu().numpy()
+    assert np.sqrt(((f - f_ref) ** 2).mean()) <= 1e-3 * np.sqrt((f_ref ** 2).mean())
+    m.close()
+    # dp_md_run_batch tunes on its first call
+    v0 = _velocities(reps, 3)
+    m2, st, x2, v2, offs2 = _batch_state(dp, water_weights, reps, v0, "mix_fp16")
+    assert m2.autotune(0) == [0, 0, 0, 0]
+    m2.md_run_batch(st, 0.5, 2)
+    assert all(g > 0 for g in m2.autotune(0))
+    m2.close()
