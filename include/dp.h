@@ -141,7 +141,8 @@ typedef struct {
  *   kappa = 9.648533e-3 A fs^-2 per eV A^-1 amu^-1.
  * Positions and velocities stay FP64 in every precision.  With capture_graph
  * != 0 the steps between rebuilds are captured once into a CUDA graph and
- * replayed.  The state's x and v are read at the start and written at the end
+ * replayed; before the first capture for a configuration the launch grids of the
+ * mixed-precision kernels are chosen by the autotuner (dp_autotune).  The state's x and v are read at the start and written at the end
  * of the call.  Works for one replica or many (nrep > 1).
  */
 dp_status dp_verlet_step(dp_model* m, dp_md_state* st, double dt_fs, int nsteps, int capture_graph);

@@ -622,7 +622,7 @@ dp_status dp_compute(dp_model* h, int natoms, const double* coords, const int* t
 
 dp_status dp_verlet_step(dp_model* h, dp_md_state* st, double dt_fs, int nsteps, int capture_graph) {
   if (!h) return DP_ERR_ARG;
-  return run_md(&h->m, st, dt_fs, nsteps, capture_graph);
+  return run_md(&h->m, st, dt_fs, nsteps, capture_graph, capture_graph != 0);
 }
 
 dp_status dp_md_run_batch(dp_model* h, dp_md_state* st, double dt_fs, int nsteps) {
