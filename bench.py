@@ -311,6 +311,9 @@ def run_mine(args, world, rank, local):
         # FP64 comparison (speed and error) on the same configuration
         if not args.no_fp64 and prec != "fp64":
             extra["fp64"] = fp64_compare(args, s, w, v0, m, stream)
+        # the water box of the same model family
+        if args.water_steps > 0 and args.workload != "water12k":
+            extra["water"] = water_leg(args, stream)
         # batched replicas (dp_md_run_batch)
         if args.batch_steps > 0:
             extra["batch"] = batch_leg(args, stream)
@@ -336,7 +339,9 @@ def run_mine(args, world, rank, local):
                            "l2": "working set per step > 1 GB, larger than the 129 MB L2; no flush",
                            "parallelism": "replicas" if world > 1 else "1 GPU"},
                 "ns_per_day": (1e3 / ms_step) * DT_FS * 86400 * 1e-6,
-                "gpu_launches": launches, "clocks": ck}
+                "gpu_launches": launches, "clocks": ck,
+                "context": {"paper_ns_per_day": 149.0, "paper_prior_ns_per_day": 4.7,
+                            "paper_hardware": "12,000 Fugaku A64FX nodes, 0.54 M atoms Cu, dt 1 fs (context only)"}}
         line.update(extra)
         print(json.dumps(line), flush=True)
 
@@ -358,7 +363,8 @@ def batch_leg(args, stream):
         v = torch.tensor(v0, device="cuda")
         t = torch.tensor(types, device="cuda")
         st = m.md_state(x, v, t, boxes, reps[0].masses(), atom_offsets=offs, rebuild_every=REBUILD)
-        m.md_run_batch(st, DT_FS, 3)
+        keep = m.md_run_batch(st, DT_FS, 3)
+        e_start = (keep["potential"] + keep["kinetic"]).cpu().numpy().copy()
         st.resume = 1
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -368,13 +374,45 @@ def batch_leg(args, stream):
         torch.cuda.synchronize()
         m.sync()
         ms = ev0.elapsed_time(ev1) / args.batch_steps
+        e_end = (keep["potential"] + keep["kinetic"]).cpu().numpy()
+        nat = np.diff(np.asarray(offs))
+        drift = np.abs(e_end - e_start) / nat
         grids = m.autotune(0)  # launch grids the autotuner chose on the first call
         m.close()
     return {"workload": f"256 H2O replicas, 32..2048 molecules each ({N} atoms), r_c 6 A, sel 46/92, "
                         f"NVE dt 0.5 fs, rebuild every {REBUILD} steps",
             "value": N / (ms * 1e-3), "unit": "atom-steps/s", "ms_per_step": ms, "steps": args.batch_steps,
             "replicas": len(reps), "natoms": N,
+            "energy_drift_eV_per_atom": {"max": float(drift.max()), "mean": float(drift.mean()),
+                                         "over_steps": args.batch_steps},
             "autotuned_grids": dict(zip(["embedding_forward", "embedding_backward", "dE_dT", "descriptor"], grids))}
+
+
+def water_leg(args, stream):
+    """Throughput of the 4096-H2O box (12,288 atoms) in the same precision: MD with graph
+    replay; the window stays before the first random-weight collapse (step ~31)."""
+    import torch
+    import paper_2410_22867_gb300 as dp
+    s, w, v0 = load_workload("water12k")
+    with torch.cuda.stream(stream):
+        m = dp.DPModel(w, args.precision, max_atoms=s.natoms, skin=2.0, stream=stream)
+        x = torch.tensor(s.coords, device="cuda")
+        v = torch.tensor(v0, device="cuda")
+        t = torch.tensor(s.types, device="cuda")
+        st = m.md_state(x, v, t, s.box, s.masses(), rebuild_every=REBUILD)
+        m.verlet(st, DT_FS, 3)
+        st.resume = 1
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        m.verlet(st, DT_FS, args.water_steps, capture_graph=True, sync=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        m.sync()
+        ms = ev0.elapsed_time(ev1) / args.water_steps
+        m.close()
+    return {"workload": WORKLOADS["water12k"], "value": s.natoms / (ms * 1e-3), "unit": "atom-steps/s",
+            "ms_per_step": ms, "ns_per_day": (1e3 / ms) * DT_FS * 86400 * 1e-6, "steps": args.water_steps}
 
 
 def fp64_compare(args, s, w, v0, m_mixed, stream):
@@ -453,6 +491,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--phase-repeats", type=int, default=10)
     ap.add_argument("--batch-steps", type=int, default=22)  # + 3 warm-up: before the first collapse (step ~35)
+    ap.add_argument("--water-steps", type=int, default=20)  # + 4 warm-up: before the first collapse (step ~31)
     ap.add_argument("--no-fp64", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -316,3 +316,29 @@ def test_mixed_copper_subbox(dp, prec):
     assert rmse / np.sqrt((Fr ** 2).mean()) <= 0.05
     Ei = out["atom_energy"].cpu().numpy()[sub]
     assert abs(Ei.sum() - ref["atom_energy"][sub].sum()) / 4000 <= 1e-4
+
+
+def test_md_water12k_fp32_tracks_fp64(dp):
+    # 4096 H2O (12,288 atoms), 300 K, dt 0.5 fs, rebuild every 10 steps.  With random weights
+    # two atoms of this box collapse together between steps 31 and 41 in every precision (an
+    # untrained model has no short-range repulsion), so the run stops at 30 steps.
+    s = synth.water_box(4096, 0)
+    w = synth.water_weights()
+    v0 = synth.maxwell_boltzmann(s.masses()[s.types], 300.0, 1)
+    res = {}
+    for prec in ("fp64", "fp32"):
+        m = dp.DPModel(w, prec, max_atoms=s.natoms)
+        x = torch.tensor(s.coords, device="cuda")
+        v = torch.tensor(v0, device="cuda")
+        t = torch.tensor(s.types, device="cuda")
+        st = m.md_state(x, v, t, s.box, s.masses(), rebuild_every=10)
+        out = m.verlet(st, 0.5, 1)
+        e1 = out["potential"].item() + out["kinetic"].item()
+        st.resume = 1
+        out = m.verlet(st, 0.5, 29)
+        e30 = out["potential"].item() + out["kinetic"].item()
+        res[prec] = (x.cpu().numpy(), out["potential"].item(), abs(e30 - e1) / s.natoms)
+        m.close()
+    assert res["fp64"][2] <= 1e-6 and res["fp32"][2] <= 1e-6
+    assert np.abs(res["fp32"][0] - res["fp64"][0]).max() <= 1e-4
+    assert res["fp32"][1] == pytest.approx(res["fp64"][1], rel=1e-6)
