@@ -25,9 +25,11 @@ __global__ void k_unpermute(int N, const int* __restrict__ perm, const double* _
 }
 
 // One block per replica: fixed-order tree sums (deterministic).
+// Per-replica energy and virial: sums of the per-atom values (caller order), or for the
+// virial the per-replica accumulator vir_rep when the backward produced one.
 __global__ void k_rep_reduce(int nrep, const int* __restrict__ rep_off, const double* __restrict__ e_user,
-                             const double* __restrict__ vir_user, double* energy, double* virial,
-                             const int* __restrict__ err) {
+                             const double* __restrict__ vir_user, const double* __restrict__ vir_rep,
+                             double* energy, double* virial, const int* __restrict__ err) {
   __shared__ double part[10][256];
   int r = blockIdx.x;
   if (r >= nrep) return;
@@ -49,7 +51,7 @@ __global__ void k_rep_reduce(int nrep, const int* __restrict__ rep_off, const do
     bool bad = err && *err != 0;
     if (energy) energy[r] = bad ? __longlong_as_double(0x7ff8000000000000ll) : part[0][0];
     if (virial)
-      for (int q = 0; q < 9; ++q) virial[r * 9 + q] = part[1 + q][0];
+      for (int q = 0; q < 9; ++q) virial[r * 9 + q] = vir_rep ? vir_rep[r * 9 + q] : part[1 + q][0];
   }
 }
 
@@ -113,8 +115,9 @@ dp_status launch_outputs(Model* m, int N, double* energy_rep, double* atom_energ
                          double* virial_rep) {
   k_unpermute<<<cdiv(N, 256), 256, 0, m->stream>>>(N, m->perm, m->e_atom, m->vir_atom, m->force, m->e_user,
                                                    m->vir_user, forces);
-  k_rep_reduce<<<m->nrep, 256, 0, m->stream>>>(m->nrep, m->rep_off_dev, m->e_user, m->vir_user, energy_rep,
-                                                virial_rep, m->err);
+  const bool mixed = is_mixed(m);
+  k_rep_reduce<<<m->nrep, 256, 0, m->stream>>>(m->nrep, m->rep_off_dev, m->e_user, mixed ? nullptr : m->vir_user,
+                                                mixed ? m->vir_rep : nullptr, energy_rep, virial_rep, m->err);
   m->launches += 2;
   if (atom_energy)
     DP_CUDA_TRY(m, cudaMemcpyAsync(atom_energy, m->e_user, sizeof(double) * N, cudaMemcpyDeviceToDevice,
@@ -159,8 +162,8 @@ dp_status launch_store_state(Model* m, int N, double* x_user, double* v_user) {
 
 dp_status launch_kinetic(Model* m, int N, double* ke_rep) {
   k_kinetic_atoms<<<cdiv(N, 256), 256, 0, m->stream>>>(N, m->perm, m->v, m->mass, m->ke_user);
-  k_rep_reduce<<<m->nrep, 256, 0, m->stream>>>(m->nrep, m->rep_off_dev, m->ke_user, nullptr, ke_rep, nullptr,
-                                                nullptr);
+  k_rep_reduce<<<m->nrep, 256, 0, m->stream>>>(m->nrep, m->rep_off_dev, m->ke_user, nullptr, nullptr, ke_rep,
+                                                nullptr, nullptr);
   m->launches += 2;
   DP_LAUNCH_CHECK(m);
   return DP_OK;

@@ -42,7 +42,9 @@ struct MixArgs {
   const float4* dT;      // [N][100]: dE/dT[c][a] * (1/S), c in x..w
   double* force;         // [N][3]
   float* force32;        // [N][3] FP32 accumulator (folded into force after the backward)
-  double* vir_atom;      // [N][9]
+  double* vir_atom;      // [N][9] (unused by the mixed backward)
+  double* vir_rep;       // [nrep][9] per-replica virial
+  const int* irep;       // [N] replica of each internal atom
   int* err;
 };
 
@@ -564,6 +566,12 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
   walk_tables(a, s_tot, s_tiend);
   __syncthreads();
   Walk wk{0, 0, -1};
+  // per-thread virial -sum g (x) d over this thread's rows, per replica (flushed with FP64
+  // atomics when the replica changes and at the end)
+  float vacc[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) vacc[q] = 0.f;
+  int vrep = -1;
   const uint32_t id64 = tc::idesc_f16(128, 64, F16);
   const uint32_t id128 = tc::idesc_f16(128, 128, F16);
   const uint32_t idH2 = tc::idesc_mn(tc::idesc_f16(128, 64, F16), false, true);
@@ -740,15 +748,24 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
       for (int c = 0; c < 3; ++c) g3[c] = common * f.d[c] + qv * dR[1 + c];
 #pragma unroll
       for (int c = 0; c < 3; ++c) atomicAdd(&a.force32[3 * (size_t)f.j + c], -g3[c]);
+      const int rep = a.irep[f.atom];
+      if (rep != vrep) {
+        if (vrep >= 0)
+#pragma unroll
+          for (int q = 0; q < 9; ++q) atomicAdd(&a.vir_rep[9 * vrep + q], (double)vacc[q]);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) vacc[q] = 0.f;
+        vrep = rep;
+      }
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) vacc[3 * p + q] = fmaf(-g3[p], f.d[q], vacc[3 * p + q]);
     }
-    // centre force and per-atom virial: warp-segmented sums over rows of the same atom
-    float vals[12];
+    // centre force: warp-segmented sums over rows of the same atom
+    float vals[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) vals[c] = g3[c];
-#pragma unroll
-    for (int p = 0; p < 3; ++p)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) vals[3 + 3 * p + q] = -g3[p] * f.d[q];
     const int my = valid ? f.la : -1;
     unsigned todo = __ballot_sync(0xffffffffu, valid);
     while (todo) {
@@ -757,20 +774,34 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
       const bool in = (my == seg);
       const unsigned mask = __ballot_sync(0xffffffffu, in);
 #pragma unroll
-      for (int q = 0; q < 12; ++q) {
+      for (int q = 0; q < 3; ++q) {
         float v = in ? vals[q] : 0.f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == leader) {
-          const size_t atom = (size_t)ti.a0 + seg;
-          if (q < 3) atomicAdd(&a.force32[3 * atom + q], v);
-          else atomicAdd(&a.vir_atom[9 * atom + q - 3], (double)v);
-        }
+        if (lane == leader) atomicAdd(&a.force32[3 * ((size_t)ti.a0 + seg) + q], v);
       }
       todo &= ~mask;
     }
     __syncthreads();
     cur += ti.nrows;
+  }
+  // flush the virial accumulators: one warp reduction when all lanes hold the same replica
+  {
+    const int r0 = __shfl_sync(0xffffffffu, vrep, 0);
+    if (__all_sync(0xffffffffu, vrep == r0)) {
+      if (r0 >= 0) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          float v = vacc[q];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) atomicAdd(&a.vir_rep[9 * r0 + q], (double)v);
+        }
+      }
+    } else if (vrep >= 0) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) atomicAdd(&a.vir_rep[9 * vrep + q], (double)vacc[q]);
+    }
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -949,6 +980,7 @@ MixArgs make_mix_args(Model* m, int N) {
   a.nl_j = m->nl_j; a.nl_d = static_cast<const float4*>(m->nl_d);
   a.Tseg = m->Tseg; a.dT = static_cast<const float4*>(m->dTm);
   a.force = m->force; a.force32 = m->force32; a.vir_atom = m->vir_atom; a.err = m->err;
+  a.vir_rep = m->vir_rep; a.irep = m->irep;
   return a;
 }
 
@@ -988,7 +1020,7 @@ dp_status launch_mix_embed_backward(Model* m, int N) {
   k_mix_dT<<<dt_grid, 32 * kDtWarps, 0, m->stream>>>(N, 1.f / (float)m->S, static_cast<const float*>(m->Tm),
                                                               static_cast<const unsigned short*>(m->dD),
                                                               static_cast<float4*>(m->dTm));
-  DP_CUDA_TRY(m, cudaMemsetAsync(m->vir_atom, 0, sizeof(double) * 9 * (size_t)N, m->stream));
+  DP_CUDA_TRY(m, cudaMemsetAsync(m->vir_rep, 0, sizeof(double) * 9 * (size_t)m->nrep, m->stream));
   DP_CUDA_TRY(m, cudaMemsetAsync(m->force32, 0, sizeof(float) * 3 * (size_t)N, m->stream));
   if (m->sub_ev[1]) DP_CUDA_TRY(m, cudaEventRecord(m->sub_ev[1], m->stream));
   MixArgs a = make_mix_args(m, N);
