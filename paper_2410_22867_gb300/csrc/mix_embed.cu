@@ -577,8 +577,10 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
   const uint32_t idH2 = tc::idesc_mn(tc::idesc_f16(128, 64, F16), false, true);
   const uint32_t idH1 = tc::idesc_mn(tc::idesc_f16(128, 32, F16), false, true);
 
+  // the first tile is located here; each later one by warp 0 in the middle of the previous
+  // tile (after the last read of sti / sRow), with its data prefetched into L2
+  if (w == 0 && c0 < c1) locate_tile(a, c0, c0, c1, wk, s_tot, s_tiend, &sti, sRow);
   for (int cur = c0; cur < c1 && ok;) {
-    if (w == 0) locate_tile(a, cur, c0, c1, wk, s_tot, s_tiend, &sti, sRow);
     __syncthreads();
     const TileInfo ti = sti;
     const int np = ti.ti * a.ntypes + ti.tj;
@@ -672,7 +674,22 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
       tc::mma_commit(&bar);
     }
     __syncwarp();
+    // while the MMA runs: locate the next tile and prefetch its rows and dE/dT into L2
+    if (w == 0 && cur + ti.nrows < c1) locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow);
     mma_sync_wait(&bar, phase, a.err, ok);
+    if (cur + ti.nrows < c1) {
+      __syncthreads();  // the next tile's sti / sRow
+      const TileInfo nx = sti;
+      if (t < nx.nrows) {
+        const int row = nx.p + t;
+        const int la = local_atom(sRow, row);
+        const size_t e = (size_t)(nx.a0 + la) * a.S + a.sel_off[nx.tj] + (row - sRow[la]);
+        tc::prefetch_l2(a.nl_d + e);
+        tc::prefetch_l2(a.nl_j + e);
+      }
+      const int nat = local_atom(sRow, nx.p + nx.nrows - 1) + 1;
+      if (t < nat * 13) tc::prefetch_l2(reinterpret_cast<const char*>(a.dT + (size_t)nx.a0 * kN3) + 128 * t);
+    }
     // layer-2 backward: g2 = dh2' + residual, dz2 = g2 (1 - t2^2) -> sA; h2's residual into dh1
     float dh1[kN1];
 #pragma unroll
