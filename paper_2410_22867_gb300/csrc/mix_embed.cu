@@ -323,8 +323,10 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     for (int c = 0; c < 4; ++c) tacc[s][c] = 0.f;
   long long carry = -1;  // (tj, atom) whose partial T sits in slot 0
 
+  // the first tile is located here; each later one by warp 0 during the previous tile's T
+  // product (the tile's own sRow facts are kept in registers by then)
+  if (w == 0 && c0 < c1) locate_tile(a, c0, c0, c1, wk, s_tot, s_tiend, &sti, sRow);
   for (int cur = c0; cur < c1 && ok;) {
-    if (w == 0) locate_tile(a, cur, c0, c1, wk, s_tot, s_tiend, &sti, sRow);
     // the R_hat^T operand starts from zero (rows of other atoms stay zero)
     {
       uint4* z = reinterpret_cast<uint4*>(sRs);
@@ -332,6 +334,13 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     }
     __syncthreads();
     const TileInfo ti = sti;
+    // the write-out's facts about this tile's atom slots (sRow is rewritten mid-tile)
+    const int last_la = local_atom(sRow, ti.p + ti.nrows - 1);
+    const bool last_done = (ti.p + ti.nrows == sRow[last_la + 1]);
+    unsigned shared_mask = 0u;
+#pragma unroll
+    for (int s = 0; s < kMaxAtoms; ++s)
+      if ((sRow[s] < ti.cs) || (sRow[s + 1] > ti.ce)) shared_mask |= 1u << s;
     const int np = ti.ti * a.ntypes + ti.tj;
     if (np != pair) {
       load_fwd_weights<F16>(a.w + (size_t)np * kEmbParams, sB2, sB3, small);
@@ -416,6 +425,18 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
       }
       tc::mma_commit(&bar);
     }
+    __syncwarp();
+    // while the T product runs: locate the next tile and prefetch its rows into L2
+    if (cur + ti.nrows < c1) {
+      if (w == 0) locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow);
+      __syncthreads();
+      const TileInfo nx = sti;
+      if (t < nx.nrows) {
+        const int row = nx.p + t;
+        const int la = local_atom(sRow, row);
+        tc::prefetch_l2(a.nl_d + (size_t)(nx.a0 + la) * a.S + a.sel_off[nx.tj] + (row - sRow[la]));
+      }
+    }
     mma_sync_wait(&bar, phase, a.err, ok);
     {
       float v[32];
@@ -428,14 +449,12 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
         for (int c = 0; c < 4; ++c) tacc[s][c] += v[4 * s + c];
     }
     // write complete atoms (feature t of each); carry the open one into slot 0
-    const int last_la = local_atom(sRow, ti.p + ti.nrows - 1);
-    const bool last_done = (ti.p + ti.nrows == sRow[last_la + 1]);
     const int n_out = last_done ? last_la + 1 : last_la;
     if (t < kN3) {
 #pragma unroll
       for (int s = 0; s < kMaxAtoms; ++s) {
         if (s < n_out) {
-          const bool shared = (sRow[s] < ti.cs) || (sRow[s + 1] > ti.ce);
+          const bool shared = (shared_mask >> s) & 1u;
           float* dst = a.Tseg + ((size_t)ti.tj * a.N + ti.a0 + s) * 400 + t;
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
