@@ -38,11 +38,15 @@ constexpr uint32_t kXLo = 4 * kBlk;       // X_lo: 4 blocks
 constexpr uint32_t kSt = 8 * kBlk;        // 64 KB: four split staging slots
 constexpr uint32_t kSSlot = 128 * 128;    // split job: [128 x 64] 16-bit weight block (16 KB)
 constexpr int kSSlots = 4;
-constexpr uint32_t kPrm = kSt + kSSlots * kSSlot;  // b1, b2, b3, w4
+constexpr uint32_t kStageRow = kBChunk * 2 + 16;  // padded row of the dE/dD staging tile (bytes)
 constexpr uint32_t kL1Slot = kBlk + kWB;  // L1 job: A block + W1T block (46 KB), slots over [0, kPrm)
 constexpr int kL1Slots = 4;
 constexpr uint32_t kB1Slot = kBChunk * 128;  // B1 job: W1 block [160 x 64] (20 KB), slots over [kXLo, kPrm)
-constexpr int kB1Slots = 6;
+constexpr int kB1Slots = 5;
+// dE/dD of one B1 chunk is staged here [128 rows x 160 fp16] and written out in whole row
+// segments; it overlays L1 slot 3 and the split slots, both idle during B1
+constexpr uint32_t kStage = kXLo + kB1Slots * kB1Slot;
+constexpr uint32_t kPrm = kStage + kFR * kStageRow;  // b1, b2, b3, w4
 constexpr int kSplitSlot = 6;             // barrier index of the first split staging slot (6..9)
 constexpr int kSplitJobs = 16;            // per split GEMM: 4 K blocks x 2 N halves x {hi, lo}
 constexpr int kL1Jobs = kKD / 64;         // 25
@@ -147,6 +151,7 @@ struct Issuer {
   int ty, row0;
   int* err;
   bool* ok;
+  uint64_t keep, stream;  // L2 policies: weights (evict_last), streamed D (evict_first)
   // Every CTA walks the shared weight matrices starting at a different block, so the
   // SMs do not all request the same L2 lines at the same moment.
   int rot_l1, rot_s, rot_b1;
@@ -161,15 +166,16 @@ struct Issuer {
     unsigned char* a = sm + k * kL1Slot;
     const int kb = l1_block(j);
     tc::mbar_arrive_expect_tx(&s->full[k], kL1Slot);
-    tc::tma_load_2d(a, &mp->D, &s->full[k], 64 * kb, row0);
-    tc::tma_load_2d(a + kBlk, &mp->W1T[ty], &s->full[k], 64 * kb, 0);
+    tc::tma_load_2d_hint(a, &mp->D, &s->full[k], 64 * kb, row0, stream);
+    tc::tma_load_2d_hint(a + kBlk, &mp->W1T[ty], &s->full[k], 64 * kb, 0, keep);
   }
   // B1 job j: W1 rows of chunk b1_chunk(j / 4), K block j % 4, into slot j % 6 (X_lo + split area)
   __device__ void load_b1(int j) {
     const int k = j % kB1Slots;
     slot_acquire(*s, k, s->uses[k], err, *ok);
     tc::mbar_arrive_expect_tx(&s->full[k], kB1Slot);
-    tc::tma_load_2d(sm + kXLo + k * kB1Slot, &mp->W1[ty], &s->full[k], 64 * (j & 3), kBChunk * b1_chunk(j >> 2));
+    tc::tma_load_2d_hint(sm + kXLo + k * kB1Slot, &mp->W1[ty], &s->full[k], 64 * (j & 3), kBChunk * b1_chunk(j >> 2),
+                         keep);
   }
   // split job i of GEMM g: weight half i & 1 (0 = hi, 1 = lo), N half (i >> 1) & 1 (rows 0..127
   // or 128..255; rows past 240 are zero-filled by the TMA) of K block split_block(i >> 2),
@@ -178,8 +184,8 @@ struct Issuer {
     const int k = kSplitSlot + (i & 3);
     slot_acquire(*s, k, s->uses[k], err, *ok);
     tc::mbar_arrive_expect_tx(&s->full[k], kSSlot);
-    tc::tma_load_2d(sm + kSt + (i & 3) * kSSlot, &mp->S[ty][g][i & 1], &s->full[k], 64 * split_block(i >> 2),
-                    128 * ((i >> 1) & 1));
+    tc::tma_load_2d_hint(sm + kSt + (i & 3) * kSSlot, &mp->S[ty][g][i & 1], &s->full[k], 64 * split_block(i >> 2),
+                         128 * ((i >> 1) & 1), keep);
   }
   // the first three jobs of split GEMM g (issued under the preceding epilogue)
   __device__ void prefetch_split(int g) {
@@ -238,6 +244,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
   const int c_beg = half ? 8 : 0, c_end = half ? 15 : 8;
   Issuer is;
   is.s = &sl; is.sm = sm; is.mp = &maps; is.err = a.err; is.ok = &ok;
+  is.keep = tc::make_policy_evict_last();
+  is.stream = tc::make_policy_evict_first();
   is.rot_l1 = blockIdx.x % kL1Jobs;
   is.rot_s = blockIdx.x & 3;
   is.rot_b1 = blockIdx.x % (kKD / kBChunk);
@@ -500,11 +508,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
       wait_acc(rg);
       const uint32_t src = rg ? acc1 : acc0;
 #pragma unroll 1
+      // this thread's 80 columns of its row into the staging tile (fp16)
       for (int c = half ? 5 : 0; c < (half ? 10 : 5); ++c) {
         float z[16];
         tc::tmem_ld16(src + 16 * c, z);
         tc::tmem_wait_ld();
-        if (valid) store_g16<true>(a.dD + grow * kKD + kBChunk * is.b1_chunk(n) + 16 * c, z);
+        uint32_t p[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) p[h] = tc::pack2<true>(z[2 * h], z[2 * h + 1]);
+        uint4* d = reinterpret_cast<uint4*>(sm + kStage + row * kStageRow + 32 * c);
+        d[0] = make_uint4(p[0], p[1], p[2], p[3]);
+        d[1] = make_uint4(p[4], p[5], p[6], p[7]);
+      }
+      __syncthreads();
+      // whole row segments (320 B) to dE/dD: warp w writes rows w, w + 8, ...; lanes 0..19
+      {
+        const int col0 = kBChunk * is.b1_chunk(n);
+        for (int r = w; r < nrow; r += kThreads / 32)
+          if ((t & 31) < kBChunk / 8) {
+            const uint4 v = *reinterpret_cast<const uint4*>(sm + kStage + r * kStageRow + 16 * (t & 31));
+            __stcs(reinterpret_cast<uint4*>(a.dD + (size_t)(row0 + r) * kKD + col0 + 8 * (t & 31)), v);
+          }
       }
       tc::tc_fence_before();
       __syncthreads();
@@ -597,7 +621,8 @@ FitMaps* maps_of(Model* m) {
 
 constexpr size_t kFitSmem = kPrm + 4 * kF * 4 + 1024;
 static_assert(kL1Slots * kL1Slot <= kPrm, "L1 slots exceed the staging area");
-static_assert(kXLo + kB1Slots * kB1Slot <= kPrm, "B1 slots exceed the staging area");
+static_assert(kXLo + kB1Slots * kB1Slot <= kStage, "B1 slots overlap the dE/dD staging tile");
+static_assert(kSt + kSSlots * kSSlot <= kPrm, "split slots exceed the staging area");
 
 }  // namespace
 
