@@ -53,20 +53,19 @@ __device__ __forceinline__ unsigned char* align1024(unsigned char* p) {
   return p + ((1024u - (a & 1023u)) & 1023u);
 }
 
-template <class T>
-__device__ __forceinline__ void switch_fn(T r, T rs, T rc, int kind, T& sw, T& dsw) {
-  if (r < rs) { sw = T(1); dsw = T(0); return; }
-  if (r >= rc) { sw = T(0); dsw = T(0); return; }
-  T w = rc - rs;
-  T u = (r - rs) / w;
+// Smooth switch sw(r) and its derivative; winv = 1 / (rc - rs).
+__device__ __forceinline__ void switch_fn(float r, float rs, float rc, float winv, int kind, float& sw, float& dsw) {
+  if (r < rs) { sw = 1.f; dsw = 0.f; return; }
+  if (r >= rc) { sw = 0.f; dsw = 0.f; return; }
+  const float u = (r - rs) * winv;
   if (kind == 1) {
-    const T pi = T(3.14159265358979323846);
-    sw = T(0.5) * cosf(pi * u) + T(0.5);
-    dsw = T(-0.5) * pi * sinf(pi * u) / w;
+    const float pi = 3.14159265358979323846f;
+    sw = 0.5f * cosf(pi * u) + 0.5f;
+    dsw = -0.5f * pi * sinf(pi * u) * winv;
   } else {
-    T u2 = u * u;
-    sw = u2 * u * (T(-6) * u2 + T(15) * u - T(10)) + T(1);
-    dsw = T(-30) * u2 * (u - T(1)) * (u - T(1)) / w;
+    const float u2 = u * u;
+    sw = u2 * u * (-6.f * u2 + 15.f * u - 10.f) + 1.f;
+    dsw = -30.f * u2 * (u - 1.f) * (u - 1.f) * winv;
   }
 }
 
@@ -91,26 +90,44 @@ __device__ void walk_tables(const MixArgs& a, int* tot, int* tiend) {
   }
 }
 
-// Warp 0 locates the tile starting at global row `cur` of chunk [c0, c1): one coalesced
-// load of 32 row offsets from the hint atom finds the first atom; a binary search runs
+// Warp 0, at the start of a tile: enters the stream of the next tile (starting at global row
+// `next`) and issues the load of the 32 row offsets from the hint atom.  The value is consumed
+// by locate_tile much later in the tile, so the load's latency is hidden.
+__device__ __forceinline__ int locate_window(const MixArgs& a, int next, Walk& wk, const int* tot) {
+  while (wk.tj < a.ntypes - 1 && next >= wk.base + tot[wk.tj]) {
+    wk.base += tot[wk.tj];
+    wk.tj += 1;
+    wk.hint = -1;
+  }
+  if (wk.hint < 0) return 0;
+  return a.rowoff[(size_t)wk.tj * (a.N + 1) + min(wk.hint + (int)(threadIdx.x & 31), a.N)];
+}
+
+// Warp 0 locates the tile starting at global row `cur` of chunk [c0, c1).  The window of 32
+// row offsets from the hint atom (`win`, from locate_window when `have_win`) finds the first
+// atom and, when it reaches far enough, the tile's atom offsets too; a binary search runs
 // only when a CTA enters a stream.
 __device__ void locate_tile(const MixArgs& a, int cur, int c0, int c1, Walk& wk, const int* tot, const int* tiend,
-                            TileInfo* ti_out, int* sRow) {
+                            TileInfo* ti_out, int* sRow, int win = 0, bool have_win = false) {
   const int lane = threadIdx.x & 31;
   while (wk.tj < a.ntypes - 1 && cur >= wk.base + tot[wk.tj]) {
     wk.base += tot[wk.tj];
     wk.tj += 1;
     wk.hint = -1;
+    have_win = false;
   }
   const int tj = wk.tj;
   const int* ro = a.rowoff + (size_t)tj * (a.N + 1);
   const int p = cur - wk.base;
   int a0 = -1;
-  if (wk.hint >= 0) {
-    const int v = ro[min(wk.hint + lane, a.N)];
+  const int hint = wk.hint;
+  int v = 0;
+  if (hint >= 0) {
+    v = have_win ? win : ro[min(hint + lane, a.N)];
     const unsigned m = __ballot_sync(0xffffffffu, v <= p);  // a prefix of the lanes (offsets ascend)
-    if (m != 0xffffffffu && m != 0u) a0 = wk.hint + __popc(m) - 1;
+    if (m != 0xffffffffu && m != 0u) a0 = hint + __popc(m) - 1;
   }
+  const bool in_win = a0 >= 0 && a0 - hint + kMaxAtoms <= 31;
   if (a0 < 0) {  // largest atom i with ro[i] <= p
     int lo = 0, hi = a.N - 1;
     while (lo < hi) {
@@ -121,7 +138,10 @@ __device__ void locate_tile(const MixArgs& a, int cur, int c0, int c1, Walk& wk,
   }
   int ti = 0;
   while (ti < a.ntypes - 1 && p >= tiend[tj * a.ntypes + ti]) ++ti;
-  const int rk = ro[min(a0 + (lane < kMaxAtoms + 1 ? lane : 0), a.N)];
+  // ro[min(a0 + k, N)] for k <= kMaxAtoms: lane a0 - hint + k of the window when it is there
+  const int k = lane < kMaxAtoms + 1 ? lane : 0;
+  const int vk = __shfl_sync(0xffffffffu, v, in_win ? a0 - hint + k : 0);
+  const int rk = in_win ? vk : ro[min(a0 + k, a.N)];
   if (lane <= kMaxAtoms) sRow[lane] = rk;
   const int r8 = __shfl_sync(0xffffffffu, rk, kMaxAtoms);
   int end = min(c1 - wk.base, tot[tj]);
@@ -140,9 +160,51 @@ __device__ void locate_tile(const MixArgs& a, int cur, int c0, int c1, Walk& wk,
   wk.hint = last;
 }
 
+// The layer biases enter the tensor-core products: the A operands carry ones in the two K
+// columns after the last unit, and the B blocks carry the bias split into a 16-bit head and
+// the 16-bit rounding of the remainder there, so z = h W + b_hi + b_lo is accumulated in FP32
+// with the bias exact to about 2^-22 relative.
+template <bool F16>
+__device__ __forceinline__ float split_hi(float b) {
+  if (F16) return __half2float(__float2half_rn(b));
+  return __bfloat162float(__float2bfloat16_rn(b));
+}
+
+// Element (k, n) of the layer-2 block: W2[k][n] (k < 25), the bias b2[n] at k = 25, 26.
+template <bool F16>
+__device__ __forceinline__ float w2_elem(const float* __restrict__ W, int k, int n) {
+  if (n >= kN2) return 0.f;
+  if (k < kN1) return W[kEW2 + k * kN2 + n];
+  if (k == kN1 || k == kN1 + 1) {
+    const float b = W[kEb2 + n], hi = split_hi<F16>(b);
+    return k == kN1 ? hi : b - hi;
+  }
+  return 0.f;
+}
+
+// Element (k, f) of the layer-3 block: W3[k][f] (k < 50), the bias b3[f] at k = 50, 51.
+template <bool F16>
+__device__ __forceinline__ float w3_elem(const float* __restrict__ W, int k, int f) {
+  if (f < 0 || f >= kN3) return 0.f;
+  if (k < kN2) return W[kEW3 + k * kN3 + f];
+  if (k == kN2 || k == kN2 + 1) {
+    const float b = W[kEb3 + f], hi = split_hi<F16>(b);
+    return k == kN2 ? hi : b - hi;
+  }
+  return 0.f;
+}
+
+// Layer-1 weights in FP32 for the CUDA cores (16-byte aligned slots for vector loads):
+// small[0..31] = W1 (25 used), small[32..63] = b1 (25 used).
+constexpr int kSmall = 64;
+__device__ __forceinline__ void load_small(const float* __restrict__ W, float* small) {
+  for (int q = threadIdx.x; q < kSmall; q += blockDim.x)
+    small[q] = (q & 31) < kN1 ? W[(q < 32 ? kEW1 : kEb1) + (q & 31)] : 0.f;
+}
+
 // Embedding weights of pair (ti, tj) into the MMA operand blocks and small fp32 arrays.
-//   B2: [64 x 64] rows n (layer-2 output), K = layer-1 unit (25 used) -> W2[k][n]
-//   B3: [112 x 64] rows a (layer-3 output), K = layer-2 unit (50 used) -> W3[m][a]
+//   B2: [64 x 64] rows n (layer-2 output), K = layer-1 unit (25 used, bias at 25/26) -> W2[k][n]
+//   B3: [112 x 64] rows a (layer-3 output), K = layer-2 unit (50 used, bias at 50/51) -> W3[m][a]
 template <bool F16>
 __device__ void load_fwd_weights(const float* __restrict__ W, unsigned char* sB2, unsigned char* sB3, float* small) {
   const int t = threadIdx.x;
@@ -152,9 +214,7 @@ __device__ void load_fwd_weights(const float* __restrict__ W, unsigned char* sB2
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       int k = k0 + 2 * h;
-      float x0 = (n < kN2 && k < kN1) ? W[kEW2 + k * kN2 + n] : 0.f;
-      float x1 = (n < kN2 && k + 1 < kN1) ? W[kEW2 + (k + 1) * kN2 + n] : 0.f;
-      p[h] = tc::pack2<F16>(x0, x1);
+      p[h] = tc::pack2<F16>(w2_elem<F16>(W, k, n), w2_elem<F16>(W, k + 1, n));
     }
     tc::st_chunk(sB2, n, k0, make_uint4(p[0], p[1], p[2], p[3]));
   }
@@ -164,26 +224,16 @@ __device__ void load_fwd_weights(const float* __restrict__ W, unsigned char* sB2
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       int k = k0 + 2 * h;
-      float x0 = (n < kN3 && k < kN2) ? W[kEW3 + k * kN3 + n] : 0.f;
-      float x1 = (n < kN3 && k + 1 < kN2) ? W[kEW3 + (k + 1) * kN3 + n] : 0.f;
-      p[h] = tc::pack2<F16>(x0, x1);
+      p[h] = tc::pack2<F16>(w3_elem<F16>(W, k, n), w3_elem<F16>(W, k + 1, n));
     }
     tc::st_chunk(sB3, n, k0, make_uint4(p[0], p[1], p[2], p[3]));
   }
-  // small: W1[25], b1[25], b2[50], b3[100]
-  for (int q = t; q < 200; q += kRows) {
-    float v;
-    if (q < 25) v = W[kEW1 + q];
-    else if (q < 50) v = W[kEb1 + q - 25];
-    else if (q < 100) v = W[kEb2 + q - 50];
-    else v = W[kEb3 + q - 100];
-    small[q] = v;
-  }
+  load_small(W, small);
 }
 
 // Per-row front end shared by forward and backward: environment row and layer 1.
 struct RowFront {
-  float d[3], R[4], r, sw, dsw;
+  float d[3], R[4], r, rinv, sw, dsw;
   int atom, la, j;
 };
 
@@ -206,39 +256,54 @@ __device__ __forceinline__ float4 row_load(const MixArgs& a, const TileInfo& ti,
   return a.nl_d[e];
 }
 
-__device__ __forceinline__ void row_compute(const MixArgs& a, const TileInfo& ti, float4 dv, RowFront& f) {
+// 1/r from one reciprocal square root (a few ulp; the row feeds 16-bit operands and FP32
+// sums), r = r^2 / r, and no divisions on the row's critical path.
+__device__ __forceinline__ void row_compute(const MixArgs& a, const TileInfo& ti, float4 dv, float winv,
+                                            RowFront& f) {
   f.d[0] = dv.x; f.d[1] = dv.y; f.d[2] = dv.z;
-  f.r = sqrtf(dv.x * dv.x + dv.y * dv.y + dv.z * dv.z);
-  switch_fn<float>(f.r, a.rs, a.rc, a.switch_kind, f.sw, f.dsw);
-  const float s = f.sw / f.r;
-  f.R[0] = s; f.R[1] = s * dv.x / f.r; f.R[2] = s * dv.y / f.r; f.R[3] = s * dv.z / f.r;
+  const float r2 = dv.x * dv.x + dv.y * dv.y + dv.z * dv.z;
+  f.rinv = rsqrtf(r2);
+  f.r = r2 * f.rinv;
+  switch_fn(f.r, a.rs, a.rc, winv, a.switch_kind, f.sw, f.dsw);
+  const float s = f.sw * f.rinv, sr = s * f.rinv;
+  f.R[0] = s; f.R[1] = sr * dv.x; f.R[2] = sr * dv.y; f.R[3] = sr * dv.z;
 #pragma unroll
   for (int c = 0; c < 4; ++c) f.R[c] = (f.R[c] - a.stat[ti.ti * 4 + c]) * a.stat[(a.ntypes + ti.ti) * 4 + c];
 }
 
 __device__ __forceinline__ void row_front(const MixArgs& a, const TileInfo& ti, const int* sRow, int t,
-                                          bool want_j, RowFront& f) {
-  row_compute(a, ti, row_load(a, ti, sRow, t, want_j, f), f);
+                                          bool want_j, float winv, RowFront& f) {
+  row_compute(a, ti, row_load(a, ti, sRow, t, want_j, f), winv, f);
 }
 
-// h1 = tanh(s_hat W1 + b1) and its 16-bit copy into the A block (K = 32 used).
+// h1 = tanh(s_hat W1 + b1) and its 16-bit copy into the A block (K = 32: 25 units, then the
+// two bias ones).
 template <bool F16>
 __device__ __forceinline__ void layer1(const float* small, float x, float* h1, unsigned char* sA, int t) {
 #pragma unroll
-  for (int k = 0; k < kN1; ++k) h1[k] = tc::tanh_fast(fmaf(x, small[k], small[25 + k]));
+  for (int k4 = 0; k4 < 7; ++k4) {
+    const float4 wv = reinterpret_cast<const float4*>(small)[k4];
+    const float4 bv = reinterpret_cast<const float4*>(small)[8 + k4];
+    const float w4[4] = {wv.x, wv.y, wv.z, wv.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (4 * k4 + u < kN1) h1[4 * k4 + u] = tc::tanh_fast(fmaf(x, w4[u], b4[u]));
+  }
 #pragma unroll
   for (int k0 = 0; k0 < 32; k0 += 8) {
     uint32_t p[4];
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       int k = k0 + 2 * h;
-      p[h] = tc::pack2<F16>(k < kN1 ? h1[k] : 0.f, k + 1 < kN1 ? h1[k + 1] : 0.f);
+      p[h] = tc::pack2<F16>(k < kN1 ? h1[k] : (k <= kN1 + 1 ? 1.f : 0.f),
+                            k + 1 < kN1 ? h1[k + 1] : (k + 1 <= kN1 + 1 ? 1.f : 0.f));
     }
     tc::st_chunk(sA, t, k0, make_uint4(p[0], p[1], p[2], p[3]));
   }
 }
 
-// Layer-2 epilogue: h2 = [h1, h1] + tanh(z2 + b2); 16-bit copy into the A block (K = 64, 50 used).
+// Layer-2 epilogue: h2 = [h1, h1] + tanh(z2) (z2 includes b2); 16-bit copy into the A block
+// (K = 64: 50 units, then the two bias ones).
 template <bool F16>
 __device__ __forceinline__ void layer2_epi(uint32_t tl, const float* small, const float* h1, float* h2,
                                            unsigned char* sA, int t) {
@@ -250,7 +315,7 @@ __device__ __forceinline__ void layer2_epi(uint32_t tl, const float* small, cons
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       const int m = 16 * c + u;
-      if (m < kN2) h2[m] = h1[m % kN1] + tc::tanh_fast(z[u] + small[50 + m]);
+      if (m < kN2) h2[m] = h1[m % kN1] + tc::tanh_fast(z[u]);
     }
   }
 #pragma unroll
@@ -259,7 +324,8 @@ __device__ __forceinline__ void layer2_epi(uint32_t tl, const float* small, cons
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       int m = k0 + 2 * h;
-      p[h] = tc::pack2<F16>(m < kN2 ? h2[m] : 0.f, m + 1 < kN2 ? h2[m + 1] : 0.f);
+      p[h] = tc::pack2<F16>(m < kN2 ? h2[m] : (m <= kN2 + 1 ? 1.f : 0.f),
+                            m + 1 < kN2 ? h2[m + 1] : (m + 1 <= kN2 + 1 ? 1.f : 0.f));
     }
     tc::st_chunk(sA, t, k0, make_uint4(p[0], p[1], p[2], p[3]));
   }
@@ -288,13 +354,14 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
   unsigned char* sRs = sm + 32768;                 // 8 KB: block-sparse R_hat^T [(atom, c)][row] fp16
   unsigned char* sB2 = sRs + 8192;                 // 8 KB
   unsigned char* sB3 = sB2 + 8192;                 // 14 KB
-  float* small = reinterpret_cast<float*>(sB3 + 14336);  // 200
-  int* sRow = reinterpret_cast<int*>(small + 200);       // kMaxAtoms + 1
+  float* small = reinterpret_cast<float*>(sB3 + 14336);  // kSmall
+  int* sRow = reinterpret_cast<int*>(small + kSmall);    // kMaxAtoms + 1
   __shared__ uint64_t bar;
   __shared__ uint32_t tslot;
   __shared__ TileInfo sti;
   __shared__ int s_tot[kMaxTypes], s_tiend[kMaxTypes * kMaxTypes];
   const int t = threadIdx.x, w = t >> 5;
+  const float winv = 1.f / (a.rc - a.rs);
 
   int total = 0;
   for (int tj = 0; tj < a.ntypes; ++tj) total += a.rowoff[(size_t)tj * (a.N + 1) + a.N];
@@ -334,6 +401,8 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     }
     __syncthreads();
     const TileInfo ti = sti;
+    int win = 0;
+    if (w == 0 && cur + ti.nrows < c1) win = locate_window(a, cur + ti.nrows, wk, s_tot);
     // the write-out's facts about this tile's atom slots (sRow is rewritten mid-tile)
     const int last_la = local_atom(sRow, ti.p + ti.nrows - 1);
     const bool last_done = (ti.p + ti.nrows == sRow[last_la + 1]);
@@ -358,7 +427,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     RowFront f;
     const bool valid = t < ti.nrows;
     if (valid) {
-      row_front(a, ti, sRow, t, false, f);
+      row_front(a, ti, sRow, t, false, winv, f);
     } else {
       f.R[0] = f.R[1] = f.R[2] = f.R[3] = 0.f;
       f.la = 0;
@@ -378,7 +447,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
       tc::mma_commit(&bar);
     }
     mma_sync_wait(&bar, phase, a.err, ok);
-    // layer-3 epilogue: G = [h2, h2] + tanh(z3 + b3); G^T and this row's R_hat column go to
+    // layer-3 epilogue: G = [h2, h2] + tanh(z3) (z3 includes b3); G^T and this row's R_hat column go to
     // the fp16 operands of the T product T_slot[c][a] = sum_rows R_hat[row][c] G[row][a]
     {
       // G^T is the A operand stored MN-major: row = tile row (K), 64 features per 128-byte
@@ -392,7 +461,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
           const int q = 16 * c + u;
-          g[u] = (q < kN3) ? h2[q % kN2] + tc::tanh_fast(z[u] + small[100 + q]) : 0.f;
+          g[u] = (q < kN3) ? h2[q % kN2] + tc::tanh_fast(z[u]) : 0.f;
         }
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
@@ -428,7 +497,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     __syncwarp();
     // while the T product runs: locate the next tile and prefetch its rows into L2
     if (cur + ti.nrows < c1) {
-      if (w == 0) locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow);
+      if (w == 0) locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow, win, true);
       __syncthreads();
       const TileInfo nx = sti;
       if (t < nx.nrows) {
@@ -506,7 +575,7 @@ __device__ __forceinline__ int bwd_q_of(int n) {
 // Backward operand blocks of pair (ti, tj): B2 as in the forward ([64 x 64], rows = layer-2
 // unit, K = layer-1 unit) and B3 with 128 rows in the column order above (K = layer-2
 // unit).  The transposed products dz3 W3^T and dz2 W2^T read the same two blocks as MN-major
-// operands.  small: W1, b1, b2, b3 (b3 by feature index).
+// operands (their bias rows land in result columns that are never read).  small: W1, b1.
 template <bool F16>
 __device__ void load_bwd_ops(const float* __restrict__ W, unsigned char* sB2, unsigned char* sB3, float* small) {
   const int t = threadIdx.x;
@@ -516,9 +585,7 @@ __device__ void load_bwd_ops(const float* __restrict__ W, unsigned char* sB2, un
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       const int k = k0 + 2 * h;
-      const float x0 = (n < kN2 && k < kN1) ? W[kEW2 + k * kN2 + n] : 0.f;
-      const float x1 = (n < kN2 && k + 1 < kN1) ? W[kEW2 + (k + 1) * kN2 + n] : 0.f;
-      p[h] = tc::pack2<F16>(x0, x1);
+      p[h] = tc::pack2<F16>(w2_elem<F16>(W, k, n), w2_elem<F16>(W, k + 1, n));
     }
     tc::st_chunk(sB2, n, k0, make_uint4(p[0], p[1], p[2], p[3]));
   }
@@ -529,20 +596,11 @@ __device__ void load_bwd_ops(const float* __restrict__ W, unsigned char* sB2, un
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       const int k = k0 + 2 * h;
-      const float x0 = (f >= 0 && k < kN2) ? W[kEW3 + k * kN3 + f] : 0.f;
-      const float x1 = (f >= 0 && k + 1 < kN2) ? W[kEW3 + (k + 1) * kN3 + f] : 0.f;
-      p[h] = tc::pack2<F16>(x0, x1);
+      p[h] = tc::pack2<F16>(w3_elem<F16>(W, k, f), w3_elem<F16>(W, k + 1, f));
     }
     tc::st_chunk(sB3, n, k0, make_uint4(p[0], p[1], p[2], p[3]));
   }
-  for (int q = t; q < 200; q += kRows) {
-    float v;
-    if (q < 25) v = W[kEW1 + q];
-    else if (q < 50) v = W[kEb1 + q - 25];
-    else if (q < 100) v = W[kEb2 + q - 50];
-    else v = W[kEb3 + q - 100];
-    small[q] = v;
-  }
+  load_small(W, small);
 }
 
 // Embedding backward with recompute, prod_force and per-atom virial.  One row per thread and
@@ -559,13 +617,14 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
   unsigned char* sB2 = sm + 32768;                 // 8 KB
   unsigned char* sB3 = sB2 + 8192;                 // 16 KB (128 rows, backward column order)
   float4* sdT = reinterpret_cast<float4*>(sB3 + 16384);              // [kMaxAtoms][100]
-  float* small = reinterpret_cast<float*>(sdT + kMaxAtoms * kN3);    // 200
-  int* sRow = reinterpret_cast<int*>(small + 200);
+  float* small = reinterpret_cast<float*>(sdT + kMaxAtoms * kN3);    // kSmall
+  int* sRow = reinterpret_cast<int*>(small + kSmall);
   __shared__ uint64_t bar;
   __shared__ uint32_t tslot;
   __shared__ TileInfo sti;
   __shared__ int s_tot[kMaxTypes], s_tiend[kMaxTypes * kMaxTypes];
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const float winv = 1.f / (a.rc - a.rs);
 
   int total = 0;
   for (int tj = 0; tj < a.ntypes; ++tj) total += a.rowoff[(size_t)tj * (a.N + 1) + a.N];
@@ -602,6 +661,8 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
   for (int cur = c0; cur < c1 && ok;) {
     __syncthreads();
     const TileInfo ti = sti;
+    int win = 0;
+    if (w == 0 && cur + ti.nrows < c1) win = locate_window(a, cur + ti.nrows, wk, s_tot);
     const int np = ti.ti * a.ntypes + ti.tj;
     if (np != pair) {
       load_bwd_ops<F16>(a.w + (size_t)np * kEmbParams, sB2, sB3, small);
@@ -618,7 +679,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
 
     float h1[kN1], h2[kN2];
     if (valid) {
-      row_compute(a, ti, dv, f);
+      row_compute(a, ti, dv, winv, f);
     } else {
       f.R[0] = f.R[1] = f.R[2] = f.R[3] = 0.f;
       f.la = 0; f.j = 0; f.atom = ti.a0;
@@ -658,8 +719,8 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
           const int m = 16 * c + 8 * hh + u;
           da[u] = db[u] = r[u] = 0.f;
           if (m < kN2) {
-            const float ta = tc::tanh_fast(za[8 * hh + u] + small[100 + m]);
-            const float tb = tc::tanh_fast(zb[8 * hh + u] + small[150 + m]);
+            const float ta = tc::tanh_fast(za[8 * hh + u]);
+            const float tb = tc::tanh_fast(zb[8 * hh + u]);
             const float Ga = h2[m] + ta, Gb = h2[m] + tb;
             const float4 pa = dTa[m], pb = dTa[m + kN2];
             dR[0] = fmaf(pa.x, Ga, fmaf(pb.x, Gb, dR[0]));
@@ -694,7 +755,8 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
     }
     __syncwarp();
     // while the MMA runs: locate the next tile and prefetch its rows and dE/dT into L2
-    if (w == 0 && cur + ti.nrows < c1) locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow);
+    if (w == 0 && cur + ti.nrows < c1)
+      locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow, win, true);
     mma_sync_wait(&bar, phase, a.err, ok);
     if (cur + ti.nrows < c1) {
       __syncthreads();  // the next tile's sti / sRow
@@ -757,11 +819,16 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
       tc::tmem_ld16(tl + 16 * c, z);
       tc::tmem_wait_ld();
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int k = 16 * c + u;
-        if (k < kN1) {
-          const float g1 = z[u] + dh1[k];
-          ds = fmaf(g1 * (1.f - h1[k] * h1[k]), small[k], ds);
+      for (int u4 = 0; u4 < 4; ++u4) {
+        const float4 wv = reinterpret_cast<const float4*>(small)[4 * c + u4];
+        const float w4[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = 16 * c + 4 * u4 + u;
+          if (k < kN1) {
+            const float g1 = z[4 * u4 + u] + dh1[k];
+            ds = fmaf(g1 * (1.f - h1[k] * h1[k]), w4[u], ds);
+          }
         }
       }
     }
@@ -774,7 +841,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
       dR[0] += ds;
 #pragma unroll
       for (int c = 0; c < 4; ++c) dR[c] *= a.stat[(a.ntypes + ti.ti) * 4 + c];
-      const float rinv = 1.f / f.r;
+      const float rinv = f.rinv;
       const float dsr = f.dsw * rinv - f.sw * rinv * rinv;
       const float qv = f.sw * rinv * rinv;
       const float dq = f.dsw * rinv * rinv - 2.f * f.sw * rinv * rinv * rinv;
@@ -1020,8 +1087,8 @@ MixArgs make_mix_args(Model* m, int N) {
   return a;
 }
 
-constexpr size_t kFwdSmem = 32768 + 8192 + 8192 + 14336 + 200 * 4 + 64 + 1024;
-constexpr size_t kBwdSmem = 32768 + 8192 + 16384 + kMaxAtoms * kN3 * 16 + 200 * 4 + 64 + 1024;
+constexpr size_t kFwdSmem = 32768 + 8192 + 8192 + 14336 + kSmall * 4 + 64 + 1024;
+constexpr size_t kBwdSmem = 32768 + 8192 + 16384 + kMaxAtoms * kN3 * 16 + kSmall * 4 + 64 + 1024;
 
 }  // namespace
 
