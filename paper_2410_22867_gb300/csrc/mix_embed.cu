@@ -106,9 +106,11 @@ __device__ __forceinline__ int locate_window(const MixArgs& a, int next, Walk& w
 // Warp 0 locates the tile starting at global row `cur` of chunk [c0, c1).  The window of 32
 // row offsets from the hint atom (`win`, from locate_window when `have_win`) finds the first
 // atom and, when it reaches far enough, the tile's atom offsets too; a binary search runs
-// only when a CTA enters a stream.
+// only when a CTA enters a stream.  With `sdT`, lane 0 then starts the bulk copy of dE/dT of
+// the tile's atoms into it, completing on `dbar`.
 __device__ void locate_tile(const MixArgs& a, int cur, int c0, int c1, Walk& wk, const int* tot, const int* tiend,
-                            TileInfo* ti_out, int* sRow, int win = 0, bool have_win = false) {
+                            TileInfo* ti_out, int* sRow, int win = 0, bool have_win = false,
+                            float4* sdT = nullptr, uint64_t* dbar = nullptr) {
   const int lane = threadIdx.x & 31;
   while (wk.tj < a.ntypes - 1 && cur >= wk.base + tot[wk.tj]) {
     wk.base += tot[wk.tj];
@@ -140,8 +142,8 @@ __device__ void locate_tile(const MixArgs& a, int cur, int c0, int c1, Walk& wk,
   while (ti < a.ntypes - 1 && p >= tiend[tj * a.ntypes + ti]) ++ti;
   // ro[min(a0 + k, N)] for k <= kMaxAtoms: lane a0 - hint + k of the window when it is there
   const int k = lane < kMaxAtoms + 1 ? lane : 0;
-  const int vk = __shfl_sync(0xffffffffu, v, in_win ? a0 - hint + k : 0);
-  const int rk = in_win ? vk : ro[min(a0 + k, a.N)];
+  int rk = __shfl_sync(0xffffffffu, v, in_win ? a0 - hint + k : 0);
+  if (!in_win) rk = tc::ld_global_once(ro + min(a0 + k, a.N));
   if (lane <= kMaxAtoms) sRow[lane] = rk;
   const int r8 = __shfl_sync(0xffffffffu, rk, kMaxAtoms);
   int end = min(c1 - wk.base, tot[tj]);
@@ -158,7 +160,13 @@ __device__ void locate_tile(const MixArgs& a, int cur, int c0, int c1, Walk& wk,
 #pragma unroll
   for (int k = 1; k < kMaxAtoms; ++k) last += (__shfl_sync(0xffffffffu, rk, k) <= end - 1) ? 1 : 0;
   wk.hint = last;
+  if (sdT != nullptr && lane == 0) {
+    const uint32_t bytes = (uint32_t)(last - a0 + 1) * kN3 * 16u;
+    tc::mbar_arrive_expect_tx(dbar, bytes);
+    tc::bulk_load(sdT, a.dT + (size_t)a0 * kN3, bytes, dbar);
+  }
 }
+
 
 // The layer biases enter the tensor-core products: the A operands carry ones in the two K
 // columns after the last unit, and the B blocks carry the bias split into a 16-bit head and
@@ -242,6 +250,18 @@ __device__ __forceinline__ int local_atom(const int* sRow, int row) {
 #pragma unroll
   for (int k = 1; k < kMaxAtoms; ++k) la += (sRow[k] <= row) ? 1 : 0;
   return la;
+}
+
+// Thread t's row of tile `ti` (pair vector, neighbour index, replica of the centre atom) copied
+// asynchronously into shared memory; waited for with cp_async_wait_all.
+__device__ __forceinline__ void stage_row(const MixArgs& a, const TileInfo& ti, const int* sRow, int t, float4* sNd,
+                                          int* sNj, int* sRep) {
+  const int row = ti.p + t;
+  const int la = local_atom(sRow, row);
+  const size_t e = (size_t)(ti.a0 + la) * a.S + a.sel_off[ti.tj] + (row - sRow[la]);
+  tc::cp_async16(sNd + t, a.nl_d + e);
+  tc::cp_async4(sNj + t, a.nl_j + e);
+  tc::cp_async4(sRep + t, a.irep + ti.a0 + la);
 }
 
 // Load half: the row's slot, atom, neighbour index and pair vector (issued early so the
@@ -617,9 +637,12 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
   unsigned char* sB2 = sm + 32768;                 // 8 KB
   unsigned char* sB3 = sB2 + 8192;                 // 16 KB (128 rows, backward column order)
   float4* sdT = reinterpret_cast<float4*>(sB3 + 16384);              // [kMaxAtoms][100]
-  float* small = reinterpret_cast<float*>(sdT + kMaxAtoms * kN3);    // kSmall
+  float4* sNd = sdT + kMaxAtoms * kN3;                               // [kRows] pair vectors
+  int* sNj = reinterpret_cast<int*>(sNd + kRows);                    // [kRows] neighbour index
+  int* sRep = sNj + kRows;                                           // [2][kRows] replica, by tile parity
+  float* small = reinterpret_cast<float*>(sRep + 2 * kRows);         // kSmall
   int* sRow = reinterpret_cast<int*>(small + kSmall);
-  __shared__ uint64_t bar;
+  __shared__ uint64_t bar, dbar;
   __shared__ uint32_t tslot;
   __shared__ TileInfo sti;
   __shared__ int s_tot[kMaxTypes], s_tiend[kMaxTypes * kMaxTypes];
@@ -631,14 +654,14 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
   const int per = (total + gridDim.x - 1) / gridDim.x;
   const int c0 = min(total, blockIdx.x * per), c1 = min(total, c0 + per);
 
-  if (t == 0) { tc::mbar_init(&bar, 1); tc::mbar_fence_init(); }
+  if (t == 0) { tc::mbar_init(&bar, 1); tc::mbar_init(&dbar, 1); tc::mbar_fence_init(); }
   if (w == 0) { tc::tmem_alloc(&tslot, kTmemCols); tc::tmem_relinquish(); }
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = tslot;
   const uint32_t tl = tmem + ((uint32_t)(32 * w) << 16);
-  uint32_t phase = 0;
+  uint32_t phase = 0, dphase = 0;
   bool ok = true;
   int pair = -1;
   walk_tables(a, s_tot, s_tiend);
@@ -656,9 +679,14 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
   const uint32_t idH1 = tc::idesc_mn(tc::idesc_f16(128, 32, F16), false, true);
 
   // the first tile is located here; each later one by warp 0 in the middle of the previous
-  // tile (after the last read of sti / sRow), with its data prefetched into L2
-  if (w == 0 && c0 < c1) locate_tile(a, c0, c0, c1, wk, s_tot, s_tiend, &sti, sRow);
-  for (int cur = c0; cur < c1 && ok;) {
+  // tile (after the last reads of sti, sRow and sdT), which also starts the copies of the
+  // tile's dE/dT (bulk, on dbar) and rows (per thread) into shared memory
+  if (w == 0 && c0 < c1) locate_tile(a, c0, c0, c1, wk, s_tot, s_tiend, &sti, sRow, 0, false, sdT, &dbar);
+  __syncthreads();
+  if (c0 < c1 && t < sti.nrows) stage_row(a, sti, sRow, t, sNd, sNj, sRep);
+  bool dT_pending = c0 < c1;
+  int it = 0;
+  for (int cur = c0; cur < c1 && ok; ++it) {
     __syncthreads();
     const TileInfo ti = sti;
     int win = 0;
@@ -667,15 +695,22 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
     if (np != pair) {
       load_bwd_ops<F16>(a.w + (size_t)np * kEmbParams, sB2, sB3, small);
       pair = np;
+      __syncthreads();
     }
-    // this row's neighbour data is requested before the dE/dT staging and its barrier
+    // this thread's row and the tile's dE/dT, copied during the previous tile
     RowFront f;
     const bool valid = t < ti.nrows;
+    tc::cp_async_wait_all();
+    ok = tc::mbar_wait(&dbar, dphase, a.err) && ok;
+    dphase ^= 1u;
+    dT_pending = false;
     float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (valid) dv = row_load(a, ti, sRow, t, true, f);
-    const int natoms_tile = local_atom(sRow, ti.p + ti.nrows - 1) + 1;
-    for (int q = t; q < natoms_tile * kN3; q += kRows) sdT[q] = a.dT[(size_t)ti.a0 * kN3 + q];
-    __syncthreads();
+    if (valid) {
+      f.la = local_atom(sRow, ti.p + t);
+      f.atom = ti.a0 + f.la;
+      f.j = sNj[t];
+      dv = sNd[t];
+    }
 
     float h1[kN1], h2[kN2];
     if (valid) {
@@ -754,22 +789,15 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
       tc::mma_commit(&bar);
     }
     __syncwarp();
-    // while the MMA runs: locate the next tile and prefetch its rows and dE/dT into L2
+    // while the MMA runs: locate the next tile and start the copies of its dE/dT and rows
     if (w == 0 && cur + ti.nrows < c1)
-      locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow, win, true);
+      locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow, win, true, sdT, &dbar);
     mma_sync_wait(&bar, phase, a.err, ok);
     if (cur + ti.nrows < c1) {
+      dT_pending = true;
       __syncthreads();  // the next tile's sti / sRow
       const TileInfo nx = sti;
-      if (t < nx.nrows) {
-        const int row = nx.p + t;
-        const int la = local_atom(sRow, row);
-        const size_t e = (size_t)(nx.a0 + la) * a.S + a.sel_off[nx.tj] + (row - sRow[la]);
-        tc::prefetch_l2(a.nl_d + e);
-        tc::prefetch_l2(a.nl_j + e);
-      }
-      const int nat = local_atom(sRow, nx.p + nx.nrows - 1) + 1;
-      if (t < nat * 13) tc::prefetch_l2(reinterpret_cast<const char*>(a.dT + (size_t)nx.a0 * kN3) + 128 * t);
+      if (t < nx.nrows) stage_row(a, nx, sRow, t, sNd, sNj, sRep + ((it + 1) & 1) * kRows);
     }
     // layer-2 backward: g2 = dh2' + residual, dz2 = g2 (1 - t2^2) -> sA; h2's residual into dh1
     float dh1[kN1];
@@ -851,7 +879,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
       for (int c = 0; c < 3; ++c) g3[c] = common * f.d[c] + qv * dR[1 + c];
 #pragma unroll
       for (int c = 0; c < 3; ++c) atomicAdd(&a.force32[3 * (size_t)f.j + c], -g3[c]);
-      const int rep = a.irep[f.atom];
+      const int rep = sRep[(it & 1) * kRows + t];
       if (rep != vrep) {
         if (vrep >= 0)
 #pragma unroll
@@ -888,6 +916,9 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
     __syncthreads();
     cur += ti.nrows;
   }
+  // copies still in flight after an early exit
+  tc::cp_async_wait_all();
+  if (dT_pending) tc::mbar_wait(&dbar, dphase, a.err);
   // flush the virial accumulators: one warp reduction when all lanes hold the same replica
   {
     const int r0 = __shfl_sync(0xffffffffu, vrep, 0);
@@ -1088,7 +1119,7 @@ MixArgs make_mix_args(Model* m, int N) {
 }
 
 constexpr size_t kFwdSmem = 32768 + 8192 + 8192 + 14336 + kSmall * 4 + 64 + 1024;
-constexpr size_t kBwdSmem = 32768 + 8192 + 16384 + kMaxAtoms * kN3 * 16 + kSmall * 4 + 64 + 1024;
+constexpr size_t kBwdSmem = 32768 + 8192 + 16384 + kMaxAtoms * kN3 * 16 + kRows * (16 + 4 + 8) + kSmall * 4 + 64 + 1024;
 
 }  // namespace
 
