@@ -565,7 +565,7 @@ dp_status dp_create(dp_model** out, int ntypes, const char* const* type_map, dou
     A_(scan_blk, 4 * (size_t)nt * (N / 1024 + 2));
     A_(Tseg, 4 * (size_t)nt * N * 400);
     A_(dTm, 16 * N * kN3);
-    A_(force32, 12 * N);
+    A_(force32, 16 * N);
     A_(vir_rep, 72 * R + 64);
     A_(tc_weights, mix_fit_weight_bytes(nt));
   }

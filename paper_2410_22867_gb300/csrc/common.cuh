@@ -151,7 +151,7 @@ struct Model {
   int* scan_blk = nullptr;    // [nt][N / 1024 + 1]
   float* Tseg = nullptr;      // [nt][N][400] partial T per neighbour type
   void* dTm = nullptr;        // [N][100] float4
-  float* force32 = nullptr;   // [N*3] FP32 force accumulator of the mixed-precision backward
+  float* force32 = nullptr;   // [N*4] FP32 force accumulator of the mixed-precision backward (x y z pad)
   double* vir_rep = nullptr;  // [max_reps][9] per-replica virial accumulated by the mixed backward
   // parameter gradient
   void* pg_ws = nullptr;      // per-chunk activations and adjoints (FP64 or FP32)

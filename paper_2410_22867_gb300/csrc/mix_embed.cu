@@ -41,7 +41,7 @@ struct MixArgs {
   float* Tseg;           // [nt][N][400] partial T per neighbour type
   const float4* dT;      // [N][100]: dE/dT[c][a] * (1/S), c in x..w
   double* force;         // [N][3]
-  float* force32;        // [N][3] FP32 accumulator (folded into force after the backward)
+  float* force32;        // [N][4] FP32 accumulator, x y z and a pad (folded into force after the backward)
   double* vir_atom;      // [N][9] (unused by the mixed backward)
   double* vir_rep;       // [nrep][9] per-replica virial
   const int* irep;       // [N] replica of each internal atom
@@ -264,16 +264,11 @@ __device__ __forceinline__ void stage_row(const MixArgs& a, const TileInfo& ti, 
   tc::cp_async4(sRep + t, a.irep + ti.a0 + la);
 }
 
-// Load half: the row's slot, atom, neighbour index and pair vector (issued early so the
-// global loads overlap other work); row_compute forms the environment row from them.
-__device__ __forceinline__ float4 row_load(const MixArgs& a, const TileInfo& ti, const int* sRow, int t,
-                                          bool want_j, RowFront& f) {
+// Thread t's pair vector of tile `ti` copied asynchronously into shared memory.
+__device__ __forceinline__ void stage_pair(const MixArgs& a, const TileInfo& ti, const int* sRow, int t, float4* sNd) {
   const int row = ti.p + t;
-  f.la = local_atom(sRow, row);
-  f.atom = ti.a0 + f.la;
-  const size_t e = (size_t)f.atom * a.S + a.sel_off[ti.tj] + (row - sRow[f.la]);
-  f.j = want_j ? a.nl_j[e] : 0;
-  return a.nl_d[e];
+  const int la = local_atom(sRow, row);
+  tc::cp_async16(sNd + t, a.nl_d + (size_t)(ti.a0 + la) * a.S + a.sel_off[ti.tj] + (row - sRow[la]));
 }
 
 // 1/r from one reciprocal square root (a few ulp; the row feeds 16-bit operands and FP32
@@ -289,11 +284,6 @@ __device__ __forceinline__ void row_compute(const MixArgs& a, const TileInfo& ti
   f.R[0] = s; f.R[1] = sr * dv.x; f.R[2] = sr * dv.y; f.R[3] = sr * dv.z;
 #pragma unroll
   for (int c = 0; c < 4; ++c) f.R[c] = (f.R[c] - a.stat[ti.ti * 4 + c]) * a.stat[(a.ntypes + ti.ti) * 4 + c];
-}
-
-__device__ __forceinline__ void row_front(const MixArgs& a, const TileInfo& ti, const int* sRow, int t,
-                                          bool want_j, float winv, RowFront& f) {
-  row_compute(a, ti, row_load(a, ti, sRow, t, want_j, f), winv, f);
 }
 
 // h1 = tanh(s_hat W1 + b1) and its 16-bit copy into the A block (K = 32: 25 units, then the
@@ -374,7 +364,8 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
   unsigned char* sRs = sm + 32768;                 // 8 KB: block-sparse R_hat^T [(atom, c)][row] fp16
   unsigned char* sB2 = sRs + 8192;                 // 8 KB
   unsigned char* sB3 = sB2 + 8192;                 // 14 KB
-  float* small = reinterpret_cast<float*>(sB3 + 14336);  // kSmall
+  float4* sNd = reinterpret_cast<float4*>(sB3 + 14336);  // [kRows] pair vectors of the tile
+  float* small = reinterpret_cast<float*>(sNd + kRows);  // kSmall
   int* sRow = reinterpret_cast<int*>(small + kSmall);    // kMaxAtoms + 1
   __shared__ uint64_t bar;
   __shared__ uint32_t tslot;
@@ -411,8 +402,11 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
   long long carry = -1;  // (tj, atom) whose partial T sits in slot 0
 
   // the first tile is located here; each later one by warp 0 during the previous tile's T
-  // product (the tile's own sRow facts are kept in registers by then)
+  // product (the tile's own sRow facts are kept in registers by then), after which every
+  // thread starts the copy of its row's pair vector into shared memory
   if (w == 0 && c0 < c1) locate_tile(a, c0, c0, c1, wk, s_tot, s_tiend, &sti, sRow);
+  __syncthreads();
+  if (c0 < c1 && t < sti.nrows) stage_pair(a, sti, sRow, t, sNd);
   for (int cur = c0; cur < c1 && ok;) {
     // the R_hat^T operand starts from zero (rows of other atoms stay zero)
     {
@@ -446,8 +440,11 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     float h1[kN1], h2[kN2];
     RowFront f;
     const bool valid = t < ti.nrows;
+    tc::cp_async_wait_all();
     if (valid) {
-      row_front(a, ti, sRow, t, false, winv, f);
+      f.la = local_atom(sRow, ti.p + t);
+      f.atom = ti.a0 + f.la;
+      row_compute(a, ti, sNd[t], winv, f);
     } else {
       f.R[0] = f.R[1] = f.R[2] = f.R[3] = 0.f;
       f.la = 0;
@@ -515,16 +512,12 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
       tc::mma_commit(&bar);
     }
     __syncwarp();
-    // while the T product runs: locate the next tile and prefetch its rows into L2
+    // while the T product runs: locate the next tile and start the copies of its rows
     if (cur + ti.nrows < c1) {
       if (w == 0) locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow, win, true);
       __syncthreads();
       const TileInfo nx = sti;
-      if (t < nx.nrows) {
-        const int row = nx.p + t;
-        const int la = local_atom(sRow, row);
-        tc::prefetch_l2(a.nl_d + (size_t)(nx.a0 + la) * a.S + a.sel_off[nx.tj] + (row - sRow[la]));
-      }
+      if (t < nx.nrows) stage_pair(a, nx, sRow, t, sNd);
     }
     mma_sync_wait(&bar, phase, a.err, ok);
     {
@@ -573,6 +566,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     tc::tc_fence_after();
     cur += ti.nrows;
   }
+  tc::cp_async_wait_all();  // copies in flight after an early exit
   // an atom left open at the chunk end continues in the next CTA
   if (carry >= 0 && t < kN3) {
     float* dst = a.Tseg + (size_t)carry * 400 + t;
@@ -878,7 +872,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) g3[c] = common * f.d[c] + qv * dR[1 + c];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) atomicAdd(&a.force32[3 * (size_t)f.j + c], -g3[c]);
+      tc::red_add_v4(a.force32 + 4 * (size_t)f.j, -g3[0], -g3[1], -g3[2], 0.f);
       const int rep = sRep[(it & 1) * kRows + t];
       if (rep != vrep) {
         if (vrep >= 0)
@@ -893,10 +887,8 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) vacc[3 * p + q] = fmaf(-g3[p], f.d[q], vacc[3 * p + q]);
     }
-    // centre force: warp-segmented sums over rows of the same atom
-    float vals[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) vals[c] = g3[c];
+    // centre force: warp-segmented sums over rows of the same atom (the three components
+    // reduced together, one vector atomic per segment)
     const int my = valid ? f.la : -1;
     unsigned todo = __ballot_sync(0xffffffffu, valid);
     while (todo) {
@@ -904,13 +896,14 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
       const int seg = __shfl_sync(0xffffffffu, my, leader);
       const bool in = (my == seg);
       const unsigned mask = __ballot_sync(0xffffffffu, in);
+      float v0 = in ? g3[0] : 0.f, v1 = in ? g3[1] : 0.f, v2 = in ? g3[2] : 0.f;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        float v = in ? vals[q] : 0.f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == leader) atomicAdd(&a.force32[3 * ((size_t)ti.a0 + seg) + q], v);
+      for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
       }
+      if (lane == leader) tc::red_add_v4(a.force32 + 4 * ((size_t)ti.a0 + seg), v0, v1, v2, 0.f);
       todo &= ~mask;
     }
     __syncthreads();
@@ -1099,10 +1092,10 @@ __global__ void __launch_bounds__(32 * kDtWarps) k_mix_dT(int N, float invS, con
   }
 }
 
-// force (FP64) += force32 (the mixed backward's FP32 accumulation).
+// force (FP64, [N][3]) += force32 (the mixed backward's FP32 accumulation, [N][4]).
 __global__ void k_fold_force32(int n3, const float* __restrict__ f32, double* __restrict__ force) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n3) force[k] += (double)f32[k];
+  if (k < n3) force[k] += (double)f32[4 * (k / 3) + k % 3];
 }
 
 MixArgs make_mix_args(Model* m, int N) {
@@ -1118,7 +1111,7 @@ MixArgs make_mix_args(Model* m, int N) {
   return a;
 }
 
-constexpr size_t kFwdSmem = 32768 + 8192 + 8192 + 14336 + kSmall * 4 + 64 + 1024;
+constexpr size_t kFwdSmem = 32768 + 8192 + 8192 + 14336 + kRows * 16 + kSmall * 4 + 64 + 1024;
 constexpr size_t kBwdSmem = 32768 + 8192 + 16384 + kMaxAtoms * kN3 * 16 + kRows * (16 + 4 + 8) + kSmall * 4 + 64 + 1024;
 
 }  // namespace
@@ -1155,7 +1148,7 @@ dp_status launch_mix_embed_backward(Model* m, int N) {
                                                               static_cast<const unsigned short*>(m->dD),
                                                               static_cast<float4*>(m->dTm));
   DP_CUDA_TRY(m, cudaMemsetAsync(m->vir_rep, 0, sizeof(double) * 9 * (size_t)m->nrep, m->stream));
-  DP_CUDA_TRY(m, cudaMemsetAsync(m->force32, 0, sizeof(float) * 3 * (size_t)N, m->stream));
+  DP_CUDA_TRY(m, cudaMemsetAsync(m->force32, 0, sizeof(float) * 4 * (size_t)N, m->stream));
   if (m->sub_ev[1]) DP_CUDA_TRY(m, cudaEventRecord(m->sub_ev[1], m->stream));
   MixArgs a = make_mix_args(m, N);
   const bool f16 = m->prec == DP_MIX_FP16;
