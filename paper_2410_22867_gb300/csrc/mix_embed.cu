@@ -25,6 +25,7 @@ namespace {
 constexpr int kRows = 128;     // rows per tile = threads per CTA = TMEM lanes
 constexpr int kMaxAtoms = 6;   // atom segments per tile
 constexpr uint32_t kTmemCols = 128;  // per CTA: D2/D3 share columns 0..111
+constexpr int kLocWarp = 1;    // the warp that locates tiles (thread 0 issues the MMAs)
 
 struct MixArgs {
   int N, ntypes, S;
@@ -74,7 +75,7 @@ struct TileInfo {
   int tj, ti, p, nrows, a0, cs, ce;  // stream, centre type, first row (stream coords), rows, first atom, chunk
 };
 
-// Walk state of one CTA over the concatenated streams (held uniformly by warp 0).
+// Walk state of one CTA over the concatenated streams (held uniformly by the locating warp).
 struct Walk {
   int tj, base, hint;  // current stream, its first row in concatenated coordinates, atom at or before the tile
 };
@@ -90,9 +91,9 @@ __device__ void walk_tables(const MixArgs& a, int* tot, int* tiend) {
   }
 }
 
-// Warp 0, at the start of a tile: enters the stream of the next tile (starting at global row
-// `next`) and issues the load of the 32 row offsets from the hint atom.  The value is consumed
-// by locate_tile much later in the tile, so the load's latency is hidden.
+// The locating warp, at the start of a tile: enters the stream of the next tile (starting at
+// global row `next`) and issues the load of the 32 row offsets from the hint atom.  The value
+// is consumed by locate_tile much later in the tile, so the load's latency is hidden.
 __device__ __forceinline__ int locate_window(const MixArgs& a, int next, Walk& wk, const int* tot) {
   while (wk.tj < a.ntypes - 1 && next >= wk.base + tot[wk.tj]) {
     wk.base += tot[wk.tj];
@@ -103,14 +104,14 @@ __device__ __forceinline__ int locate_window(const MixArgs& a, int next, Walk& w
   return a.rowoff[(size_t)wk.tj * (a.N + 1) + min(wk.hint + (int)(threadIdx.x & 31), a.N)];
 }
 
-// Warp 0 locates the tile starting at global row `cur` of chunk [c0, c1).  The window of 32
-// row offsets from the hint atom (`win`, from locate_window when `have_win`) finds the first
+// The locating warp finds the tile starting at global row `cur` of chunk [c0, c1).  The window
+// of 32 row offsets from the hint atom (`win`, from locate_window when `have_win`) finds the first
 // atom and, when it reaches far enough, the tile's atom offsets too; a binary search runs
 // only when a CTA enters a stream.  With `sdT`, lane 0 then starts the bulk copy of dE/dT of
 // the tile's atoms into it, completing on `dbar`.
-__device__ void locate_tile(const MixArgs& a, int cur, int c0, int c1, Walk& wk, const int* tot, const int* tiend,
-                            TileInfo* ti_out, int* sRow, int win = 0, bool have_win = false,
-                            float4* sdT = nullptr, uint64_t* dbar = nullptr) {
+__device__ __forceinline__ void locate_tile(const MixArgs& a, int cur, int c0, int c1, Walk& wk, const int* tot,
+                                            const int* tiend, TileInfo* ti_out, int* sRow, int win = 0,
+                                            bool have_win = false, float4* sdT = nullptr, uint64_t* dbar = nullptr) {
   const int lane = threadIdx.x & 31;
   while (wk.tj < a.ntypes - 1 && cur >= wk.base + tot[wk.tj]) {
     wk.base += tot[wk.tj];
@@ -401,10 +402,10 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     for (int c = 0; c < 4; ++c) tacc[s][c] = 0.f;
   long long carry = -1;  // (tj, atom) whose partial T sits in slot 0
 
-  // the first tile is located here; each later one by warp 0 during the previous tile's T
-  // product (the tile's own sRow facts are kept in registers by then), after which every
+  // the first tile is located here; each later one by the locating warp during the previous
+  // tile's T product (the tile's own sRow facts are kept in registers by then), after which every
   // thread starts the copy of its row's pair vector into shared memory
-  if (w == 0 && c0 < c1) locate_tile(a, c0, c0, c1, wk, s_tot, s_tiend, &sti, sRow);
+  if (w == kLocWarp && c0 < c1) locate_tile(a, c0, c0, c1, wk, s_tot, s_tiend, &sti, sRow);
   __syncthreads();
   if (c0 < c1 && t < sti.nrows) stage_pair(a, sti, sRow, t, sNd);
   for (int cur = c0; cur < c1 && ok;) {
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     __syncthreads();
     const TileInfo ti = sti;
     int win = 0;
-    if (w == 0 && cur + ti.nrows < c1) win = locate_window(a, cur + ti.nrows, wk, s_tot);
+    if (w == kLocWarp && cur + ti.nrows < c1) win = locate_window(a, cur + ti.nrows, wk, s_tot);
     // the write-out's facts about this tile's atom slots (sRow is rewritten mid-tile)
     const int last_la = local_atom(sRow, ti.p + ti.nrows - 1);
     const bool last_done = (ti.p + ti.nrows == sRow[last_la + 1]);
@@ -514,7 +515,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     __syncwarp();
     // while the T product runs: locate the next tile and start the copies of its rows
     if (cur + ti.nrows < c1) {
-      if (w == 0) locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow, win, true);
+      if (w == kLocWarp) locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow, win, true);
       __syncthreads();
       const TileInfo nx = sti;
       if (t < nx.nrows) stage_pair(a, nx, sRow, t, sNd);
@@ -672,10 +673,10 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
   const uint32_t idH2 = tc::idesc_mn(tc::idesc_f16(128, 64, F16), false, true);
   const uint32_t idH1 = tc::idesc_mn(tc::idesc_f16(128, 32, F16), false, true);
 
-  // the first tile is located here; each later one by warp 0 in the middle of the previous
-  // tile (after the last reads of sti, sRow and sdT), which also starts the copies of the
+  // the first tile is located here; each later one by the locating warp in the middle of the
+  // previous tile (after the last reads of sti, sRow and sdT), which also starts the copies of the
   // tile's dE/dT (bulk, on dbar) and rows (per thread) into shared memory
-  if (w == 0 && c0 < c1) locate_tile(a, c0, c0, c1, wk, s_tot, s_tiend, &sti, sRow, 0, false, sdT, &dbar);
+  if (w == kLocWarp && c0 < c1) locate_tile(a, c0, c0, c1, wk, s_tot, s_tiend, &sti, sRow, 0, false, sdT, &dbar);
   __syncthreads();
   if (c0 < c1 && t < sti.nrows) stage_row(a, sti, sRow, t, sNd, sNj, sRep);
   bool dT_pending = c0 < c1;
@@ -684,7 +685,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
     __syncthreads();
     const TileInfo ti = sti;
     int win = 0;
-    if (w == 0 && cur + ti.nrows < c1) win = locate_window(a, cur + ti.nrows, wk, s_tot);
+    if (w == kLocWarp && cur + ti.nrows < c1) win = locate_window(a, cur + ti.nrows, wk, s_tot);
     const int np = ti.ti * a.ntypes + ti.tj;
     if (np != pair) {
       load_bwd_ops<F16>(a.w + (size_t)np * kEmbParams, sB2, sB3, small);
@@ -784,7 +785,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
     }
     __syncwarp();
     // while the MMA runs: locate the next tile and start the copies of its dE/dT and rows
-    if (w == 0 && cur + ti.nrows < c1)
+    if (w == kLocWarp && cur + ti.nrows < c1)
       locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow, win, true, sdT, &dbar);
     mma_sync_wait(&bar, phase, a.err, ok);
     if (cur + ti.nrows < c1) {
