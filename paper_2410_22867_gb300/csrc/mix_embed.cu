@@ -92,26 +92,29 @@ __device__ void walk_tables(const MixArgs& a, int* tot, int* tiend) {
 }
 
 // The locating warp, at the start of a tile: enters the stream of the next tile (starting at
-// global row `next`) and issues the load of the 32 row offsets from the hint atom.  The value
-// is consumed by locate_tile much later in the tile, so the load's latency is hidden.
-__device__ __forceinline__ int locate_window(const MixArgs& a, int next, Walk& wk, const int* tot) {
+// global row `next`) and starts the copy of the 32 row offsets from the hint atom into sWin
+// (lane l copies entry l).  locate_tile reads them much later in the tile, so the copy's
+// latency is hidden and no register waits for it.
+__device__ __forceinline__ void locate_window(const MixArgs& a, int next, Walk& wk, const int* tot, int* sWin) {
   while (wk.tj < a.ntypes - 1 && next >= wk.base + tot[wk.tj]) {
     wk.base += tot[wk.tj];
     wk.tj += 1;
     wk.hint = -1;
   }
-  if (wk.hint < 0) return 0;
-  return a.rowoff[(size_t)wk.tj * (a.N + 1) + min(wk.hint + (int)(threadIdx.x & 31), a.N)];
+  if (wk.hint < 0) return;
+  const int lane = threadIdx.x & 31;
+  tc::cp_async4(sWin + lane, a.rowoff + (size_t)wk.tj * (a.N + 1) + min(wk.hint + lane, a.N));
 }
 
 // The locating warp finds the tile starting at global row `cur` of chunk [c0, c1).  The window
-// of 32 row offsets from the hint atom (`win`, from locate_window when `have_win`) finds the first
-// atom and, when it reaches far enough, the tile's atom offsets too; a binary search runs
+// of 32 row offsets from the hint atom (in sWin from locate_window when `have_win`) finds the
+// first atom and, when it reaches far enough, the tile's atom offsets too; a binary search runs
 // only when a CTA enters a stream.  With `sdT`, lane 0 then starts the bulk copy of dE/dT of
 // the tile's atoms into it, completing on `dbar`.
 __device__ __forceinline__ void locate_tile(const MixArgs& a, int cur, int c0, int c1, Walk& wk, const int* tot,
-                                            const int* tiend, TileInfo* ti_out, int* sRow, int win = 0,
-                                            bool have_win = false, float4* sdT = nullptr, uint64_t* dbar = nullptr) {
+                                            const int* tiend, TileInfo* ti_out, int* sRow,
+                                            const int* sWin = nullptr, bool have_win = false,
+                                            float4* sdT = nullptr, uint64_t* dbar = nullptr) {
   const int lane = threadIdx.x & 31;
   while (wk.tj < a.ntypes - 1 && cur >= wk.base + tot[wk.tj]) {
     wk.base += tot[wk.tj];
@@ -126,7 +129,12 @@ __device__ __forceinline__ void locate_tile(const MixArgs& a, int cur, int c0, i
   const int hint = wk.hint;
   int v = 0;
   if (hint >= 0) {
-    v = have_win ? win : ro[min(hint + lane, a.N)];
+    if (have_win) {
+      tc::cp_async_wait_all();  // this lane's window entry (its only copy in flight)
+      v = sWin[lane];
+    } else {
+      v = ro[min(hint + lane, a.N)];
+    }
     const unsigned m = __ballot_sync(0xffffffffu, v <= p);  // a prefix of the lanes (offsets ascend)
     if (m != 0xffffffffu && m != 0u) a0 = hint + __popc(m) - 1;
   }
@@ -368,6 +376,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
   float4* sNd = reinterpret_cast<float4*>(sB3 + 14336);  // [kRows] pair vectors of the tile
   float* small = reinterpret_cast<float*>(sNd + kRows);  // kSmall
   int* sRow = reinterpret_cast<int*>(small + kSmall);    // kMaxAtoms + 1
+  int* sWin = sRow + 8;                                  // 32 row offsets (next tile's window)
   __shared__ uint64_t bar;
   __shared__ uint32_t tslot;
   __shared__ TileInfo sti;
@@ -416,8 +425,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     }
     __syncthreads();
     const TileInfo ti = sti;
-    int win = 0;
-    if (w == kLocWarp && cur + ti.nrows < c1) win = locate_window(a, cur + ti.nrows, wk, s_tot);
+    if (w == kLocWarp && cur + ti.nrows < c1) locate_window(a, cur + ti.nrows, wk, s_tot, sWin);
     // the write-out's facts about this tile's atom slots (sRow is rewritten mid-tile)
     const int last_la = local_atom(sRow, ti.p + ti.nrows - 1);
     const bool last_done = (ti.p + ti.nrows == sRow[last_la + 1]);
@@ -515,7 +523,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     __syncwarp();
     // while the T product runs: locate the next tile and start the copies of its rows
     if (cur + ti.nrows < c1) {
-      if (w == kLocWarp) locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow, win, true);
+      if (w == kLocWarp) locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow, sWin, true);
       __syncthreads();
       const TileInfo nx = sti;
       if (t < nx.nrows) stage_pair(a, nx, sRow, t, sNd);
@@ -636,7 +644,8 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
   int* sNj = reinterpret_cast<int*>(sNd + kRows);                    // [kRows] neighbour index
   int* sRep = sNj + kRows;                                           // [2][kRows] replica, by tile parity
   float* small = reinterpret_cast<float*>(sRep + 2 * kRows);         // kSmall
-  int* sRow = reinterpret_cast<int*>(small + kSmall);
+  int* sRow = reinterpret_cast<int*>(small + kSmall);                // kMaxAtoms + 1
+  int* sWin = sRow + 8;                                              // 32 row offsets
   __shared__ uint64_t bar, dbar;
   __shared__ uint32_t tslot;
   __shared__ TileInfo sti;
@@ -676,7 +685,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
   // the first tile is located here; each later one by the locating warp in the middle of the
   // previous tile (after the last reads of sti, sRow and sdT), which also starts the copies of the
   // tile's dE/dT (bulk, on dbar) and rows (per thread) into shared memory
-  if (w == kLocWarp && c0 < c1) locate_tile(a, c0, c0, c1, wk, s_tot, s_tiend, &sti, sRow, 0, false, sdT, &dbar);
+  if (w == kLocWarp && c0 < c1) locate_tile(a, c0, c0, c1, wk, s_tot, s_tiend, &sti, sRow, nullptr, false, sdT, &dbar);
   __syncthreads();
   if (c0 < c1 && t < sti.nrows) stage_row(a, sti, sRow, t, sNd, sNj, sRep);
   bool dT_pending = c0 < c1;
@@ -684,8 +693,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
   for (int cur = c0; cur < c1 && ok; ++it) {
     __syncthreads();
     const TileInfo ti = sti;
-    int win = 0;
-    if (w == kLocWarp && cur + ti.nrows < c1) win = locate_window(a, cur + ti.nrows, wk, s_tot);
+    if (w == kLocWarp && cur + ti.nrows < c1) locate_window(a, cur + ti.nrows, wk, s_tot, sWin);
     const int np = ti.ti * a.ntypes + ti.tj;
     if (np != pair) {
       load_bwd_ops<F16>(a.w + (size_t)np * kEmbParams, sB2, sB3, small);
@@ -786,7 +794,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
     __syncwarp();
     // while the MMA runs: locate the next tile and start the copies of its dE/dT and rows
     if (w == kLocWarp && cur + ti.nrows < c1)
-      locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow, win, true, sdT, &dbar);
+      locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow, sWin, true, sdT, &dbar);
     mma_sync_wait(&bar, phase, a.err, ok);
     if (cur + ti.nrows < c1) {
       dT_pending = true;
@@ -1112,8 +1120,10 @@ MixArgs make_mix_args(Model* m, int N) {
   return a;
 }
 
-constexpr size_t kFwdSmem = 32768 + 8192 + 8192 + 14336 + kRows * 16 + kSmall * 4 + 64 + 1024;
-constexpr size_t kBwdSmem = 32768 + 8192 + 16384 + kMaxAtoms * kN3 * 16 + kRows * (16 + 4 + 8) + kSmall * 4 + 64 + 1024;
+// (+ 160: sRow (8 ints) and sWin (32 ints); + 1024: alignment of the operand blocks)
+constexpr size_t kFwdSmem = 32768 + 8192 + 8192 + 14336 + kRows * 16 + kSmall * 4 + 160 + 1024;
+constexpr size_t kBwdSmem =
+    32768 + 8192 + 16384 + kMaxAtoms * kN3 * 16 + kRows * (16 + 4 + 8) + kSmall * 4 + 160 + 1024;
 
 }  // namespace
 
