@@ -109,12 +109,10 @@ __device__ __forceinline__ void locate_window(const MixArgs& a, int next, Walk& 
 // The locating warp finds the tile starting at global row `cur` of chunk [c0, c1).  The window
 // of 32 row offsets from the hint atom (in sWin from locate_window when `have_win`) finds the
 // first atom and, when it reaches far enough, the tile's atom offsets too; a binary search runs
-// only when a CTA enters a stream.  With `sdT`, lane 0 then starts the bulk copy of dE/dT of
-// the tile's atoms into it, completing on `dbar`.
+// only when a CTA enters a stream.  With `sNat`, lane 0 also stores the tile's atom count.
 __device__ __forceinline__ void locate_tile(const MixArgs& a, int cur, int c0, int c1, Walk& wk, const int* tot,
                                             const int* tiend, TileInfo* ti_out, int* sRow,
-                                            const int* sWin = nullptr, bool have_win = false,
-                                            float4* sdT = nullptr, uint64_t* dbar = nullptr) {
+                                            const int* sWin = nullptr, bool have_win = false, int* sNat = nullptr) {
   const int lane = threadIdx.x & 31;
   while (wk.tj < a.ntypes - 1 && cur >= wk.base + tot[wk.tj]) {
     wk.base += tot[wk.tj];
@@ -169,13 +167,15 @@ __device__ __forceinline__ void locate_tile(const MixArgs& a, int cur, int c0, i
 #pragma unroll
   for (int k = 1; k < kMaxAtoms; ++k) last += (__shfl_sync(0xffffffffu, rk, k) <= end - 1) ? 1 : 0;
   wk.hint = last;
-  if (sdT != nullptr && lane == 0) {
-    const uint32_t bytes = (uint32_t)(last - a0 + 1) * kN3 * 16u;
-    tc::mbar_arrive_expect_tx(dbar, bytes);
-    tc::bulk_load(sdT, a.dT + (size_t)a0 * kN3, bytes, dbar);
-  }
+  if (sNat != nullptr && lane == 0) *sNat = last - a0 + 1;
 }
 
+// dE/dT of `nat` atoms from atom a0 into sdT by one bulk copy, completing on dbar.
+__device__ __forceinline__ void fetch_dT(const MixArgs& a, int a0, int nat, float4* sdT, uint64_t* dbar) {
+  const uint32_t bytes = (uint32_t)nat * kN3 * 16u;
+  tc::mbar_arrive_expect_tx(dbar, bytes);
+  tc::bulk_load(sdT, a.dT + (size_t)a0 * kN3, bytes, dbar);
+}
 
 // The layer biases enter the tensor-core products: the A operands carry ones in the two K
 // columns after the last unit, and the B blocks carry the bias split into a 16-bit head and
@@ -412,8 +412,8 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
   long long carry = -1;  // (tj, atom) whose partial T sits in slot 0
 
   // the first tile is located here; each later one by the locating warp during the previous
-  // tile's T product (the tile's own sRow facts are kept in registers by then), after which every
-  // thread starts the copy of its row's pair vector into shared memory
+  // tile's T product (the tile's own sRow facts are kept in registers by then), after which
+  // every thread starts the copy of its row's pair vector into shared memory
   if (w == kLocWarp && c0 < c1) locate_tile(a, c0, c0, c1, wk, s_tot, s_tiend, &sti, sRow);
   __syncthreads();
   if (c0 < c1 && t < sti.nrows) stage_pair(a, sti, sRow, t, sNd);
@@ -425,6 +425,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     }
     __syncthreads();
     const TileInfo ti = sti;
+    tc::cp_async_wait_all();  // this thread's row, copied during the previous tile
     if (w == kLocWarp && cur + ti.nrows < c1) locate_window(a, cur + ti.nrows, wk, s_tot, sWin);
     // the write-out's facts about this tile's atom slots (sRow is rewritten mid-tile)
     const int last_la = local_atom(sRow, ti.p + ti.nrows - 1);
@@ -449,7 +450,6 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     float h1[kN1], h2[kN2];
     RowFront f;
     const bool valid = t < ti.nrows;
-    tc::cp_async_wait_all();
     if (valid) {
       f.la = local_atom(sRow, ti.p + t);
       f.atom = ti.a0 + f.la;
@@ -513,11 +513,10 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     // A = G^T read MN-major, B = R_hat^T K-major)
     if (t == 0) {
       const uint32_t id = tc::idesc_mn(tc::idesc_f16(128, 32, true), true, false);
-      for (int k = 0; k < 8; ++k) {
-        const uint64_t ad = tc::sdesc_sw128_mn(tc::smem_u32(sGt) + 2048 * k, 16384);
-        const uint64_t bd = tc::sdesc_sw128(tc::smem_u32(sRs + (k >> 2) * 4096) + 32 * (k & 3));
-        tc::mma_f16(tmem, ad, bd, id, k > 0 ? 1u : 0u);
-      }
+      const uint64_t a0 = tc::sdesc_sw128_mn(tc::smem_u32(sGt), 16384), b0 = tc::sdesc_sw128(tc::smem_u32(sRs));
+      for (int k = 0; k < 8; ++k)
+        tc::mma_f16(tmem, tc::sdesc_add(a0, 2048 * k), tc::sdesc_add(b0, (k >> 2) * 4096 + 32 * (k & 3)), id,
+                    k > 0 ? 1u : 0u);
       tc::mma_commit(&bar);
     }
     __syncwarp();
@@ -647,6 +646,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
   int* sRow = reinterpret_cast<int*>(small + kSmall);                // kMaxAtoms + 1
   int* sWin = sRow + 8;                                              // 32 row offsets
   __shared__ uint64_t bar, dbar;
+  __shared__ int sNat;
   __shared__ uint32_t tslot;
   __shared__ TileInfo sti;
   __shared__ int s_tot[kMaxTypes], s_tiend[kMaxTypes * kMaxTypes];
@@ -683,16 +683,20 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
   const uint32_t idH1 = tc::idesc_mn(tc::idesc_f16(128, 32, F16), false, true);
 
   // the first tile is located here; each later one by the locating warp in the middle of the
-  // previous tile (after the last reads of sti, sRow and sdT), which also starts the copies of the
+  // previous tile (after the last reads of sti, sRow and sdT), followed by the copies of the
   // tile's dE/dT (bulk, on dbar) and rows (per thread) into shared memory
-  if (w == kLocWarp && c0 < c1) locate_tile(a, c0, c0, c1, wk, s_tot, s_tiend, &sti, sRow, nullptr, false, sdT, &dbar);
+  if (w == kLocWarp && c0 < c1) locate_tile(a, c0, c0, c1, wk, s_tot, s_tiend, &sti, sRow, nullptr, false, &sNat);
   __syncthreads();
-  if (c0 < c1 && t < sti.nrows) stage_row(a, sti, sRow, t, sNd, sNj, sRep);
+  if (c0 < c1) {
+    if (t == 32 * kLocWarp) fetch_dT(a, sti.a0, sNat, sdT, &dbar);
+    if (t < sti.nrows) stage_row(a, sti, sRow, t, sNd, sNj, sRep);
+  }
   bool dT_pending = c0 < c1;
   int it = 0;
   for (int cur = c0; cur < c1 && ok; ++it) {
     __syncthreads();
     const TileInfo ti = sti;
+    tc::cp_async_wait_all();  // this thread's row, copied during the previous tile
     if (w == kLocWarp && cur + ti.nrows < c1) locate_window(a, cur + ti.nrows, wk, s_tot, sWin);
     const int np = ti.ti * a.ntypes + ti.tj;
     if (np != pair) {
@@ -700,10 +704,9 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
       pair = np;
       __syncthreads();
     }
-    // this thread's row and the tile's dE/dT, copied during the previous tile
+    // the tile's dE/dT, copied during the previous tile
     RowFront f;
     const bool valid = t < ti.nrows;
-    tc::cp_async_wait_all();
     ok = tc::mbar_wait(&dbar, dphase, a.err) && ok;
     dphase ^= 1u;
     dT_pending = false;
@@ -784,17 +787,19 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
     operand_barrier();
     // dh2' = dz3 W3^T (B = the rows of B3 read MN-major: K = layer-3 column, N = layer-2 unit)
     if (t == 0) {
-      for (int k = 0; k < 8; ++k) {
-        const uint64_t ad = tc::sdesc_sw128(tc::smem_u32(sA + (k >> 2) * 16384) + 32 * (k & 3));
-        const uint64_t bd = tc::sdesc_sw128_mn(tc::smem_u32(sB3) + 2048 * k, 8192);
-        tc::mma_f16(tmem, ad, bd, idH2, k > 0 ? 1u : 0u);
-      }
+      const uint64_t a0 = tc::sdesc_sw128(tc::smem_u32(sA)), b0 = tc::sdesc_sw128_mn(tc::smem_u32(sB3), 8192);
+      for (int k = 0; k < 8; ++k)
+        tc::mma_f16(tmem, tc::sdesc_add(a0, (k >> 2) * 16384 + 32 * (k & 3)), tc::sdesc_add(b0, 2048 * k), idH2,
+                    k > 0 ? 1u : 0u);
       tc::mma_commit(&bar);
     }
     __syncwarp();
-    // while the MMA runs: locate the next tile and start the copies of its dE/dT and rows
-    if (w == kLocWarp && cur + ti.nrows < c1)
-      locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow, sWin, true, sdT, &dbar);
+    // while the MMA runs: locate the next tile and start the copies of its dE/dT (sdT is free
+    // now) and rows
+    if (w == kLocWarp && cur + ti.nrows < c1) {
+      locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow, sWin, true, &sNat);
+      if (lane == 0) fetch_dT(a, sti.a0, sNat, sdT, &dbar);  // values this lane has just written
+    }
     mma_sync_wait(&bar, phase, a.err, ok);
     if (cur + ti.nrows < c1) {
       dT_pending = true;
@@ -834,11 +839,9 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
     operand_barrier();
     // dh1' = dz2 W2^T (B = the rows of B2 read MN-major: K = layer-2 unit, N = layer-1 unit)
     if (t == 0) {
-      for (int k = 0; k < 4; ++k) {
-        const uint64_t ad = tc::sdesc_sw128(tc::smem_u32(sA) + 32 * k);
-        const uint64_t bd = tc::sdesc_sw128_mn(tc::smem_u32(sB2) + 2048 * k, 8192);
-        tc::mma_f16(tmem, ad, bd, idH1, k > 0 ? 1u : 0u);
-      }
+      const uint64_t a0 = tc::sdesc_sw128(tc::smem_u32(sA)), b0 = tc::sdesc_sw128_mn(tc::smem_u32(sB2), 8192);
+      for (int k = 0; k < 4; ++k)
+        tc::mma_f16(tmem, tc::sdesc_add(a0, 32 * k), tc::sdesc_add(b0, 2048 * k), idH1, k > 0 ? 1u : 0u);
       tc::mma_commit(&bar);
     }
     __syncwarp();

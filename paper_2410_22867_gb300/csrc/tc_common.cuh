@@ -209,15 +209,18 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
+// The same shared-memory descriptor `bytes` further on.  The start-address field holds
+// (address >> 4) in the low 14 bits and shared-memory addresses stay below 256 KB, so the add
+// never carries into the other fields.
+__device__ __forceinline__ uint64_t sdesc_add(uint64_t d, uint32_t bytes) { return d + (uint64_t)(bytes >> 4); }
+
 // One K-major SW128 operand block of `rows` rows: MMA over its 64 K elements
 // (4 instructions of K = 16), starting address advanced by 32 bytes per step.
 __device__ __forceinline__ void mma_kblock(uint32_t d_tmem, uint32_t a_saddr, uint32_t b_saddr, uint32_t idesc,
                                           bool accumulate_first, int ksteps = 4) {
-  for (int k = 0; k < ksteps; ++k) {
-    uint64_t a = sdesc_sw128(a_saddr + 32 * k);
-    uint64_t b = sdesc_sw128(b_saddr + 32 * k);
-    mma_f16(d_tmem, a, b, idesc, (accumulate_first || k > 0) ? 1u : 0u);
-  }
+  const uint64_t a = sdesc_sw128(a_saddr), b = sdesc_sw128(b_saddr);
+  for (int k = 0; k < ksteps; ++k)
+    mma_f16(d_tmem, sdesc_add(a, 32 * k), sdesc_add(b, 32 * k), idesc, (accumulate_first || k > 0) ? 1u : 0u);
 }
 
 // ------------------------------------------------------------------ TMEM <-> registers
