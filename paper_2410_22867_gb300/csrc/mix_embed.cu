@@ -1005,7 +1005,7 @@ constexpr int kDescWarps = 8;
 
 template <bool F16>
 __global__ void __launch_bounds__(32 * kDescWarps) k_mix_descriptor(int N, int ntypes, float invS,
-                                                                   const float* __restrict__ Tseg, float* Tm,
+                                                                   const float* __restrict__ Tseg, float4* Tm,
                                                                    unsigned short* Dm) {
   __shared__ __align__(16) float sT[kDescWarps][400];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1019,9 +1019,10 @@ __global__ void __launch_bounds__(32 * kDescWarps) k_mix_descriptor(int N, int n
       }
       v.x *= invS; v.y *= invS; v.z *= invS; v.w *= invS;
       reinterpret_cast<float4*>(T)[q] = v;
-      reinterpret_cast<float4*>(Tm + (size_t)i * 400)[q] = v;
     }
     __syncwarp();
+    for (int aa = lane; aa < kN3; aa += 32)
+      Tm[(size_t)i * kN3 + aa] = make_float4(T[aa], T[kN3 + aa], T[2 * kN3 + aa], T[3 * kN3 + aa]);
     for (int aa = lane; aa < kN3; aa += 32) {
       float out[kM2];
 #pragma unroll
@@ -1042,65 +1043,81 @@ __global__ void __launch_bounds__(32 * kDescWarps) k_mix_descriptor(int N, int n
   }
 }
 
-// dT[c][a] = (1/S) (sum_b dD[a][b] T[c][b] + [a < 16] sum_a' dD[a'][a] T[c][a']), stored [N][100] float4;
-// dD (dE/dD from the fitting kernel) is fp16.
-// One warp per atom: T (4 x 100) and dD (100 x 16, rows padded to 17 floats so that a
-// warp reading one column hits 32 banks) staged in shared memory; the second term's 64
-// outputs (c, a < 16) are split over the 32 lanes, two each.
+// dT[c][a] = (1/S) (sum_b dD[a][b] T[c][b] + [a < 16] sum_a' dD[a'][a] T[c][a']), stored [N][100]
+// float4; dD (dE/dD from the fitting kernel) is fp16 and T is stored feature-major ([N][100]
+// float4 of the four components).
+// One warp per atom at a time: the atom's T and dD are copied into a per-warp double buffer by
+// cp.async one atom ahead, so the copies of the next atom overlap this one's arithmetic.  The
+// second term's 64 outputs (c, a < 16) take lanes (a, half of the a' range) and one shuffle.
 constexpr int kDtWarps = 4;
-constexpr int kDtRow = kM2 + 1;
 
-__global__ void __launch_bounds__(32 * kDtWarps) k_mix_dT(int N, float invS, const float* __restrict__ Tm,
+__global__ void __launch_bounds__(32 * kDtWarps) k_mix_dT(int N, float invS, const float4* __restrict__ Tm,
                                                          const unsigned short* __restrict__ dD,
                                                          float4* __restrict__ dT) {
-  __shared__ __align__(16) float sT[kDtWarps][400];
-  __shared__ float sD[kDtWarps][kN3 * kDtRow];
-  __shared__ float s2[kDtWarps][4 * kM2];
+  __shared__ __align__(16) float4 sT[kDtWarps][2][kN3];
+  __shared__ __align__(16) unsigned short sD[kDtWarps][2][kKD];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  float* T = sT[w];
-  float* D = sD[w];
-  float* t2 = s2[w];
-  for (int i = blockIdx.x * kDtWarps + w; i < N; i += gridDim.x * kDtWarps) {
-    const float4* Ti = reinterpret_cast<const float4*>(Tm + (size_t)i * 400);
-    for (int q = lane; q < 100; q += 32) reinterpret_cast<float4*>(T)[q] = Ti[q];
-    const uint4* Di = reinterpret_cast<const uint4*>(dD + (size_t)i * kKD);  // fp16, 8 per load
-    for (int q = lane; q < kKD / 8; q += 32) {
-      const uint4 v = Di[q];
-      const uint32_t p[4] = {v.x, v.y, v.z, v.w};
-      float* d = D + (q >> 1) * kDtRow + (q & 1) * 8;
+  const int stride = gridDim.x * kDtWarps;
+  auto issue = [&](int atom, int buf) {
+    const float4* Ti = Tm + (size_t)atom * kN3;
+    for (int q = lane; q < kN3; q += 32) tc::cp_async16(&sT[w][buf][q], Ti + q);
+    const uint4* Di = reinterpret_cast<const uint4*>(dD + (size_t)atom * kKD);
+    uint4* Ds = reinterpret_cast<uint4*>(sD[w][buf]);
+    for (int q = lane; q < kKD / 8; q += 32) tc::cp_async16(Ds + q, Di + q);
+    tc::cp_async_commit();
+  };
+  int i = blockIdx.x * kDtWarps + w;
+  if (i < N) issue(i, 0);
+  for (int buf = 0; i < N; i += stride, buf ^= 1) {
+    if (i + stride < N) {
+      issue(i + stride, buf ^ 1);
+      tc::cp_async_wait_group<1>();
+    } else {
+      tc::cp_async_wait_group<0>();
+    }
+    __syncwarp();
+    const float4* T = sT[w][buf];
+    const __half* D = reinterpret_cast<const __half*>(sD[w][buf]);
+    // second term: lane -> a = lane % 16 over a' in [50 h, 50 h + 50), h = lane / 16
+    float u[4] = {0.f, 0.f, 0.f, 0.f};
+    {
+      const int a = lane & 15, h = lane >> 4;
+#pragma unroll 5
+      for (int a2 = 50 * h; a2 < 50 * h + 50; ++a2) {
+        const float d = __half2float(D[a2 * kM2 + a]);
+        const float4 tv = T[a2];
+        u[0] = fmaf(d, tv.x, u[0]); u[1] = fmaf(d, tv.y, u[1]);
+        u[2] = fmaf(d, tv.z, u[2]); u[3] = fmaf(d, tv.w, u[3]);
+      }
 #pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const float2 f2 = __half22float2(*reinterpret_cast<const __half2*>(&p[h]));
-        d[2 * h] = f2.x;
-        d[2 * h + 1] = f2.y;
-      }
+      for (int c = 0; c < 4; ++c) u[c] += __shfl_xor_sync(0xffffffffu, u[c], 16);
     }
-    __syncwarp();
-    {  // second term: lane -> a = lane % 16, c = lane / 16 and c + 2
-      const int a = lane & 15, c = lane >> 4;
-      float u0 = 0.f, u1 = 0.f;
-      for (int a2 = 0; a2 < kN3; ++a2) {
-        const float d = D[a2 * kDtRow + a];
-        u0 = fmaf(d, T[c * kN3 + a2], u0);
-        u1 = fmaf(d, T[(c + 2) * kN3 + a2], u1);
-      }
-      t2[c * kM2 + a] = u0;
-      t2[(c + 2) * kM2 + a] = u1;
-    }
-    __syncwarp();
+    // first term: lane -> features a = lane, lane + 32, ...; T[b] for b < 16 held in registers
+    float4 tb[kM2];
+#pragma unroll
+    for (int b = 0; b < kM2; ++b) tb[b] = T[b];
     for (int a = lane; a < kN3; a += 32) {
       float v[4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) v[c] = (a < kM2) ? t2[c * kM2 + a] : 0.f;
+      for (int c = 0; c < 4; ++c) v[c] = (a < kM2) ? u[c] : 0.f;
+      const uint4* Drow = reinterpret_cast<const uint4*>(D + a * kM2);
 #pragma unroll
-      for (int b = 0; b < kM2; ++b) {
-        const float d = D[a * kDtRow + b];
+      for (int hc = 0; hc < 2; ++hc) {
+        const uint4 raw = Drow[hc];
+        const uint32_t p[4] = {raw.x, raw.y, raw.z, raw.w};
 #pragma unroll
-        for (int c = 0; c < 4; ++c) v[c] = fmaf(d, T[c * kN3 + b], v[c]);
+        for (int e = 0; e < 4; ++e) {
+          const float2 d2 = __half22float2(*reinterpret_cast<const __half2*>(&p[e]));
+          const float4 t0 = tb[8 * hc + 2 * e], t1 = tb[8 * hc + 2 * e + 1];
+          v[0] = fmaf(d2.x, t0.x, v[0]); v[1] = fmaf(d2.x, t0.y, v[1]);
+          v[2] = fmaf(d2.x, t0.z, v[2]); v[3] = fmaf(d2.x, t0.w, v[3]);
+          v[0] = fmaf(d2.y, t1.x, v[0]); v[1] = fmaf(d2.y, t1.y, v[1]);
+          v[2] = fmaf(d2.y, t1.z, v[2]); v[3] = fmaf(d2.y, t1.w, v[3]);
+        }
       }
       dT[(size_t)i * kN3 + a] = make_float4(v[0] * invS, v[1] * invS, v[2] * invS, v[3] * invS);
     }
-    __syncwarp();
+    __syncwarp();  // every lane is done with this buffer before it is refilled
   }
 }
 
@@ -1147,10 +1164,10 @@ dp_status launch_mix_descriptor(Model* m, int N) {
   const int dgrid = std::max(1, std::min((N + kDescWarps - 1) / kDescWarps, tuned_grid(m, 3, 8 * num_sms())));
   if (f16)
     k_mix_descriptor<true><<<dgrid, 32 * kDescWarps, 0, m->stream>>>(
-        N, m->ntypes, 1.f / (float)m->S, m->Tseg, static_cast<float*>(m->Tm), static_cast<unsigned short*>(m->Dm));
+        N, m->ntypes, 1.f / (float)m->S, m->Tseg, static_cast<float4*>(m->Tm), static_cast<unsigned short*>(m->Dm));
   else
     k_mix_descriptor<false><<<dgrid, 32 * kDescWarps, 0, m->stream>>>(
-        N, m->ntypes, 1.f / (float)m->S, m->Tseg, static_cast<float*>(m->Tm), static_cast<unsigned short*>(m->Dm));
+        N, m->ntypes, 1.f / (float)m->S, m->Tseg, static_cast<float4*>(m->Tm), static_cast<unsigned short*>(m->Dm));
   m->launches += 4;
   DP_LAUNCH_CHECK(m);
   return DP_OK;
@@ -1158,7 +1175,7 @@ dp_status launch_mix_descriptor(Model* m, int N) {
 
 dp_status launch_mix_embed_backward(Model* m, int N) {
   const int dt_grid = std::max(1, std::min((N + kDtWarps - 1) / kDtWarps, tuned_grid(m, 2, 5 * num_sms())));
-  k_mix_dT<<<dt_grid, 32 * kDtWarps, 0, m->stream>>>(N, 1.f / (float)m->S, static_cast<const float*>(m->Tm),
+  k_mix_dT<<<dt_grid, 32 * kDtWarps, 0, m->stream>>>(N, 1.f / (float)m->S, static_cast<const float4*>(m->Tm),
                                                               static_cast<const unsigned short*>(m->dD),
                                                               static_cast<float4*>(m->dTm));
   DP_CUDA_TRY(m, cudaMemsetAsync(m->vir_rep, 0, sizeof(double) * 9 * (size_t)m->nrep, m->stream));
