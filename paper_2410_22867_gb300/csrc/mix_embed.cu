@@ -997,49 +997,80 @@ __global__ void k_scan_fix(int N, int nblk, int* rowoff, const int* blk) {
   if (i < N) rowoff[(size_t)tj * (N + 1) + i] += off;
 }
 
-// T = sum over neighbour types of the partial sums, scaled by 1/S (kept in FP32 for the
-// dE/dT kernel); D = T^T T[:, :16] in 16 bits for the fitting net.  One warp per atom: T
-// (float4 loads) in shared memory, then lane -> rows a = lane, lane + 32, ... of D (16
-// values, two 16-byte stores).
-constexpr int kDescWarps = 8;
+// T = sum over neighbour types of the partial sums, scaled by 1/S (kept in FP32, feature-major,
+// for the dE/dT kernel); D = T^T T[:, :16] in 16 bits for the fitting net.  One warp per atom
+// at a time: the atom's partial sums (one 1.6 KB segment per neighbour type) are copied into a
+// per-warp double buffer in dynamic shared memory by cp.async one atom ahead; T[c][b < 16] is
+// held in registers and lane -> rows a = lane, lane + 32, ... of D (16 values, two 16-byte
+// stores).
+constexpr int kDescWarps = 4;
 
 template <bool F16>
 __global__ void __launch_bounds__(32 * kDescWarps) k_mix_descriptor(int N, int ntypes, float invS,
                                                                    const float* __restrict__ Tseg, float4* Tm,
                                                                    unsigned short* Dm) {
-  __shared__ __align__(16) float sT[kDescWarps][400];
+  extern __shared__ float4 sbuf[];  // [kDescWarps][2][ntypes][100]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  float* T = sT[w];
-  for (int i = blockIdx.x * kDescWarps + w; i < N; i += gridDim.x * kDescWarps) {
-    for (int q = lane; q < 100; q += 32) {
-      float4 v = reinterpret_cast<const float4*>(Tseg + (size_t)i * 400)[q];
+  float4* mine = sbuf + (size_t)w * 2 * ntypes * kN3;
+  const int stride = gridDim.x * kDescWarps;
+  auto issue = [&](int atom, int buf) {
+    float4* dst = mine + buf * ntypes * kN3;
+    for (int tj = 0; tj < ntypes; ++tj) {
+      const float4* src = reinterpret_cast<const float4*>(Tseg + ((size_t)tj * N + atom) * 400);
+      for (int q = lane; q < kN3; q += 32) tc::cp_async16(dst + tj * kN3 + q, src + q);
+    }
+    tc::cp_async_commit();
+  };
+  int i = blockIdx.x * kDescWarps + w;
+  if (i < N) issue(i, 0);
+  for (int buf = 0; i < N; i += stride, buf ^= 1) {
+    if (i + stride < N) {
+      issue(i + stride, buf ^ 1);
+      tc::cp_async_wait_group<1>();
+    } else {
+      tc::cp_async_wait_group<0>();
+    }
+    __syncwarp();
+    float4* seg = mine + buf * ntypes * kN3;
+    // T (c-major, 400 floats) in place of the first segment
+    for (int q = lane; q < kN3; q += 32) {
+      float4 v = seg[q];
       for (int tj = 1; tj < ntypes; ++tj) {
-        const float4 u = reinterpret_cast<const float4*>(Tseg + ((size_t)tj * N + i) * 400)[q];
+        const float4 u = seg[tj * kN3 + q];
         v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
       }
       v.x *= invS; v.y *= invS; v.z *= invS; v.w *= invS;
-      reinterpret_cast<float4*>(T)[q] = v;
+      seg[q] = v;
     }
     __syncwarp();
-    for (int aa = lane; aa < kN3; aa += 32)
-      Tm[(size_t)i * kN3 + aa] = make_float4(T[aa], T[kN3 + aa], T[2 * kN3 + aa], T[3 * kN3 + aa]);
-    for (int aa = lane; aa < kN3; aa += 32) {
-      float out[kM2];
+    const float* T = reinterpret_cast<const float*>(seg);
+    float tb[4][kM2];
 #pragma unroll
-      for (int b = 0; b < kM2; ++b) {
-        float v = 0.f;
+    for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) v = fmaf(T[c * kN3 + aa], T[c * kN3 + b], v);
-        out[b] = v;
+      for (int b4 = 0; b4 < kM2 / 4; ++b4) {
+        const float4 v = seg[(c * kN3) / 4 + b4];
+        tb[c][4 * b4] = v.x; tb[c][4 * b4 + 1] = v.y; tb[c][4 * b4 + 2] = v.z; tb[c][4 * b4 + 3] = v.w;
       }
+    for (int aa = lane; aa < kN3; aa += 32) {
+      const float t0 = T[aa], t1 = T[kN3 + aa], t2 = T[2 * kN3 + aa], t3 = T[3 * kN3 + aa];
+      Tm[(size_t)i * kN3 + aa] = make_float4(t0, t1, t2, t3);
       uint32_t pk[8];
 #pragma unroll
-      for (int h = 0; h < 8; ++h) pk[h] = tc::pack2<F16>(out[2 * h], out[2 * h + 1]);
+      for (int h = 0; h < 8; ++h) {
+        float o[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int b = 2 * h + e;
+          o[e] = fmaf(t3, tb[3][b], fmaf(t2, tb[2][b], fmaf(t1, tb[1][b], t0 * tb[0][b])));
+        }
+        pk[h] = tc::pack2<F16>(o[0], o[1]);
+      }
       uint4* dst = reinterpret_cast<uint4*>(Dm + (size_t)i * kKD + aa * kM2);
       dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
       dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
     }
-    __syncwarp();
+    __syncwarp();  // every lane is done with this buffer before it is refilled
   }
 }
 
@@ -1162,11 +1193,15 @@ dp_status launch_mix_descriptor(Model* m, int N) {
   else k_mix_embed_fwd<false><<<grid, kRows, kFwdSmem, m->stream>>>(a);
   if (m->sub_ev[0]) DP_CUDA_TRY(m, cudaEventRecord(m->sub_ev[0], m->stream));
   const int dgrid = std::max(1, std::min((N + kDescWarps - 1) / kDescWarps, tuned_grid(m, 3, 8 * num_sms())));
+  const size_t dsm = (size_t)kDescWarps * 2 * m->ntypes * kN3 * sizeof(float4);
+  const void* dfn = f16 ? reinterpret_cast<const void*>(k_mix_descriptor<true>)
+                        : reinterpret_cast<const void*>(k_mix_descriptor<false>);
+  DP_CUDA_TRY(m, ensure_smem(dfn, dsm));
   if (f16)
-    k_mix_descriptor<true><<<dgrid, 32 * kDescWarps, 0, m->stream>>>(
+    k_mix_descriptor<true><<<dgrid, 32 * kDescWarps, dsm, m->stream>>>(
         N, m->ntypes, 1.f / (float)m->S, m->Tseg, static_cast<float4*>(m->Tm), static_cast<unsigned short*>(m->Dm));
   else
-    k_mix_descriptor<false><<<dgrid, 32 * kDescWarps, 0, m->stream>>>(
+    k_mix_descriptor<false><<<dgrid, 32 * kDescWarps, dsm, m->stream>>>(
         N, m->ntypes, 1.f / (float)m->S, m->Tseg, static_cast<float4*>(m->Tm), static_cast<unsigned short*>(m->Dm));
   m->launches += 4;
   DP_LAUNCH_CHECK(m);
