@@ -15,6 +15,8 @@
 // "Split": x = x_hi + x_lo with both halves 16-bit, x*w ~ x_hi w_hi + x_hi w_lo +
 // x_lo w_hi, which keeps ~16 mantissa bits; rounding the 240 x 240 layers to plain
 // 16 bits biases E_i by ~1e-3 eV (bf16), above the 1e-4 eV/atom target.
+// The activations tanh come from e^{2x} (hardware base-2 exponential and reciprocal), within
+// ~1e-6 absolute: an E_i error far below the 1e-4 eV/atom target.
 // dE/dD is written in fp16 for the dE/dT kernel.
 // The activation operand X (hi and lo) lives in shared memory, the FP32 residual
 // stream (h1, h2, dh2) in TMEM columns 256..495, the factors 1 - h1^2 and 1 - t2^2
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
       tc::tmem_wait_ld();
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
-        h[u] = tanhf(z[u] + b1[16 * c + u]);
+        h[u] = tc::tanh_exp(z[u] + b1[16 * c + u]);
         f[u] = 1.f - h[u] * h[u];
       }
       store_x16<F16>(sm, row, 16 * c, h, true);
@@ -364,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
       tc::tmem_wait_ld();
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
-        const float t2 = tanhf(z[u] + b2[16 * c + u]);
+        const float t2 = tc::tanh_exp(z[u] + b2[16 * c + u]);
         r[u] += t2;
         f[u] = 1.f - t2 * t2;
       }
@@ -390,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
       tc::tmem_wait_ld();
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
-        const float t3 = tanhf(z[u] + b3[16 * c + u]);
+        const float t3 = tc::tanh_exp(z[u] + b3[16 * c + u]);
         const float wv = w4[16 * c + u];
         e = fmaf(r[u] + t3, wv, e);
         dz[u] = wv * (1.f - t3 * t3);

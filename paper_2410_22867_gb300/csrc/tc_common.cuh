@@ -287,6 +287,16 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
 }
 
 // tanh on the SFU (single MUFU op; max relative error about 2^-11)
+// tanh(x) = 1 - 2 / (e^{2x} + 1) from the base-2 exponential and reciprocal approximations
+// (each within a few ulp): absolute error below ~1e-6 over the whole range, limits exactly
+// -1 and +1 (e^{2x} underflows to 0 or overflows to infinity).
+__device__ __forceinline__ float tanh_exp(float x) {
+  float e, r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(x * 2.885390081777927f));  // 2 / ln 2
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(e + 1.f));
+  return fmaf(-2.f, r, 1.f);
+}
+
 __device__ __forceinline__ float tanh_fast(float x) {
   float y;
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
