@@ -548,7 +548,7 @@ dp_status dp_create(dp_model** out, int ntypes, const char* const* type_map, dou
   A_(geom, sizeof(RepGeom) * R);
   A_(cell_of, 4 * N);
   A_(cell_count, 4 * (size_t)m->max_cells); A_(cell_start, 4 * ((size_t)m->max_cells + 1));
-  A_(cell_fill, 4 * (size_t)m->max_cells); A_(cell_atoms, 4 * N);
+  A_(cell_fill, 4 * (size_t)m->max_cells); A_(cell_atoms, 4 * N); A_(cell_xf, 16 * N);
   A_(vl_j, 4 * N * m->VS); A_(vl_img, 4 * N * m->VS); A_(vl_d0, 16 * N * m->VS); A_(vcount, 4 * N * nt);
   A_(nl_j, 4 * N * m->S); A_(nl_img, 4 * N * m->S);
   A_(nl_d, (prec == DP_FP64 ? 32 : 16) * N * m->S);

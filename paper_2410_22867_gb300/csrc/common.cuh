@@ -118,6 +118,7 @@ struct Model {
   int* cell_start = nullptr;
   int* cell_fill = nullptr;
   int* cell_atoms = nullptr;
+  float4* cell_xf = nullptr;  // [N] FP32 positions in cell order (beside cell_atoms)
 
   // Verlet list (r_c + skin)
   int* vl_j = nullptr;        // [N*VS]

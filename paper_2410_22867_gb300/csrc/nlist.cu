@@ -185,13 +185,16 @@ __global__ void k_scan_cells(int ncells, const int* __restrict__ cell_count, int
   if (threadIdx.x == 0) cell_start[ncells] = carry;
 }
 
+// Counting-sort scatter: the atoms of each cell, and their FP32 positions in the same order
+// (so the Verlet walk reads index and position of a candidate with two independent loads).
 __global__ void k_fill_cells(int N, const int* __restrict__ cell_of, const int* __restrict__ cell_start,
-                             int* cell_fill, int* cell_atoms) {
+                             const float4* __restrict__ xf, int* cell_fill, int* cell_atoms, float4* cell_xf) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= N) return;
   int cid = cell_of[k];
   int pos = cell_start[cid] + atomicAdd(&cell_fill[cid], 1);
   cell_atoms[pos] = k;
+  cell_xf[pos] = xf[k];
 }
 
 // ------------------------------------------------------------------ Verlet list
@@ -209,6 +212,7 @@ struct VerletArgs {
   const int* cell_of;
   const int* cell_start;
   const int* cell_atoms;
+  const float4* cell_xf;
   int* vl_j;
   int* vl_img;
   float4* vl_d0;
@@ -234,7 +238,8 @@ __device__ __forceinline__ float fixed_diff(long long qj, long long qi, int n, l
 // FP64 test near the cutoff), so a pair is taken when its FP32 r^2 is below (r_c + skin)^2
 // plus a band wider than the FP32 rounding error: no FP64 in the candidate test.  The
 // stencil's cells are taken 32 at a time; their candidates form one flat range that the
-// lanes walk two at a time (independent gathers in flight).  Accepted pairs go straight to
+// lanes walk four at a time (independent loads of the cell-ordered index and position in
+// flight).  Accepted pairs go straight to
 // the list, grouped by neighbour type, in the order found: every consumer is independent
 // of the order within a type (the descriptor is a sum over neighbours; the format is a
 // compaction), and dp_get_nlist sorts a copy into the canonical order.  The pair vector at
@@ -268,10 +273,11 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
       const int mid = (lo + hi + 1) >> 1;
       if (s_off[w][mid] <= q) lo = mid; else hi = mid - 1;
     }
-    j = a.cell_atoms[s_beg[w][lo] + q - s_off[w][lo]];
+    const int idx = s_beg[w][lo] + q - s_off[w][lo];
+    j = a.cell_atoms[idx];
+    const float4 xfj = a.cell_xf[idx];
     code = s_img[w][lo];
     if (j == i && code == self_code) return;
-    const float4 xfj = a.xf[j];
     const float dx = (xfj.x + s_sh[w][lo][0]) - xfi.x;
     const float dy = (xfj.y + s_sh[w][lo][1]) - xfi.y;
     const float dz = (xfj.z + s_sh[w][lo][2]) - xfi.z;
@@ -334,13 +340,13 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
     s_sh[w][lane][0] = sh[0]; s_sh[w][lane][1] = sh[1]; s_sh[w][lane][2] = sh[2];
     __syncwarp();
     const int nb = min(32, ncell - cb);
-    for (int base = 0; base < total; base += 64) {
-      bool acc0, acc1;
-      int j0, j1, t0, t1, c0, c1;
-      fetch(base + lane, total, nb, acc0, j0, t0, c0);
-      fetch(base + 32 + lane, total, nb, acc1, j1, t1, c1);
-      append(acc0, j0, t0, c0);
-      append(acc1, j1, t1, c1);
+    for (int base = 0; base < total; base += 128) {
+      bool acc[4];
+      int jj[4], tt[4], cc[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) fetch(base + 32 * h + lane, total, nb, acc[h], jj[h], tt[h], cc[h]);
+#pragma unroll
+      for (int h = 0; h < 4; ++h) append(acc[h], jj[h], tt[h], cc[h]);
     }
     __syncwarp();
   }
@@ -526,7 +532,8 @@ dp_status launch_rebuild(Model* m, int N) {
   k_wrap_bin<<<cdiv(N, 256), 256, 0, s>>>(N, m->irep, m->itype, m->geom, m->x, m->xref, m->xf, m->xq,
                                           m->delta, m->cell_of, m->cell_count);
   k_scan_cells<<<1, 1024, 0, s>>>(m->ncells, m->cell_count, m->cell_start);
-  k_fill_cells<<<cdiv(N, 256), 256, 0, s>>>(N, m->cell_of, m->cell_start, m->cell_fill, m->cell_atoms);
+  k_fill_cells<<<cdiv(N, 256), 256, 0, s>>>(N, m->cell_of, m->cell_start, m->xf, m->cell_fill, m->cell_atoms,
+                                            m->cell_xf);
   VerletArgs a;
   a.N = N; a.ntypes = m->ntypes; a.VS = m->VS;
   for (int t = 0; t < m->ntypes; ++t) {
@@ -540,7 +547,7 @@ dp_status launch_rebuild(Model* m, int N) {
   double band = 1.25e-5 * rcs * (max_box_length(m) + rcs) + 1e-3;
   a.rcs2_hi = (float)(a.rcs2 + band);
   a.itype = m->itype; a.irep = m->irep; a.geom = m->geom; a.x = m->x; a.xf = m->xf; a.xq = m->xq;
-  a.cell_of = m->cell_of; a.cell_start = m->cell_start; a.cell_atoms = m->cell_atoms;
+  a.cell_of = m->cell_of; a.cell_start = m->cell_start; a.cell_atoms = m->cell_atoms; a.cell_xf = m->cell_xf;
   a.vl_j = m->vl_j; a.vl_img = m->vl_img; a.vl_d0 = m->vl_d0; a.vcount = m->vcount; a.err = m->err;
   k_verlet<<<cdiv(N, kVerletWarps), 32 * kVerletWarps, 0, s>>>(a);
   m->launches += 4;
