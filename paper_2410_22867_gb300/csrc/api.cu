@@ -127,40 +127,46 @@ dp_status setup_replicas(Model* m, int nrep, const int* offs, const double* boxe
   DP_CUDA_TRY(m, cudaStreamSynchronize(m->stream));
   int* off_h = reinterpret_cast<int*>(m->geom_host + m->max_reps);
   const double rcs = m->rc + m->skin;
+  // Cells of edge >= (r_c + skin) / 2 and a 5 x 5 x 5 stencil when they fit the allocated cell
+  // list (about half the candidates of edge >= r_c + skin with 3 x 3 x 3), else full-size cells.
   int cells = 0;
-  for (int r = 0; r < nrep; ++r) {
-    const double* b = boxes + 9 * r;
-    for (int a = 0; a < 3; ++a)
-      for (int c = 0; c < 3; ++c)
-        if (a != c && b[3 * a + c] != 0.0) {
-          m->last_error = "only orthorhombic boxes are supported";
-          return DP_ERR_UNSUPPORTED;
-        }
-    RepGeom& g = m->geom_host[r];
-    std::memset(&g, 0, sizeof(g));
-    const double eff = rcs * (1.0 + 1e-9);
-    int ncr = 1;
-    for (int a = 0; a < 3; ++a) {
-      double L = b[4 * a];
-      if (!(L > 0.0) || !std::isfinite(L)) { m->last_error = "box length must be positive"; return DP_ERR_ARG; }
-      g.L[a] = L;
-      g.Lf[a] = (float)L;
-      g.Lq[a] = std::llrint(L * 4294967296.0);
-      int nc = (int)std::floor(L / eff);
-      if (nc < 1) nc = 1;
-      if (nc > 1024) nc = 1024;
-      g.nc[a] = nc;
-      g.edge[a] = L / nc;
-      g.m[a] = (int)std::ceil(eff / g.edge[a]);
-      if (g.m[a] > 200) { m->last_error = "box too small for the cutoff"; return DP_ERR_UNSUPPORTED; }
-      if (L >= 2147483648.0) { m->last_error = "box length too large"; return DP_ERR_UNSUPPORTED; }
-      ncr *= nc;
+  for (int div = 2; div >= 1; --div) {
+    cells = 0;
+    for (int r = 0; r < nrep; ++r) {
+      const double* b = boxes + 9 * r;
+      for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c)
+          if (a != c && b[3 * a + c] != 0.0) {
+            m->last_error = "only orthorhombic boxes are supported";
+            return DP_ERR_UNSUPPORTED;
+          }
+      RepGeom& g = m->geom_host[r];
+      std::memset(&g, 0, sizeof(g));
+      const double eff = rcs * (1.0 + 1e-9);
+      int ncr = 1;
+      for (int a = 0; a < 3; ++a) {
+        double L = b[4 * a];
+        if (!(L > 0.0) || !std::isfinite(L)) { m->last_error = "box length must be positive"; return DP_ERR_ARG; }
+        g.L[a] = L;
+        g.Lf[a] = (float)L;
+        g.Lq[a] = std::llrint(L * 4294967296.0);
+        int nc = (int)std::floor(div * L / eff);
+        if (nc < 1) nc = 1;
+        if (nc > 1024) nc = 1024;
+        g.nc[a] = nc;
+        g.edge[a] = L / nc;
+        g.m[a] = (int)std::ceil(eff / g.edge[a]);
+        if (g.m[a] > 200) { m->last_error = "box too small for the cutoff"; return DP_ERR_UNSUPPORTED; }
+        if (L >= 2147483648.0) { m->last_error = "box length too large"; return DP_ERR_UNSUPPORTED; }
+        ncr *= nc;
+      }
+      g.cell_off = cells;
+      g.atom_off = offs ? offs[r] : 0;
+      g.natoms = offs ? offs[r + 1] - offs[r] : N;
+      cells += ncr;
+      off_h[r] = g.atom_off;
     }
-    g.cell_off = cells;
-    g.atom_off = offs ? offs[r] : 0;
-    g.natoms = offs ? offs[r + 1] - offs[r] : N;
-    cells += ncr;
-    off_h[r] = g.atom_off;
+    if (cells <= m->max_cells) break;
   }
   off_h[nrep] = offs ? offs[nrep] : N;
   if (off_h[nrep] != N || off_h[0] != 0) { m->last_error = "atom_offsets must run from 0 to natoms"; return DP_ERR_ARG; }
