@@ -55,6 +55,27 @@ def test_nlist_bit_exact(dp, prec, case):
     _nl_rows_equal(nl.cpu().numpy(), im.cpu().numpy(), ref_nl, ref_im)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mix_fp16"])
+def test_nlist_bit_exact_sparse_box(dp, prec):
+    # A 108-atom copper cluster in a 70 A box, straddling the periodic corner.  Half-size cells
+    # would need 14^3 = 2744 cells, more than the cell list holds for 108 atoms (1196), so the
+    # library falls back to cells of edge >= r_c + skin (7^3).
+    c = synth.copper_fcc(3, 5)
+    L = 70.0
+    coords = np.mod(c.coords - 4.0, L)
+    s = synth.System(coords, c.types, np.array([L, 0, 0, 0, L, 0, 0, 0, L], dtype=np.float64), c.type_names)
+    w = synth.copper_weights()
+    ref_nl, ref_im, _, ovf = oracle.Model(w.to_blob()).nlist(s.coords, s.types, s.box, "brute")
+    assert not ovf
+    assert (ref_nl >= 0).sum() > 50 * s.natoms  # a dense cluster: most pairs are real neighbours
+    m = dp.DPModel(w, prec, max_atoms=s.natoms)
+    x, t = _cuda(s)
+    m.compute(x, t, s.box)
+    nl, im = m.get_nlist()
+    _nl_rows_equal(nl.cpu().numpy(), im.cpu().numpy(), ref_nl, ref_im)
+    m.close()
+
+
 def test_nlist_bit_exact_copper_full(dp):
     s = synth.copper_fcc(32, 0)
     w = synth.copper_weights()
