@@ -17,6 +17,10 @@
 // (thread = feature) and is written once the atom is complete; only atoms split
 // between two CTAs use global atomics.  Activations of the embedding net are
 // recomputed in the backward instead of being stored.
+//
+// Latency.  Both kernels run 3 CTAs of 4 warps per SM.  Thread 0 issues the MMAs; warp 1
+// locates the next tile while the last product of a tile runs, and the tile's data (rows
+// by per-thread cp.async, dE/dT by one bulk copy) arrive in shared memory before it starts.
 #include "tc_common.cuh"
 
 namespace dpg {
@@ -364,6 +368,9 @@ __device__ __forceinline__ void operand_barrier() {
 }
 
 // ------------------------------------------------------------------ forward
+// Embedding forward and T: per 128-row tile the environment row and layer 1 on the CUDA
+// cores, z2 = h1 W2 and z3 = h2 W3 on the tensor core (biases folded in), G = [h2, h2] +
+// tanh(z3), and the T product of G^T against the block-sparse R_hat^T.
 template <bool F16>
 __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
   extern __shared__ unsigned char sraw[];
@@ -625,8 +632,8 @@ __device__ void load_bwd_ops(const float* __restrict__ W, unsigned char* sB2, un
   load_small(W, small);
 }
 
-// Embedding backward with recompute, prod_force and per-atom virial.  One row per thread and
-// TMEM lane; per tile four tensor-core products (z2 = h1 W2, z3 = h2 W3, dh2' = dz3 W3^T,
+// Embedding backward with recompute, prod_force and the per-replica virial.  One row per
+// thread and TMEM lane; per tile four tensor-core products (z2 = h1 W2, z3 = h2 W3, dh2' = dz3 W3^T,
 // dh1' = dz2 W2^T; the last two read B3 / B2 MN-major).  The layer-3 epilogue takes the
 // features m and m + 50 together, so the residual part dG[m] + dG[m + 50] of dE/dh2 is final
 // when formed; it is parked in the TMEM columns of z3 just read, and added back after the
