@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -201,7 +202,9 @@ inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 // Raise a kernel's dynamic shared-memory limit once (not from inside stream capture
 // after the first call: the attribute call is skipped when already large enough).
 inline cudaError_t ensure_smem(const void* fn, size_t smem) {
+  static std::mutex mu;  // models may be driven from several host threads
   static std::vector<std::pair<const void*, size_t>> done;
+  std::lock_guard<std::mutex> lock(mu);
   for (auto& e : done)
     if (e.first == fn && e.second >= smem) return cudaSuccess;
   cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -216,7 +219,9 @@ inline cudaError_t ensure_smem(const void* fn, size_t smem) {
 // (tcgen05 kernels hold `tmem_cols` of the SM's 512 columns each).  Cached.
 inline int blocks_per_sm(const void* fn, int threads, size_t smem, int tmem_cols = 0) {
   struct E { const void* f; int t; size_t s; int c; int n; };
+  static std::mutex mu;
   static std::vector<E> cache;
+  std::lock_guard<std::mutex> lock(mu);
   for (auto& e : cache)
     if (e.f == fn && e.t == threads && e.s == smem && e.c == tmem_cols) return e.n;
   int dev = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0;

@@ -24,6 +24,8 @@
 // jobs ahead of the MMAs in slots carved from whichever buffers the current GEMM
 // does not read.
 #include <cstring>
+#include <deque>
+#include <mutex>
 
 #include "tc_common.cuh"
 
@@ -614,7 +616,9 @@ bool make_map(CUtensorMap* map, void* base, bool f16, uint64_t cols, uint64_t ro
 }
 
 FitMaps* maps_of(Model* m) {
-  static std::vector<std::pair<Model*, FitMaps>> table;
+  static std::mutex mu;
+  static std::deque<std::pair<Model*, FitMaps>> table;  // stable addresses across push_back
+  std::lock_guard<std::mutex> lock(mu);
   for (auto& e : table)
     if (e.first == m) return &e.second;
   table.push_back({m, FitMaps{}});
