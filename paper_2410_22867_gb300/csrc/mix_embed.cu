@@ -77,6 +77,9 @@ __device__ __forceinline__ void switch_fn(float r, float rs, float rc, float win
 // Shared state of a tile walk.
 struct TileInfo {
   int tj, ti, p, nrows, a0, cs, ce;  // stream, centre type, first row (stream coords), rows, first atom, chunk
+  // for the forward's write-out: slot of the tile's last atom, whether the tile completes it,
+  // and the slots whose atom starts before or ends after this CTA's chunk
+  int last_la, last_done, shared_mask;
 };
 
 // Walk state of one CTA over the concatenated streams (held uniformly by the locating warp).
@@ -161,15 +164,21 @@ __device__ __forceinline__ void locate_tile(const MixArgs& a, int cur, int c0, i
   end = min(end, tiend[tj * a.ntypes + ti]);
   end = min(end, r8);
   end = min(end, p + kRows);
+  // lanes 1 .. kMaxAtoms - 1 hold the offsets of the atoms after a0: the tile's last atom is the
+  // last one starting before its end (also the hint for the next tile)
+  const int last = a0 + __popc(__ballot_sync(0xffffffffu, lane >= 1 && lane < kMaxAtoms && rk <= end - 1));
+  const int cs = c0 - wk.base, ce = c1 - wk.base;
+  const int rk_next = __shfl_down_sync(0xffffffffu, rk, 1);  // ro[a0 + lane + 1]
+  const unsigned shared = __ballot_sync(0xffffffffu, lane < kMaxAtoms && (rk < cs || rk_next > ce));
+  const int rk_after_last = __shfl_sync(0xffffffffu, rk, last - a0 + 1);
   if (lane == 0) {
     TileInfo t;
-    t.tj = tj; t.ti = ti; t.p = p; t.nrows = end - p; t.a0 = a0; t.cs = c0 - wk.base; t.ce = c1 - wk.base;
+    t.tj = tj; t.ti = ti; t.p = p; t.nrows = end - p; t.a0 = a0; t.cs = cs; t.ce = ce;
+    t.last_la = last - a0;
+    t.last_done = (end == rk_after_last) ? 1 : 0;
+    t.shared_mask = (int)shared;
     *ti_out = t;
   }
-  // the last atom of this tile is at or before the first atom of the next one
-  int last = a0;
-#pragma unroll
-  for (int k = 1; k < kMaxAtoms; ++k) last += (__shfl_sync(0xffffffffu, rk, k) <= end - 1) ? 1 : 0;
   wk.hint = last;
   if (sNat != nullptr && lane == 0) *sNat = last - a0 + 1;
 }
@@ -434,13 +443,10 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     const TileInfo ti = sti;
     tc::cp_async_wait_all();  // this thread's row, copied during the previous tile
     if (w == kLocWarp && cur + ti.nrows < c1) locate_window(a, cur + ti.nrows, wk, s_tot, sWin);
-    // the write-out's facts about this tile's atom slots (sRow is rewritten mid-tile)
-    const int last_la = local_atom(sRow, ti.p + ti.nrows - 1);
-    const bool last_done = (ti.p + ti.nrows == sRow[last_la + 1]);
-    unsigned shared_mask = 0u;
-#pragma unroll
-    for (int s = 0; s < kMaxAtoms; ++s)
-      if ((sRow[s] < ti.cs) || (sRow[s + 1] > ti.ce)) shared_mask |= 1u << s;
+    // the write-out's facts about this tile's atom slots (from the lookup)
+    const int last_la = ti.last_la;
+    const bool last_done = ti.last_done != 0;
+    const unsigned shared_mask = (unsigned)ti.shared_mask;
     const int np = ti.ti * a.ntypes + ti.tj;
     if (np != pair) {
       load_fwd_weights<F16>(a.w + (size_t)np * kEmbParams, sB2, sB3, small);

@@ -511,18 +511,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
       const int rg = n & 1;
       wait_acc(rg);
       const uint32_t src = rg ? acc1 : acc0;
-#pragma unroll 1
-      // this thread's 80 columns of its row into the staging tile (fp16)
-      for (int c = half ? 5 : 0; c < (half ? 10 : 5); ++c) {
-        float z[16];
-        tc::tmem_ld16(src + 16 * c, z);
-        tc::tmem_wait_ld();
-        uint32_t p[8];
+      // this thread's 80 columns of its row into the staging tile (fp16): five TMEM loads in
+      // flight, one wait
+      {
+        const int cb = half ? 5 : 0;
+        float z[5][16];
 #pragma unroll
-        for (int h = 0; h < 8; ++h) p[h] = tc::pack2<true>(z[2 * h], z[2 * h + 1]);
-        uint4* d = reinterpret_cast<uint4*>(sm + kStage + row * kStageRow + 32 * c);
-        d[0] = make_uint4(p[0], p[1], p[2], p[3]);
-        d[1] = make_uint4(p[4], p[5], p[6], p[7]);
+        for (int c = 0; c < 5; ++c) tc::tmem_ld16(src + 16 * (cb + c), z[c]);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          uint32_t p[8];
+#pragma unroll
+          for (int h = 0; h < 8; ++h) p[h] = tc::pack2<true>(z[c][2 * h], z[c][2 * h + 1]);
+          uint4* d = reinterpret_cast<uint4*>(sm + kStage + row * kStageRow + 32 * (cb + c));
+          d[0] = make_uint4(p[0], p[1], p[2], p[3]);
+          d[1] = make_uint4(p[4], p[5], p[6], p[7]);
+        }
       }
       __syncthreads();
       // whole row segments (320 B) to dE/dD: warp w writes rows w, w + 8, ...; lanes 0..19
