@@ -210,8 +210,8 @@ N_SMS = 152
 # 32,000-atom copper capture, per real neighbour row; scaled to a launch by the row count.
 # Only valid while the kernel is unchanged since the capture (see profiles/).
 TRAFFIC_PER_ROW = {
-    ("embedding_backward", "mix_fp16"): (171.865088e6 + 4.128000e6) / 5726060,  # profiles/k_mix_embed_bwd_cu32k.md
-    ("embedding_forward", "mix_fp16"): (95.664384e6 + 21.536000e6) / 5726060,  # profiles/k_mix_embed_fwd_cu32k.md
+    ("embedding_backward", "mix_fp16"): (171.772672e6 + 4.658688e6) / 5726060,  # profiles/k_mix_embed_bwd_cu32k.md
+    ("embedding_forward", "mix_fp16"): (95.659008e6 + 21.622016e6) / 5726060,  # profiles/k_mix_embed_fwd_cu32k.md
 }
 
 
