@@ -63,6 +63,7 @@ def lib():
             L.oracle_md.argtypes = [_P, _I, _P, _P, _P, _P, _P, _D, _I, _I, _D, _P, _P, _P]
             L.oracle_md_harmonic.argtypes = [_I, _P, _P, _P, _D, _D, _I, _P]
             L.oracle_model_ntypes.argtypes = [_P]
+            L.oracle_env_stats.argtypes = [_P, _I, _P, _P, _P, _P]
             _lib = L
     return _lib
 
@@ -162,6 +163,15 @@ class Model:
 
     def energy(self, coords, types, box) -> float:
         return self.compute(coords, types, box, forces=False)["energy"]
+
+    def env_stats(self, coords, types, box):
+        """Per centre type t: [slots, sum s, sum s^2, sum of squared angular components,
+        atoms] over every neighbour slot (padded slots are zero rows) of the
+        un-normalised environment rows; shape [ntypes, 5]."""
+        coords, types, box = _f64(coords), _i32(types), _f64(box)
+        out = np.zeros((self.ntypes, 5))
+        _check(lib().oracle_env_stats(self.h, len(types), _ptr(coords), _ptr(types), _ptr(box), _ptr(out)))
+        return out
 
     def dir_deriv(self, coords, types, box, w):
         coords, types, box, w = _f64(coords), _i32(types), _f64(box), _f64(w)

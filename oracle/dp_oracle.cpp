@@ -15,7 +15,9 @@
 //      type;
 //   3. embedding net G = N_{ti,tj}(s_hat): 1->25->50->100, tanh, residual where the
 //      width doubles (concatenate [x, x]) or stays (x)  (Section II-A "embedding net");
-//   4. T = (1/S) R_hat^T G (4 x 100), descriptor D = T^T T[:, :16] (100 x 16);
+//   4. T = (1/S) R_hat^T G (4 x 100) summed over all S neighbour slots, a padded
+//      slot being the row of an absent neighbour (R_tilde = 0, normalised like any
+//      row, i.e. a neighbour at r_c); descriptor D = T^T T[:, :16] (100 x 16);
 //   5. fitting net per centre type 1600->240->240->240->1, tanh, residual on the
 //      equal-width layers (Section II-A "fitting net", sizes Section IV);
 //      E_i = out + e_bias[ti], E = sum_i E_i;
@@ -24,7 +26,9 @@
 //   7. velocity-Verlet NVE (Section II-A: LAMMPS updates velocities and positions),
 //      neighbour rebuild every k steps with a skin (Section IV: skin 2 A).
 // Readings where the paper is silent are listed with the library's design notes:
-// quintic switch, davg = 0 / dstd = 1, constant normaliser S = sum(sel), one
+// quintic switch, davg / dstd read from the weights (0 / 1 for untrained random
+// weights, or the per-type environment statistics of oracle_env_stats), padded
+// slots as zero rows before normalisation, constant normaliser S = sum(sel), one
 // embedding net per (ti, tj), index-ordered neighbour list, overflow is an error.
 //
 // Compile: g++ -O3 -ffp-contract=off -fopenmp -shared -fPIC (no FMA contraction
@@ -491,6 +495,7 @@ void evaluate(const Model<T>& m, int N, const T* x, const int* types, const doub
     std::vector<T> R((size_t)S * 4), dvec((size_t)S * 3), rr(S);
     std::vector<std::vector<T>> h1(S), t2(S), h2(S), t3(S), G(S);
     std::vector<T> Tm((size_t)4 * n3), Dm((size_t)n3 * M2), dD, dT((size_t)4 * n3);
+    std::vector<T> ph1, pt2, ph2, pt3, Gp;  // embedding of a padded slot
 #pragma omp for schedule(dynamic, 4)
     for (int i = 0; i < N; ++i) {
       if (centre_mask && !centre_mask[i]) continue;
@@ -513,12 +518,28 @@ void evaluate(const Model<T>& m, int N, const T* x, const int* types, const doub
         const int tj = types[j];
         emb_forward(&m.theta[m.emb_off[ti * nt + tj]], s, R[(size_t)k * 4], h1[k], t2[k], h2[k], t3[k], G[k]);
       }
-      // T = (1/S) R^T G
+      // T = (1/S) R^T G over all S slots.  A padded slot is the row of an absent
+      // neighbour, R_tilde = 0, normalised like every row: R_hat = -davg/dstd, with
+      // G from the net of (ti, the slot's neighbour type).  It equals the row of a
+      // neighbour sitting exactly at r_c (s = 0), so E stays continuous when a
+      // neighbour crosses the cutoff.  Its G is the same for every padded slot of a
+      // type segment and is computed once per atom and segment.
       for (size_t q = 0; q < Tm.size(); ++q) Tm[q] = T(0.0);
-      for (int k = 0; k < S; ++k) {
-        if (nl.j[(size_t)i * nl.S + k] < 0) continue;
-        for (int c = 0; c < 4; ++c)
-          for (int a = 0; a < n3; ++a) Tm[(size_t)c * n3 + a] += R[(size_t)k * 4 + c] * G[k][a];
+      for (int tj = 0; tj < nt; ++tj) {
+        bool have_pad = false;
+        T Rp[4];
+        for (int c = 0; c < 4; ++c) Rp[c] = (T(0.0) - T(m.davg[ti * 4 + c])) / T(m.dstd[ti * 4 + c]);
+        for (int k = m.sel_off[tj]; k < m.sel_off[tj + 1]; ++k) {
+          const bool pad = nl.j[(size_t)i * nl.S + k] < 0;
+          if (pad && !have_pad) {
+            emb_forward(&m.theta[m.emb_off[ti * nt + tj]], s, Rp[0], ph1, pt2, ph2, pt3, Gp);
+            have_pad = true;
+          }
+          const T* Rk = pad ? Rp : &R[(size_t)k * 4];
+          const std::vector<T>& Gk = pad ? Gp : G[k];
+          for (int c = 0; c < 4; ++c)
+            for (int a = 0; a < n3; ++a) Tm[(size_t)c * n3 + a] += Rk[c] * Gk[a];
+        }
       }
       for (size_t q = 0; q < Tm.size(); ++q) Tm[q] = Tm[q] / T((double)S);
       // D = T^T T[:, :M2], flattened a*M2 + b
@@ -715,6 +736,43 @@ int oracle_compute(const void* h, int N, const double* x, const int* types, cons
   Inter in{interT, interD, interdD};
   evaluate<double>(m, N, xw.data(), types, L, nl, centre_mask, want_force != 0, energy, atom_energy,
                    force, virial, &in);
+  return 0;
+}
+
+// Environment statistics of one configuration, per centre type t (the input
+// normalisation of the smooth descriptor, Section II-A): over every neighbour slot of
+// every atom of type t -- S slots per atom, a padded slot counting as the zero row --
+// of the un-normalised rows (s, s dx/r, s dy/r, s dz/r):
+//   sums[5 t + 0] = number of slots, [1] = sum of s, [2] = sum of s^2,
+//   [3] = sum of (s dx/r)^2 + (s dy/r)^2 + (s dz/r)^2, [4] = number of atoms.
+int oracle_env_stats(const void* h, int N, const double* x, const int* types, const double* box, double* sums) {
+  const Model<double>& m = *static_cast<const Model<double>*>(h);
+  double L[3];
+  if (!box_lengths(box, L)) return 4;
+  std::vector<double> xw;
+  wrap_all(N, x, L, xw);
+  NList nl;
+  nlist_cell(N, xw.data(), types, L, m.rc, m.sel, nl);
+  if (nl.overflow) return 5;
+  for (int q = 0; q < 5 * m.ntypes; ++q) sums[q] = 0.0;
+  for (int i = 0; i < N; ++i) {
+    double* o = sums + 5 * types[i];
+    o[0] += m.S;
+    o[4] += 1.0;
+    for (int k = 0; k < m.S; ++k) {
+      const int j = nl.j[(size_t)i * nl.S + k];
+      if (j < 0) continue;  // the zero row adds nothing to the sums
+      int n[3];
+      unpack_img(nl.img[(size_t)i * nl.S + k], n[0], n[1], n[2]);
+      double d[3];
+      for (int a = 0; a < 3; ++a) d[a] = (xw[3 * j + a] + (double)n[a] * L[a]) - xw[3 * i + a];
+      const double r = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      const double sv = switch_fn(r, m.rs, m.rc, m.switch_kind) / r;
+      o[1] += sv;
+      o[2] += sv * sv;
+      for (int a = 0; a < 3; ++a) o[3] += (sv * d[a] / r) * (sv * d[a] / r);
+    }
+  }
   return 0;
 }
 

@@ -211,9 +211,11 @@ class Weights:
 
 
 def xavier_weights(type_names, rcut: float, rcut_smth: float, sel, seed: int,
-                   switch_kind: int = 0) -> Weights:
+                   switch_kind: int = 0, fit_gain: float = 1.0) -> Weights:
     """Xavier-normal weights W ~ N(0, 2/(fan_in + fan_out)), biases ~ N(0, 1), e_bias = 0,
-    davg = 0, dstd = 1 (random weights come with no training statistics)."""
+    davg = 0, dstd = 1 (random weights come with no training statistics).  fit_gain
+    multiplies the fitting nets' first-layer weights (their standard deviation) after
+    the draw; the draw itself does not depend on it."""
     nt = len(type_names)
     rng = np.random.default_rng(seed)
     layout, total = theta_layout(nt)
@@ -228,6 +230,8 @@ def xavier_weights(type_names, rcut: float, rcut_smth: float, sel, seed: int,
             vals = rng.normal(0.0, math.sqrt(2.0 / (fan_in + fan_out)), size=n)
         else:
             vals = rng.normal(0.0, 1.0, size=n)
+        if leaf == "W1" and name.startswith("fit"):
+            vals = vals * fit_gain
         theta[off:off + n] = vals
     davg = np.zeros((nt, 4))
     dstd = np.ones((nt, 4))
@@ -241,6 +245,35 @@ def water_weights(seed: int = 1001) -> Weights:
 
 def copper_weights(seed: int = 1001) -> Weights:
     return xavier_weights(("Cu",), 8.0, 2.0, (512,), seed)
+
+
+def with_statistics(w: Weights, davg, dstd) -> Weights:
+    """A copy of w whose input normalisation is (davg, dstd), each [ntypes][4]."""
+    davg = np.array(davg, dtype=np.float64).reshape(w.ntypes, 4)
+    dstd = np.array(dstd, dtype=np.float64).reshape(w.ntypes, 4)
+    return Weights(w.ntypes, w.type_names, w.rcut, w.rcut_smth, w.sel, w.theta.copy(), davg, dstd,
+                   w.switch_kind)
+
+
+# Gain on the fitting nets' first layer of the normalised test models: with the
+# environment statistics in place it brings the forces of the water model to the scale
+# of a trained one (about 0.6 eV/A rms at 300 K) with the first-layer tanh unsaturated.
+NORMALISED_FIT_GAIN = 10.0
+
+
+def normalised_weights(kind: str, stats: dict, seed: int = 1001) -> Weights:
+    """The water ("water") or copper ("copper") model with its per-type environment
+    statistics stats[kind]["davg"], stats[kind]["dstd"] (as written by the oracle script
+    tests/golden/make_env_stats.py) and NORMALISED_FIT_GAIN on the fitting input layer."""
+    if kind == "water":
+        w = xavier_weights(("O", "H"), 6.0, 0.5, (46, 92), seed, fit_gain=NORMALISED_FIT_GAIN)
+    elif kind == "copper":
+        w = xavier_weights(("Cu",), 8.0, 2.0, (512,), seed, fit_gain=NORMALISED_FIT_GAIN)
+    else:
+        raise KeyError(kind)
+    if tuple(stats[kind]["type_names"]) != w.type_names:
+        raise ValueError("statistics are for other types")
+    return with_statistics(w, stats[kind]["davg"], stats[kind]["dstd"])
 
 
 def maxwell_boltzmann(masses_per_atom: np.ndarray, temperature: float, seed: int) -> np.ndarray:

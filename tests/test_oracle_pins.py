@@ -294,9 +294,24 @@ def _sparse_weights(switch_kind=0, davg=None, dstd=None):
     return w
 
 
+def _sparse_G(w, ti, tj, x):
+    """Embedding output G of pair (ti, tj) for input x with the sparse weights above,
+    written out scalar by scalar."""
+    p = f"emb{ti}{tj}."
+    W1, b1, b2, b3 = (w.block(p + k) for k in ("W1", "b1", "b2", "b3"))
+    h1 = np.tanh(x * W1[0] + b1)
+    h2 = np.concatenate([h1, h1]) + np.tanh(b2)
+    h2[7] = h1[7] + math.tanh(h1[3] * w.block(p + "W2")[3, 7] + b2[7])
+    G = np.concatenate([h2, h2]) + np.tanh(b3)
+    G[60] = h2[10] + math.tanh(h2[5] * w.block(p + "W3")[5, 60] + b3[60])
+    return G
+
+
 def _closed_form_dimer(w, r, u, ti, tj):
     """E_i of atom i (type ti) whose only neighbour (type tj) sits at r*u, with the
-    sparse weights above, written out scalar by scalar."""
+    sparse weights above, written out scalar by scalar.  Every one of the S = 46 + 92
+    slots enters T: the neighbour's row (when r < r_c) and the padded slots, whose
+    un-normalised row is zero, so R_hat = -davg/dstd with G of that input."""
     rs, rc = w.rcut_smth, w.rcut
     if r < rs:
         sw = 1.0
@@ -307,17 +322,18 @@ def _closed_form_dimer(w, r, u, ti, tj):
         sw = x ** 3 * (-6 * x * x + 15 * x - 10) + 1 if w.switch_kind == 0 else 0.5 * math.cos(math.pi * x) + 0.5
     s = sw / r
     Rt = np.array([s, s * u[0], s * u[1], s * u[2]])
-    Rh = (Rt - w.davg[ti]) / w.dstd[ti] if sw > 0 else np.zeros(4)
-    p = f"emb{ti}{tj}."
-    W1, b1, b2, b3 = (w.block(p + k) for k in ("W1", "b1", "b2", "b3"))
-    h1 = np.tanh(Rh[0] * W1[0] + b1)
-    h2 = np.concatenate([h1, h1]) + np.tanh(b2)
-    h2[7] = h1[7] + math.tanh(h1[3] * w.block(p + "W2")[3, 7] + b2[7])
-    G = np.concatenate([h2, h2]) + np.tanh(b3)
-    G[60] = h2[10] + math.tanh(h2[5] * w.block(p + "W3")[5, 60] + b3[60])
+    Rh = (Rt - w.davg[ti]) / w.dstd[ti]
+    Rp = (0.0 - w.davg[ti]) / w.dstd[ti]
     S = 138.0
-    q = float(Rh @ Rh) / (S * S)  # sum_c T[c][a] T[c][b] = q G[a] G[b]
-    D = lambda a, b: q * G[a] * G[b]  # noqa: E731
+    npad = [46, 92]
+    T = np.zeros((4, 100))
+    if r < rc:
+        T += np.outer(Rh, _sparse_G(w, ti, tj, Rh[0]))
+        npad[tj] -= 1
+    for t in (0, 1):
+        T += npad[t] * np.outer(Rp, _sparse_G(w, ti, t, Rp[0]))
+    T /= S
+    D = lambda a, b: float(T[:, a] @ T[:, b])  # noqa: E731
     f = f"fit{ti}."
     W1f, b1f, b2f, b3f, w4, b4 = (w.block(f + k) for k in ("W1", "b1", "b2", "b3", "w4", "b4"))
     h1f = np.tanh(b1f)
@@ -361,6 +377,122 @@ def test_dimer_closed_form_with_normalisation():
         res = m.compute(x, np.array([0, 1], np.int32), box)
         assert res["atom_energy"][0] == pytest.approx(_closed_form_dimer(w, r, u, 0, 1), rel=1e-13)
         assert res["atom_energy"][1] == pytest.approx(_closed_form_dimer(w, r, -u, 1, 0), rel=1e-13)
+
+
+def test_dimer_closed_form_normalised_across_cutoff():
+    # With davg != 0 the padded slots carry R_hat = -davg/dstd; the dimer's energy follows the
+    # closed form on both sides of r_c, including r > r_c where every slot is padded.
+    davg = np.array([[0.08, 0.01, -0.02, 0.03], [0.12, 0.0, 0.0, 0.0]])
+    dstd = np.array([[0.15, 0.09, 0.08, 0.1], [0.13, 0.07, 0.06, 0.08]])
+    w = _sparse_weights(0, davg, dstd)
+    m = oracle.Model(w.to_blob())
+    box = np.diag([50.0] * 3).ravel()
+    u = np.array([-0.4, 0.2, 0.7]); u /= np.linalg.norm(u)
+    for r in (0.4, 2.5, 5.5, 6.5):
+        x = np.array([[10.0, 11.0, 12.0], [10.0, 11.0, 12.0] + r * u])
+        res = m.compute(x, np.array([0, 1], np.int32), box)
+        assert res["atom_energy"][0] == pytest.approx(_closed_form_dimer(w, r, u, 0, 1), rel=1e-13)
+        assert res["atom_energy"][1] == pytest.approx(_closed_form_dimer(w, r, -u, 1, 0), rel=1e-13)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_normalised_energy_continuous_at_cutoff(kind):
+    # A padded slot is the row of a neighbour at r_c, so E and dE/dr are continuous as a
+    # neighbour leaves the cutoff.  A zero padded row (after normalisation) would make E
+    # jump there by (1/S) R_hat_pad^T G(R_hat_pad) through the fitting net.
+    w = synth.with_statistics(synth.xavier_weights(("O", "H"), 6.0, 0.5, (46, 92), 1001, switch_kind=kind,
+                                                   fit_gain=10.0),
+                              [[0.05, 0.0, 0.0, 0.0], [0.05, 0.0, 0.0, 0.0]],
+                              [[0.14, 0.09, 0.09, 0.09], [0.13, 0.08, 0.08, 0.08]])
+    m = oracle.Model(w.to_blob())
+    box = np.diag([60.0] * 3).ravel()
+    t = np.array([0, 1], np.int32)
+    e = {}
+    for side in (-1, 1):
+        x = np.array([[20.0, 20.0, 20.0], [20.0 + 6.0 + side * 1e-7, 20.0, 20.0]])
+        e[side] = m.compute(x, t, box)
+    assert e[-1]["energy"] == pytest.approx(e[1]["energy"], abs=1e-9)
+    assert abs(e[-1]["forces"][1, 0]) < 1e-6 and e[1]["forces"][1, 0] == 0.0
+    # and the padded rows do change E: the isolated-atom energy differs from davg = 0
+    w0 = synth.with_statistics(w, np.zeros((2, 4)), w.dstd)
+    e0 = oracle.Model(w0.to_blob()).compute(np.array([[20.0, 20, 20], [40.0, 40, 40]]), t, box)["energy"]
+    e1 = m.compute(np.array([[20.0, 20, 20], [40.0, 40, 40]]), t, box)["energy"]
+    assert abs(e1 - e0) > 1e-3
+
+
+def test_env_stats_closed_form():
+    # An O-H pair inside r_s (sw = 1, s = 1/r) and one at r_s < r < r_c with the quintic
+    # switch, far from each other, plus an isolated H, in a 60 A box.
+    w = synth.water_weights()
+    m = oracle.Model(w.to_blob())
+    box = np.diag([60.0] * 3).ravel()
+    r1, r2 = 0.45, 3.1
+    u = np.array([1.0, 2.0, -2.0]) / 3.0
+    x = np.array([[5.0, 5, 5], [5.0, 5, 5] + r1 * u, [30.0, 30, 30], [30.0, 30, 30] + r2 * u, [50.0, 10, 50]])
+    t = np.array([0, 1, 0, 1, 1], np.int32)
+    out = m.env_stats(x, t, box)
+    xq = (r2 - 0.5) / 5.5
+    s2 = (xq ** 3 * (-6 * xq * xq + 15 * xq - 10) + 1) / r2
+    s1 = 1.0 / r1
+    for ti, nat in ((0, 2), (1, 3)):
+        assert out[ti, 0] == 138 * nat and out[ti, 4] == nat
+        assert out[ti, 1] == pytest.approx(s1 + s2, rel=1e-14)
+        assert out[ti, 2] == pytest.approx(s1 * s1 + s2 * s2, rel=1e-14)
+        assert out[ti, 3] == pytest.approx(s1 * s1 + s2 * s2, rel=1e-13)  # |u| = 1
+
+
+def _normalised_water():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "env_stats.json")) as f:
+        return synth.normalised_weights("water", json.load(f))
+
+
+def test_normalised_model_forces_match_central_differences():
+    w = _normalised_water()
+    m = oracle.Model(w.to_blob())
+    s = synth.water_box(16, 4)
+    r = m.compute(s.coords, s.types, s.box)
+    assert np.sqrt((r["forces"] ** 2).mean()) > 0.1  # a force scale like a trained model's
+    rng = np.random.default_rng(3)
+    h = 1e-5
+    for i in rng.choice(s.natoms, 6, replace=False):
+        for a in range(3):
+            xp = s.coords.copy(); xp[i, a] += h
+            xm = s.coords.copy(); xm[i, a] -= h
+            fd = -(m.energy(xp, s.types, s.box) - m.energy(xm, s.types, s.box)) / (2 * h)
+            assert fd == pytest.approx(r["forces"][i, a], rel=1e-6, abs=1e-8)
+    # virial against the strain derivative
+    eps = 1e-6
+    def E_strain(e):
+        return m.energy(s.coords * (1 + e), s.types, s.box * (1 + e))
+    dE = (E_strain(eps) - E_strain(-eps)) / (2 * eps)
+    assert -dE == pytest.approx(np.trace(r["virial"]), rel=1e-6)
+
+
+def test_normalised_param_grad_dual_matches_finite_differences():
+    # The padded slots' G depends on the embedding parameters: the dual-number gradient
+    # must carry that term as the finite differences do.
+    w = _normalised_water()
+    s = synth.water_box(8, 12)
+    m = oracle.Model(w.to_blob())
+    E0, F0 = 0.9 * m.energy(s.coords, s.types, s.box), np.zeros((s.natoms, 3))
+    layout, _ = synth.theta_layout(2)
+    off = {name: o for name, _, o in layout}
+    idx = [off["emb01.b1"] + 3, off["emb10.W3"] + 17, off["emb11.b3"] + 42, off["emb00.W1"] + 5,
+           off["fit0.W1"] + 1234]
+    g, dE, loss = m.param_grad(s.coords, s.types, s.box, E0, F0, idx)
+    h = 1e-4
+
+    def L_at(p, e):
+        th = w.theta.copy(); th[p] += e
+        w2 = synth.Weights(w.ntypes, w.type_names, w.rcut, w.rcut_smth, w.sel, th, w.davg, w.dstd)
+        r = oracle.Model(w2.to_blob()).compute(s.coords, s.types, s.box)
+        return (r["energy"] - E0) ** 2 + ((r["forces"] - F0) ** 2).sum()
+
+    for p, gp in zip(idx, g):
+        fd = (8 * (L_at(p, h) - L_at(p, -h)) - (L_at(p, 2 * h) - L_at(p, -2 * h))) / (12 * h)
+        assert fd == pytest.approx(gp, rel=1e-5, abs=1e-8), p
 
 
 def test_isolated_atom_energy_is_fit_of_zero():
