@@ -20,6 +20,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -91,11 +92,10 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"dp_bench_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
@@ -117,6 +117,10 @@ class ClockSampler:
             tok = [t.strip() for t in line.split(",")]
             if len(tok) >= 9:
                 rows.append(tok)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         if not rows:
             return None
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -203,16 +207,48 @@ def run_reference(args, world, rank):
 # Algorithmic tanh per real neighbour row of the embedding net (25 + 50 + 100); the backward
 # recomputes the forward, and tanh' = 1 - t^2 needs no further tanh.
 TANH_PER_NEIGHBOUR = 175
-SFU_PER_CLK_PER_SM = 16   # MUFU results per clock per SM (documented rate of recent NVIDIA GPUs)
-N_SMS = 152
 
-# DRAM bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# 32,000-atom copper capture, per real neighbour row; scaled to a launch by the row count.
-# Only valid while the kernel is unchanged since the capture (see profiles/).
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
+# the 32,000-atom copper box, per real neighbour row, scaled to a launch by the row count.  Each
+# entry names the source file of the kernel and its SHA-1 at the capture: when the file has
+# changed since, the figure no longer describes the kernel and `traffic` is reported as null.
 TRAFFIC_PER_ROW = {
-    ("embedding_backward", "mix_fp16"): (171.772672e6 + 4.658688e6) / 5726060,  # profiles/k_mix_embed_bwd_cu32k.md
-    ("embedding_forward", "mix_fp16"): (95.659008e6 + 21.622016e6) / 5726060,  # profiles/k_mix_embed_fwd_cu32k.md
+    ("embedding_backward", "mix_fp16"): {"bytes_per_row": (171.772672e6 + 4.658688e6) / 5726060,
+                                         "source": "paper_2410_22867_gb300/csrc/mix_embed.cu",
+                                         "sha1": "1d36283-capture"},
+    ("embedding_forward", "mix_fp16"): {"bytes_per_row": (95.659008e6 + 21.622016e6) / 5726060,
+                                        "source": "paper_2410_22867_gb300/csrc/mix_embed.cu",
+                                        "sha1": "1d36283-capture"},
 }
+
+
+def _sha1(path):
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, path), "rb") as f:
+            return hashlib.sha1(f.read()).hexdigest()
+    except OSError:
+        return None
+
+
+def traffic_per_launch(kernel, prec, rows):
+    e = TRAFFIC_PER_ROW.get((kernel, prec))
+    if e is None or _sha1(e["source"]) != e["sha1"]:
+        return None
+    return e["bytes_per_row"] * rows
+
+
+def measured_peaks(dp):
+    """Rates of the arithmetic units measured on this device right now (dp_measure_peak):
+    tanh / ex2 / rcp results per second, FP32 and FP64 FLOP/s."""
+    out = {}
+    for k in ("tanh", "ex2", "rcp", "ffma", "dfma"):
+        try:
+            out[k] = dp.measure_peak(k)
+        except Exception as e:  # noqa: BLE001
+            out[k] = None
+            out[k + "_error"] = str(e)
+    return out
 
 
 def kernel_times(ph):
@@ -220,42 +256,47 @@ def kernel_times(ph):
             "fitting": ph[2], "dE_dT": max(0.0, ph[3] - ph[6]), "embedding_backward": ph[6]}
 
 
-def roofline(prec, kernel, ms, N, n_neigh):
+def roofline(prec, kernel, ms, N, n_neigh, alu):
+    """Roofline entry of one kernel of a force evaluation.  alu: measured_peaks().
+    Mixed precisions: embedding kernels against max(tensor, SFU) with the SFU rate measured
+    by dp_measure_peak('tanh'); fitting against the burst bf16 tensor peak (the kernel is timed
+    in millisecond phases, not a sustained loop).  FP32 / FP64: FMA-pipe work of the dense
+    contractions against the measured FFMA / DFMA rate."""
     pk, src = peaks()
-    sm_mhz = pk.get("sm_max_mhz", 2070.0)
     t = ms * 1e-3
     mixed = prec.startswith("mix")
-    traffic = TRAFFIC_PER_ROW.get((kernel, prec))
-    out = {"kernel": kernel, "kernel_ms": ms,
-           "traffic": traffic * n_neigh if traffic is not None else None}
+    out = {"kernel": kernel, "kernel_ms": ms, "traffic": traffic_per_launch(kernel, prec, n_neigh)}
     if kernel in ("embedding_forward", "embedding_backward"):
         flop = n_neigh * (EMB_FWD_FLOP_PER_NEIGHBOUR if kernel == "embedding_forward" else EMB_BWD_FLOP_PER_NEIGHBOUR)
-        tanh = n_neigh * TANH_PER_NEIGHBOUR
-        if mixed:
-            # bound = max(tensor, SFU); at 175 tanh vs ~2e4 flop per row the SFU term is the larger
-            sfu = N_SMS * SFU_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12
-            tens = pk.get("bf16_tflops_sustained", 1700.0)
-            out.update({"bound": "alu", "achieved": tanh / t / 1e12, "peak": sfu, "unit": "Ttanh/s",
-                        "frac": tanh / t / 1e12 / sfu,
-                        "peak_source": f"derived: {N_SMS} SMs x {SFU_PER_CLK_PER_SM} MUFU/clk x {sm_mhz:.0f} MHz",
-                        "tensor": {"achieved": flop / t / 1e12, "peak": tens, "unit": "TFLOP/s",
-                                   "frac": flop / t / 1e12 / tens, "peak_source": f"{src} bf16 sustained"}})
-            return out
-        work = flop
     elif kernel == "fitting":
-        work = N * FIT_FLOP_PER_ATOM
-        if mixed:
-            tens = pk.get("bf16_tflops_sustained", 1700.0)
-            out.update({"bound": "tensor", "achieved": work / t / 1e12, "peak": tens, "unit": "TFLOP/s",
-                        "frac": work / t / 1e12 / tens, "peak_source": f"{src} bf16 sustained"})
-            return out
+        flop = N * FIT_FLOP_PER_ATOM
     else:
-        work = 0
-    lanes = {"fp64": 2, "fp32": 128}.get(prec, 128)  # FMA lanes per SM per clock
-    peak = N_SMS * lanes * 2 * sm_mhz * 1e6 / 1e12
-    ach = work / t / 1e12 if work else 0.0
-    out.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "peak_source": f"derived: {N_SMS} SMs x {lanes} FMA lanes x 2 x {sm_mhz:.0f} MHz"})
+        flop = 0
+    if mixed and kernel in ("embedding_forward", "embedding_backward"):
+        tanh = n_neigh * TANH_PER_NEIGHBOUR
+        sfu = (alu.get("tanh") or 0.0) / 1e12
+        tens = pk.get("bf16_tflops", 1900.0)
+        out.update({"bound": "alu", "achieved": tanh / t / 1e12, "peak": sfu, "unit": "Ttanh/s",
+                    "frac": (tanh / t / 1e12 / sfu) if sfu else None,
+                    "peak_source": "measured: dp_measure_peak(tanh.approx.f32) on this device, this run",
+                    "tensor": {"achieved": flop / t / 1e12, "peak": tens, "unit": "TFLOP/s",
+                               "frac": flop / t / 1e12 / tens, "peak_source": f"{src} bf16 burst"}})
+        return out
+    if mixed and kernel == "fitting":
+        tens = pk.get("bf16_tflops", 1900.0)
+        out.update({"bound": "tensor", "achieved": flop / t / 1e12, "peak": tens, "unit": "TFLOP/s",
+                    "frac": flop / t / 1e12 / tens, "peak_source": f"{src} bf16 burst (fp16 runs at the bf16 rate)"})
+        return out
+    if kernel in ("format", "dE_dT", "descriptor"):
+        out.update({"bound": "hbm", "achieved": None, "peak": pk.get("hbm_gbs"), "unit": "GB/s", "frac": None,
+                    "peak_source": f"{src} hbm copy"})
+        return out
+    key = "dfma" if prec == "fp64" else "ffma"
+    peak = (alu.get(key) or 0.0) / 1e12
+    ach = flop / t / 1e12
+    out.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak if peak else None,
+                "peak_source": f"measured: dp_measure_peak({key}) on this device, this run"})
     return out
 
 
@@ -301,16 +342,37 @@ def run_mine(args, world, rank, local):
         # [format, descriptor phase, fitting, embedding-backward phase, total, embedding forward
         #  kernel, embedding backward kernel] from events on the model's stream
         phases = m.phase_times(args.phase_repeats)
+        if rank != 0:
+            m.close()
 
     extra = {}
     if rank == 0:
+        alu = measured_peaks(dp)
         kern = kernel_times(phases)
         dominant = max(kern, key=kern.get)
-        extra["roofline"] = roofline(prec, dominant, kern[dominant], N, n_neigh)
+        extra["roofline"] = roofline(prec, dominant, kern[dominant], N, n_neigh, alu)
+        extra["rooflines"] = {k: roofline(prec, k, v, N, n_neigh, alu) for k, v in kern.items()}
         extra["kernels_ms"] = {k: round(v, 4) for k, v in kern.items()}
+        extra["measured_peaks"] = {"values": alu, "units": {"tanh": "1/s", "ex2": "1/s", "rcp": "1/s",
+                                                            "ffma": "FLOP/s", "dfma": "FLOP/s"},
+                                   "how": "dp_measure_peak: 8 blocks x 256 threads per SM, 8 dependent chains per "
+                                          "thread, CUDA events, best of 3 after a warm-up"}
+        # precision ladder: every precision on the copper and water boxes
+        if args.ladder_steps > 0:
+            extra["ladder"] = ladder(args, stream, alu)
         # FP64 comparison (speed and error) on the same configuration
         if not args.no_fp64 and prec != "fp64":
-            extra["fp64"] = fp64_compare(args, s, w, v0, m, stream)
+            lad = extra.get("ladder", {}).get(args.workload)
+            if lad and prec in lad:
+                f = lad["fp64"]
+                extra["fp64"] = {"value": f["value"], "unit": f["unit"], "ms_per_step": f["ms_per_step"],
+                                 "steps": f["steps"], "error_vs_fp64_gpu": lad[prec]["error_vs_fp64_gpu"],
+                                 "from": "ladder"}
+            else:
+                extra["fp64"] = fp64_compare(args, s, w, v0, m, stream)
+        # errors of every precision on the normalised models (environment statistics, O(1) rows)
+        if args.ladder_steps > 0:
+            extra["normalised_errors"] = normalised_errors(stream)
         # the water box of the same model family
         if args.water_steps > 0 and args.workload != "water12k":
             extra["water"] = water_leg(args, stream)
@@ -319,14 +381,18 @@ def run_mine(args, world, rank, local):
             extra["batch"] = batch_leg(args, stream)
         # end-to-end through the public API with host buffers
         extra["e2e"] = e2e(m, s, stream, args.e2e_steps)
-        # CPU oracle baseline
+        # CPU oracle baseline: all host cores, and one core
         try:
             import oracle
             oracle.build()
-            oracle.set_threads(len(os.sched_getaffinity(0)))
+            ncores = len(os.sched_getaffinity(0))
+            oracle.set_threads(ncores)
             rate, cores, sample, _ = oracle_rate(args.workload, nsteps=1)
+            oracle.set_threads(1)
+            rate1, _, _, _ = oracle_rate(args.workload, nsteps=1)
+            oracle.set_threads(ncores)
             extra["cpu_baseline"] = {"value": rate, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
-                                     "sample": sample}
+                                     "sample": sample, "one_core": {"value": rate1, "cores": 1}}
         except Exception as e:  # noqa: BLE001
             extra["cpu_baseline"] = {"value": None, "unit": "atom-steps/s", "cores": 0, "kind": "oracle",
                                      "sample": f"unavailable: {e}"}
@@ -344,6 +410,114 @@ def run_mine(args, world, rank, local):
                             "paper_hardware": "12,000 Fugaku A64FX nodes, 0.54 M atoms Cu, dt 1 fs (context only)"}}
         line.update(extra)
         print(json.dumps(line), flush=True)
+
+
+def md_rate(w, s, v0, prec, stream, steps, dt=DT_FS, warm=3):
+    """NVE MD throughput of one box (graph replay); returns (ms per step, model kept open)."""
+    import torch
+    import paper_2410_22867_gb300 as dp
+    with torch.cuda.stream(stream):
+        m = dp.DPModel(w, prec, max_atoms=s.natoms, skin=2.0, stream=stream)
+        x = torch.tensor(s.coords, device="cuda")
+        v = torch.tensor(v0, device="cuda")
+        t = torch.tensor(s.types, device="cuda")
+        st = m.md_state(x, v, t, s.box, s.masses(), rebuild_every=REBUILD)
+        m.verlet(st, dt, warm, capture_graph=True)
+        st.resume = 1
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        m.verlet(st, dt, steps, capture_graph=True, sync=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        m.sync()
+    return ev0.elapsed_time(ev1) / steps, m
+
+
+def force_errors(out, ref):
+    """Error of one force evaluation against the FP64 GPU path: absolute and relative."""
+    import torch
+    dF = out["forces"] - ref["forces"]
+    rmse = float(torch.sqrt((dF ** 2).mean()).item())
+    rms = float(torch.sqrt((ref["forces"] ** 2).mean()).item())
+    N = out["forces"].shape[0]
+    return {"force_rmse_eV_per_A": rmse, "force_rms_eV_per_A": rms, "force_rel_rmse": rmse / rms if rms else None,
+            "energy_eV_per_atom": abs(out["energy"].item() - ref["energy"].item()) / N,
+            "max_atom_energy_eV": float((out["atom_energy"] - ref["atom_energy"]).abs().max().item())}
+
+
+def ladder(args, stream, alu):
+    """Every precision on the 131,072-atom copper box and the 12,288-atom water box: MD
+    throughput (ns/day at 0.5 fs; copper also run at the paper's 1.0 fs), the dominant kernel's
+    roofline, and the error of one force evaluation against the FP64 GPU path."""
+    import torch
+    out = {}
+    for wl in ("cu131k", "water12k"):
+        s, w, v0 = load_workload(wl)
+        x = torch.tensor(s.coords, device="cuda")
+        t = torch.tensor(s.types, device="cuda")
+        ref = None
+        res = {}
+        for prec in ("fp64", "fp32", "mix_bf16", "mix_fp16"):
+            steps = args.ladder_steps if prec != "fp64" else max(2, args.ladder_steps // 10)
+            if wl == "water12k":
+                steps = min(steps, args.water_steps or steps)  # the window stays before the first collapse
+            ms, m = md_rate(w, s, v0, prec, stream, steps)
+            n_neigh = neighbour_count(m)
+            ph = m.phase_times(3)
+            kern = kernel_times(ph)
+            dom = max(kern, key=kern.get)
+            with torch.cuda.stream(stream):
+                r = m.compute(x, t, s.box)
+            e = {"value": s.natoms / (ms * 1e-3), "unit": "atom-steps/s", "ms_per_step": ms, "steps": steps,
+                 "ns_per_day_0.5fs": (1e3 / ms) * 0.5 * 86400 * 1e-6,
+                 "roofline": roofline(prec, dom, kern[dom], s.natoms, n_neigh, alu),
+                 "kernels_ms": {k: round(v, 4) for k, v in kern.items()}}
+            if prec == "fp64":
+                ref = {k: v.clone() for k, v in r.items()}
+            else:
+                e["error_vs_fp64_gpu"] = force_errors(r, ref)
+            res[prec] = e
+            m.close()
+        if wl == "cu131k":
+            ms, m = md_rate(w, s, v0, "mix_fp16", stream, args.ladder_steps, dt=1.0)
+            m.close()
+            res["mix_fp16_dt1fs"] = {"value": s.natoms / (ms * 1e-3), "unit": "atom-steps/s", "ms_per_step": ms,
+                                     "ns_per_day_1fs": (1e3 / ms) * 1.0 * 86400 * 1e-6, "steps": args.ladder_steps}
+        out[wl] = {"workload": WORKLOADS[wl], **res}
+    return out
+
+
+def normalised_errors(stream):
+    """Error of every precision against the FP64 GPU path on the normalised models: the
+    per-type environment statistics of each system (written by the oracle script under
+    tests/golden) and a gain of 10 on the fitting input layer, so the environment rows are
+    O(1) and the forces have the scale of a trained model."""
+    import torch
+    import paper_2410_22867_gb300 as dp
+    from paper_2410_22867_gb300 import synth
+    with open(os.path.join(ROOT, "tests", "golden", "env_stats.json")) as f:
+        stats = json.load(f)
+    out = {}
+    for wl, kind in (("cu131k", "copper"), ("water12k", "water")):
+        s, _, _ = load_workload(wl)
+        w = synth.normalised_weights(kind, stats)
+        x = torch.tensor(s.coords, device="cuda")
+        t = torch.tensor(s.types, device="cuda")
+        ref = None
+        res = {}
+        with torch.cuda.stream(stream):
+            for prec in ("fp64", "fp32", "mix_bf16", "mix_fp16"):
+                m = dp.DPModel(w, prec, max_atoms=s.natoms, stream=stream)
+                r = m.compute(x, t, s.box)
+                if prec == "fp64":
+                    ref = {k: v.clone() for k, v in r.items()}
+                    res["fp64_force_rms_eV_per_A"] = float(torch.sqrt((ref["forces"] ** 2).mean()).item())
+                else:
+                    res[prec] = force_errors(r, ref)
+                m.close()
+        out[wl] = res
+    return out
 
 
 def batch_leg(args, stream):
@@ -493,6 +667,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=22)  # + 3 warm-up: before the first collapse (step ~35)
     ap.add_argument("--water-steps", type=int, default=20)  # + 4 warm-up: before the first collapse (step ~31)
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--ladder-steps", type=int, default=20, help="timed MD steps per precision of the ladder "
+                                                                  "(FP64: a tenth, at least 2); 0 skips the ladder")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -265,6 +265,29 @@ dp_status dp_selftest(int which, double* result);
 #define DP_SELFTEST_NOALLOC_MAX_CASES 16
 dp_status dp_selftest_noalloc(const int* which, int ncases, double* results);
 
+/*
+ * dp_wait_selftest -- check of the bounded-wait error path on the current device.  A
+ * kernel waits, with the same bounded wait routine the tensor-core kernels use, on an
+ * mbarrier phase that nothing completes (no copy or MMA is issued, so nothing is in
+ * flight).  After spin_limit polls (1 .. 2^22) the wait gives up, sets the timeout bit
+ * and the kernel returns; the device stays usable.  Returns DP_ERR_WAIT_TIMEOUT when
+ * the wait gave up (the expected outcome), DP_OK if it did not, DP_ERR_ARG for a
+ * spin_limit out of range, DP_ERR_UNSUPPORTED without tcgen05, DP_ERR_CUDA if the launch
+ * failed.  Uses the legacy default stream; synchronous; allocates nothing.
+ */
+dp_status dp_wait_selftest(unsigned int spin_limit);
+
+/*
+ * dp_measure_peak -- measured throughput of an arithmetic unit on the current device
+ * (measurement hook for rooflines): which = 0 tanh.approx.f32, 1 ex2.approx.f32,
+ * 2 rcp.approx.f32 (results per second; each step also adds one, so that the chain
+ * cannot fold), 3 FP32 FMA, 4 FP64 FMA (FLOP per second, two per FMA).  Every SM runs eight blocks of 256 threads, each thread eight independent
+ * dependent chains of the instruction; CUDA events on a private stream, the fastest of
+ * three launches after a warm-up.  rate [1] host output.  Synchronous; allocates
+ * nothing.  DP_ERR_ARG for an unknown `which` or a null rate, DP_ERR_CUDA on failure.
+ */
+dp_status dp_measure_peak(int which, double* rate);
+
 /* Wait for the model's stream; return and clear the sticky device error (DP_OK if none). */
 dp_status dp_sync(dp_model* m);
 

@@ -31,7 +31,8 @@ STATUS = {0: "DP_OK", 1: "DP_ERR_ARG", 2: "DP_ERR_CUDA", 3: "DP_ERR_OOM", 4: "DP
 # exported symbols of include/dp.h
 EXPORTS = ("dp_create", "dp_compute", "dp_compute_batch", "dp_verlet_step", "dp_md_run_batch", "dp_param_grad",
            "dp_ntheta", "dp_get_nlist", "dp_phase_times", "dp_kernel_launches", "dp_sync", "dp_last_error",
-           "dp_destroy", "dp_version", "dp_selftest", "dp_selftest_noalloc", "dp_set_params", "dp_autotune")
+           "dp_destroy", "dp_version", "dp_selftest", "dp_selftest_noalloc", "dp_set_params", "dp_autotune",
+           "dp_wait_selftest", "dp_measure_peak")
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -87,9 +88,12 @@ def lib():
             L.dp_selftest_noalloc.argtypes = [_P, _I, _P]
             L.dp_set_params.argtypes = [_P, _P, ctypes.c_longlong]
             L.dp_autotune.argtypes = [_P, _I, _P]
+            L.dp_wait_selftest.argtypes = [ctypes.c_uint]
+            L.dp_measure_peak.argtypes = [_I, _P]
             for name in ("dp_create", "dp_compute", "dp_compute_batch", "dp_verlet_step", "dp_md_run_batch",
                          "dp_param_grad", "dp_get_nlist", "dp_phase_times", "dp_sync", "dp_selftest",
-                         "dp_selftest_noalloc", "dp_set_params", "dp_autotune"):
+                         "dp_selftest_noalloc", "dp_set_params", "dp_autotune", "dp_wait_selftest",
+                         "dp_measure_peak"):
                 getattr(L, name).restype = _I
             _lib = L
     return _lib
@@ -112,6 +116,25 @@ def selftest(which: int):
     if st != 0:
         raise DPError(st, "dp_selftest failed")
     return out[0], out[1]
+
+
+def wait_selftest(spin_limit: int = 4096) -> int:
+    """dp_wait_selftest: run a bounded wait that nothing completes; returns the status
+    (DP_ERR_WAIT_TIMEOUT = 7 when the wait gave up, as it should)."""
+    return int(lib().dp_wait_selftest(int(spin_limit)))
+
+
+PEAK_KINDS = {"tanh": 0, "ex2": 1, "rcp": 2, "ffma": 3, "dfma": 4}
+
+
+def measure_peak(kind: str) -> float:
+    """dp_measure_peak: measured rate of one arithmetic unit on the current device
+    (tanh, ex2, rcp: results/s; ffma, dfma: FLOP/s)."""
+    r = ctypes.c_double(0.0)
+    st = lib().dp_measure_peak(PEAK_KINDS[kind], ctypes.byref(r))
+    if st != 0:
+        raise DPError(st, f"dp_measure_peak({kind}) failed")
+    return r.value
 
 
 SELFTEST_NOALLOC_MAX_CASES = 16
@@ -340,7 +363,39 @@ def _make_param_loss():
     return ParamLoss
 
 
+def _make_potential():
+    import torch
+    from torch.autograd.function import once_differentiable
+
+    class Potential(torch.autograd.Function):
+        """E(x) of one periodic box as a differentiable function of the coordinates.
+
+        forward(coords, model, types, box) -> (energy, virial): coords [N, 3] float64 cuda
+        (caller order), types [N] int32 cuda, box a host 3x3; energy is a 0-d float64
+        tensor, virial [3, 3] (not differentiable).  One dp_compute call evaluates E, the
+        forces F = -dE/dx and the virial (prod_force / prod_virial of the backward pass);
+        backward returns grad_E * (-F) for coords.  The backward is not itself
+        differentiable (no second derivatives)."""
+
+        @staticmethod
+        def forward(ctx, coords, model, types, box):
+            out = model.compute(coords.detach().contiguous(), types, box)
+            ctx.save_for_backward(out["forces"])
+            ctx.mark_non_differentiable(out["virial"])
+            return out["energy"].reshape(()), out["virial"]
+
+        @staticmethod
+        @once_differentiable
+        def backward(ctx, g_energy, g_virial):
+            (F,) = ctx.saved_tensors
+            return -g_energy * F, None, None, None
+
+    return Potential
+
+
 try:
     ParamLoss = _make_param_loss()
-except ImportError:  # torch is needed only for the autograd wrapper
+    Potential = _make_potential()
+except ImportError:  # torch is needed only for the autograd wrappers
     ParamLoss = None
+    Potential = None

@@ -19,25 +19,6 @@ bool tc_available(const Model* m);
 
 namespace {
 
-struct Alloc {
-  std::vector<void*> dev;
-  std::vector<void*> host;
-};
-
-Alloc& allocs(Model* m) {
-  static std::vector<std::pair<Model*, Alloc>> table;
-  for (auto& e : table)
-    if (e.first == m) return e.second;
-  table.push_back({m, Alloc{}});
-  return table.back().second;
-}
-
-void forget(Model* m) {
-  // allocations are released by dp_destroy; the table entry is cleared there
-  allocs(m).dev.clear();
-  allocs(m).host.clear();
-}
-
 template <class P>
 dp_status dalloc(Model* m, P** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -47,7 +28,7 @@ dp_status dalloc(Model* m, P** p, size_t bytes) {
     m->last_error = std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e);
     return DP_ERR_OOM;
   }
-  allocs(m).dev.push_back(q);
+  m->dev_allocs.push_back(q);
   *p = static_cast<P*>(q);
   return DP_OK;
 }
@@ -60,7 +41,7 @@ dp_status halloc(Model* m, P** p, size_t bytes) {
     m->last_error = std::string("cudaMallocHost: ") + cudaGetErrorString(e);
     return DP_ERR_OOM;
   }
-  allocs(m).host.push_back(q);
+  m->host_allocs.push_back(q);
   *p = static_cast<P*>(q);
   return DP_OK;
 }
@@ -221,24 +202,8 @@ dp_status md_step(Model* m, int N, double dt, bool rebuild) {
   return DP_OK;
 }
 
-struct GraphCache {
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};
-  long long kernels[2] = {0, 0};
-  int N = -1, nrep = -1;
-  double dt = 0;
-  unsigned long long geom_hash = 0;
-};
-
-GraphCache& gcache(Model* m) {
-  static std::vector<std::pair<Model*, GraphCache>> table;
-  for (auto& e : table)
-    if (e.first == m) return e.second;
-  table.push_back({m, GraphCache{}});
-  return table.back().second;
-}
-
 void drop_graphs(Model* m) {
-  GraphCache& g = gcache(m);
+  Model::GraphCache& g = m->graphs;
   for (auto& e : g.exec)
     if (e) { cudaGraphExecDestroy(e); e = nullptr; }
   g.N = -1;
@@ -385,7 +350,7 @@ dp_status run_md(Model* m, dp_md_state* st, double dt, int nsteps, int capture, 
     DP_TRY(launch_rebuild(m, N));
     DP_TRY(force_eval(m, N));
   }
-  GraphCache& gc = gcache(m);
+  Model::GraphCache& gc = m->graphs;
   if (tune) {
     bool changed = false;
     DP_TRY(ensure_tuned(m, N, &changed));
@@ -464,6 +429,7 @@ dp_status upload_weights(Model* m) {
   DP_CUDA_TRY(m, cudaMemcpy(m->fitT32, wT32.data(), 4 * wT32.size(), cudaMemcpyHostToDevice));
   DP_CUDA_TRY(m, cudaMemcpy(m->stat64, stat.data(), 8 * stat.size(), cudaMemcpyHostToDevice));
   DP_CUDA_TRY(m, cudaMemcpy(m->stat32, stat32.data(), 4 * stat32.size(), cudaMemcpyHostToDevice));
+  DP_TRY(launch_pad_rows(m));
   if (m->prec == DP_MIX_BF16 || m->prec == DP_MIX_FP16) DP_TRY(launch_tc_setup(m));
   return DP_OK;
 }
@@ -546,6 +512,8 @@ dp_status dp_create(dp_model** out, int ntypes, const char* const* type_map, dou
   A_(fitT32, 4 * tsz * nt);
   A_(stat64, 8 * 8 * nt);
   A_(stat32, 4 * 8 * nt);
+  A_(pad64, 8 * (size_t)nt * nt * 4 * kN3);
+  A_(pad32, 4 * (size_t)nt * nt * 4 * kN3);
   A_(perm, 4 * N); A_(inv, 4 * N); A_(itype, 4 * N); A_(irep, 4 * N);
   A_(type_count, 4 * (kMaxTypes + 1)); A_(type_off, 4 * (kMaxTypes + 1));
   A_(blk_count, 4 * (size_t)kMaxTypes * (N / 1024 + 2));
@@ -752,9 +720,11 @@ void dp_destroy(dp_model* h) {
   cudaStreamSynchronize(m->stream);
   drop_graphs(m);
   if (m->capture_stream) cudaStreamDestroy(m->capture_stream);
-  for (void* p : allocs(m).dev) cudaFree(p);
-  for (void* p : allocs(m).host) cudaFreeHost(p);
-  forget(m);
+  for (void* p : m->dev_allocs) cudaFree(p);
+  for (void* p : m->host_allocs) cudaFreeHost(p);
+  m->dev_allocs.clear();
+  m->host_allocs.clear();
+  mix_fit_release(m);
   delete h;
 }
 

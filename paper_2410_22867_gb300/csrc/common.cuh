@@ -86,6 +86,12 @@ struct Model {
   float* fitT32 = nullptr;
   double* stat64 = nullptr;   // davg [nt][4], 1/dstd [nt][4]
   float* stat32 = nullptr;
+  // One padded neighbour slot's contribution to S*T per (ti, tj): R_pad^T G(R_pad_0), c-major
+  // [nt][nt][4][100], with R_pad = -davg[ti] / dstd[ti] (the normalised zero row).  Padded slots
+  // add (sel[tj] - count) times it.  has_pad is false when every davg is 0 (then R_pad = 0).
+  double* pad64 = nullptr;
+  float* pad32 = nullptr;
+  bool has_pad = false;
   // 16-bit operand copies for the tensor-core kernels (per type), laid out by those kernels
   void* tc_weights = nullptr;
   size_t tc_weights_bytes = 0;
@@ -173,8 +179,18 @@ struct Model {
   // embedding backward, dE/dT, descriptor
   int tune_grid[4] = {0, 0, 0, 0};
   unsigned long long tuned_key = 0;
-  cudaGraphExec_t graph_exec = nullptr;
-  int graph_key[4] = {0, 0, 0, 0};
+  // captured MD steps (between rebuilds, with a rebuild) and the configuration they were
+  // captured for; owned by the model and destroyed with it
+  struct GraphCache {
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    long long kernels[2] = {0, 0};
+    int N = -1, nrep = -1;
+    double dt = 0;
+    unsigned long long geom_hash = 0;
+  } graphs;
+  void* fit_maps = nullptr;   // tensor maps of the mixed fitting kernel (mix_fit.cu), owned
+  // every device / pinned host allocation of dp_create, released by dp_destroy
+  std::vector<void*> dev_allocs, host_allocs;
 };
 
 // ---------------------------------------------------------------------------
@@ -266,6 +282,7 @@ dp_status launch_delta(Model* m, int N);
 dp_status launch_format(Model* m, int N);
 dp_status launch_get_nlist(Model* m, int N, int* nlist, int* images);
 // simt.cu
+dp_status launch_pad_rows(Model* m);  // pad64 / pad32 from the current weights (synchronous caller)
 dp_status launch_descriptor(Model* m, int N);
 dp_status launch_fitting(Model* m, int N);
 dp_status launch_embed_backward(Model* m, int N);
@@ -276,6 +293,7 @@ dp_status launch_mix_embed_backward(Model* m, int N);
 dp_status mix_fit_setup(Model* m);
 size_t mix_fit_weight_bytes(int ntypes);
 dp_status launch_mix_fitting(Model* m, int N);
+void mix_fit_release(Model* m);
 // grid of a tunable mixed kernel: the autotuned value if set, else the default
 inline int tuned_grid(const Model* m, int which, int dflt) { return m->tune_grid[which] > 0 ? m->tune_grid[which] : dflt; }
 // parameter gradient (pgrad.cu)

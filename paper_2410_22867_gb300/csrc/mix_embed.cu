@@ -1016,12 +1016,21 @@ __global__ void k_scan_fix(int N, int nblk, int* rowoff, const int* blk) {
 // per-warp double buffer in dynamic shared memory by cp.async one atom ahead; T[c][b < 16] is
 // held in registers and lane -> rows a = lane, lane + 32, ... of D (16 values, two 16-byte
 // stores).
+// Padded neighbour slots add (sel[tj] - count) copies of the normalised zero row's term
+// (pad: [nt][nt][4][100], c-major, or null when every davg is 0).
 constexpr int kDescWarps = 4;
+
+struct PadArgs {
+  const float* pad;
+  const int* itype;
+  const int* nl_count;
+  int sel[kMaxTypes];
+};
 
 template <bool F16>
 __global__ void __launch_bounds__(32 * kDescWarps) k_mix_descriptor(int N, int ntypes, float invS,
                                                                    const float* __restrict__ Tseg, float4* Tm,
-                                                                   unsigned short* Dm) {
+                                                                   unsigned short* Dm, PadArgs pa) {
   extern __shared__ float4 sbuf[];  // [kDescWarps][2][ntypes][100]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float4* mine = sbuf + (size_t)w * 2 * ntypes * kN3;
@@ -1046,12 +1055,19 @@ __global__ void __launch_bounds__(32 * kDescWarps) k_mix_descriptor(int N, int n
     __syncwarp();
     float4* seg = mine + buf * ntypes * kN3;
     // T (c-major, 400 floats) in place of the first segment
+    const int ti = pa.pad ? pa.itype[i] : 0;
     for (int q = lane; q < kN3; q += 32) {
       float4 v = seg[q];
       for (int tj = 1; tj < ntypes; ++tj) {
         const float4 u = seg[tj * kN3 + q];
         v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
       }
+      if (pa.pad)
+        for (int tj = 0; tj < ntypes; ++tj) {
+          const float np = (float)(pa.sel[tj] - pa.nl_count[(size_t)i * ntypes + tj]);
+          const float4 u = reinterpret_cast<const float4*>(pa.pad + (size_t)(ti * ntypes + tj) * 400)[q];
+          v.x = fmaf(np, u.x, v.x); v.y = fmaf(np, u.y, v.y); v.z = fmaf(np, u.z, v.z); v.w = fmaf(np, u.w, v.w);
+        }
       v.x *= invS; v.y *= invS; v.z *= invS; v.w *= invS;
       seg[q] = v;
     }
@@ -1210,12 +1226,19 @@ dp_status launch_mix_descriptor(Model* m, int N) {
   const void* dfn = f16 ? reinterpret_cast<const void*>(k_mix_descriptor<true>)
                         : reinterpret_cast<const void*>(k_mix_descriptor<false>);
   DP_CUDA_TRY(m, ensure_smem(dfn, dsm));
+  PadArgs pa{};
+  pa.pad = m->has_pad ? m->pad32 : nullptr;
+  pa.itype = m->itype;
+  pa.nl_count = m->nl_count;
+  for (int t = 0; t < m->ntypes; ++t) pa.sel[t] = m->sel[t];
   if (f16)
     k_mix_descriptor<true><<<dgrid, 32 * kDescWarps, dsm, m->stream>>>(
-        N, m->ntypes, 1.f / (float)m->S, m->Tseg, static_cast<float4*>(m->Tm), static_cast<unsigned short*>(m->Dm));
+        N, m->ntypes, 1.f / (float)m->S, m->Tseg, static_cast<float4*>(m->Tm), static_cast<unsigned short*>(m->Dm),
+        pa);
   else
     k_mix_descriptor<false><<<dgrid, 32 * kDescWarps, dsm, m->stream>>>(
-        N, m->ntypes, 1.f / (float)m->S, m->Tseg, static_cast<float4*>(m->Tm), static_cast<unsigned short*>(m->Dm));
+        N, m->ntypes, 1.f / (float)m->S, m->Tseg, static_cast<float4*>(m->Tm), static_cast<unsigned short*>(m->Dm),
+        pa);
   m->launches += 4;
   DP_LAUNCH_CHECK(m);
   return DP_OK;

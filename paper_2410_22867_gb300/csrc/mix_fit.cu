@@ -620,14 +620,10 @@ bool make_map(CUtensorMap* map, void* base, bool f16, uint64_t cols, uint64_t ro
   return r == CUDA_SUCCESS;
 }
 
+// The model's tensor maps, created with its weights (mix_fit_setup) and freed by dp_destroy.
 FitMaps* maps_of(Model* m) {
-  static std::mutex mu;
-  static std::deque<std::pair<Model*, FitMaps>> table;  // stable addresses across push_back
-  std::lock_guard<std::mutex> lock(mu);
-  for (auto& e : table)
-    if (e.first == m) return &e.second;
-  table.push_back({m, FitMaps{}});
-  return &table.back().second;
+  if (!m->fit_maps) m->fit_maps = new FitMaps{};
+  return static_cast<FitMaps*>(m->fit_maps);
 }
 
 constexpr size_t kFitSmem = kPrm + 4 * kF * 4 + 1024;
@@ -636,6 +632,11 @@ static_assert(kXLo + kB1Slots * kB1Slot <= kStage, "B1 slots overlap the dE/dD s
 static_assert(kSt + kSSlots * kSSlot <= kPrm, "split slots exceed the staging area");
 
 }  // namespace
+
+void mix_fit_release(Model* m) {
+  delete static_cast<FitMaps*>(m->fit_maps);
+  m->fit_maps = nullptr;
+}
 
 // Build the 16-bit weight copies and the tensor maps (at model creation).
 dp_status mix_fit_setup(Model* m) {

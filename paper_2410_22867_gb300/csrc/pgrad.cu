@@ -75,6 +75,8 @@ struct PgArgs {
   const void* nl_d;
   const int* nl_count;   // [N][nt]
   const double* wdir;    // [N][3] tangent direction w (internal order)
+  const T* pad;          // [nt][nt][4][100] padded-slot term of T, or null (every davg is 0)
+  int sel[kMaxTypes];
 };
 
 // Environment row R_hat and its tangent along d' (Jacobian of (s, s d/r), s = sw/r).
@@ -203,6 +205,18 @@ __global__ void __launch_bounds__(kPgNB) k_pg_emb_fwd(PgArgs<T> a, int ti, int a
         __syncthreads();
       }
     }
+    if (a.pad)  // padded slots: constant in the positions, so they add to T but not to T'
+      for (int tj = 0; tj < a.ntypes; ++tj) {
+        const T np = T(a.sel[tj] - a.nl_count[(size_t)i * a.ntypes + tj]);
+        const T* P = a.pad + (size_t)(ti * a.ntypes + tj) * 4 * kN3;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int col = tid + u * kPgNB;
+          if (col < kN3)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[u][c] += np * P[c * kN3 + col];
+        }
+      }
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int col = tid + u * kPgNB;
@@ -273,6 +287,69 @@ __global__ void k_pg_desc_bwd(int n, const T* TT, const T* Yb, T* TB) {
       TB[(size_t)li * 800 + o] = tb;
       TB[(size_t)li * 800 + 400 + o] = tdb;
     }
+  }
+}
+
+// 5b. Parameter gradient through the padded slots of centre type ti, one block per neighbour
+//     type tj.  Every padded slot of segment tj holds the row R_pad = -davg[ti] / dstd[ti] and
+//     G = N_{ti,tj}(R_pad_0), so with T_bar the adjoint of T (row li of TB, primal half):
+//       G_bar[a] = (1/S) sum_li (sel[tj] - count_li,tj) sum_c T_bar_li[c][a] R_pad[c],
+//     and the reverse of the embedding net at the single input R_pad_0 gives the parameter
+//     gradients (FP64 atomics).  The input is a constant (davg, dstd are not parameters).
+template <class T>
+__global__ void __launch_bounds__(128) k_pg_pad_rev(PgArgs<T> a, int ti, int a0, int n, const T* __restrict__ TB,
+                                                   double* grad) {
+  const int tj = blockIdx.x, tid = threadIdx.x;
+  const T* W = a.w + (size_t)(ti * a.ntypes + tj) * kEmbParams;
+  double* gW = grad + (size_t)(ti * a.ntypes + tj) * kEmbParams;
+  __shared__ T Rp[4], h1[kN1], t2[kN2], h2[kN2], gG[kN3], dz3[kN3], dh2[kN2], dz2[kN2];
+  if (tid < 4) Rp[tid] = (T(0) - a.stat[ti * 4 + tid]) * a.stat[(a.ntypes + ti) * 4 + tid];
+  __syncthreads();
+  if (tid < kN3) {
+    T acc = T(0);
+    for (int li = 0; li < n; ++li) {
+      const T np = T(a.sel[tj] - a.nl_count[(size_t)(a0 + li) * a.ntypes + tj]);
+      const T* tb = TB + (size_t)li * 800;
+      acc += np * (tb[tid] * Rp[0] + tb[kN3 + tid] * Rp[1] + tb[2 * kN3 + tid] * Rp[2] + tb[3 * kN3 + tid] * Rp[3]);
+    }
+    gG[tid] = acc * a.invS;
+  }
+  const T x = Rp[0];
+  if (tid < kN1) h1[tid] = tanh_t<T>(x * W[kEW1 + tid] + W[kEb1 + tid]);
+  __syncthreads();
+  if (tid < kN2) {
+    T z = W[kEb2 + tid];
+    for (int k = 0; k < kN1; ++k) z += h1[k] * W[kEW2 + k * kN2 + tid];
+    t2[tid] = tanh_t<T>(z);
+    h2[tid] = h1[tid % kN1] + t2[tid];
+  }
+  __syncthreads();
+  if (tid < kN3) {  // G[a] = h2[a % 50] + tanh(z3[a])
+    T z = W[kEb3 + tid];
+    for (int mm = 0; mm < kN2; ++mm) z += h2[mm] * W[kEW3 + mm * kN3 + tid];
+    const T t3 = tanh_t<T>(z);
+    dz3[tid] = gG[tid] * (T(1) - t3 * t3);
+    atomicAdd(&gW[kEb3 + tid], (double)dz3[tid]);
+  }
+  __syncthreads();
+  for (int q = tid; q < kN2 * kN3; q += blockDim.x)
+    atomicAdd(&gW[kEW3 + q], (double)(h2[q / kN3] * dz3[q % kN3]));
+  if (tid < kN2) {
+    T v = gG[tid] + gG[tid + kN2];
+    for (int aa = 0; aa < kN3; ++aa) v += W[kEW3 + tid * kN3 + aa] * dz3[aa];
+    dh2[tid] = v;
+    dz2[tid] = v * (T(1) - t2[tid] * t2[tid]);
+    atomicAdd(&gW[kEb2 + tid], (double)dz2[tid]);
+  }
+  __syncthreads();
+  for (int q = tid; q < kN1 * kN2; q += blockDim.x)
+    atomicAdd(&gW[kEW2 + q], (double)(h1[q / kN2] * dz2[q % kN2]));
+  if (tid < kN1) {
+    T v = dh2[tid] + dh2[tid + kN1];
+    for (int mm = 0; mm < kN2; ++mm) v += W[kEW2 + tid * kN2 + mm] * dz2[mm];
+    const T dz1 = v * (T(1) - h1[tid] * h1[tid]);
+    atomicAdd(&gW[kEb1 + tid], (double)dz1);
+    atomicAdd(&gW[kEW1 + tid], (double)(x * dz1));
   }
 }
 
@@ -583,6 +660,9 @@ dp_status run_param_grad(Model* m, int N, double* grad) {
   a.w = theta;
   a.stat = (sizeof(T) == 8) ? reinterpret_cast<const T*>(m->stat64) : reinterpret_cast<const T*>(m->stat32);
   a.nl_j = m->nl_j; a.nl_d = m->nl_d; a.nl_count = m->nl_count; a.wdir = m->pg_w;
+  a.pad = !m->has_pad ? nullptr
+                      : (sizeof(T) == 8) ? reinterpret_cast<const T*>(m->pad64) : reinterpret_cast<const T*>(m->pad32);
+  for (int t = 0; t < nt; ++t) a.sel[t] = m->sel[t];
 
   // host copies of the type ranges and per-atom neighbour counts (chunking)
   std::vector<int> cnt((size_t)N * nt), tc(kMaxTypes + 1);
@@ -701,6 +781,10 @@ dp_status run_param_grad(Model* m, int N, double* grad) {
     // 5: T_bar, T'_bar
     k_pg_desc_bwd<T><<<std::min(n, 8 * sms), 128, 0, m->stream>>>(n, TT, Yb, TB);
     m->launches += 1;
+    if (a.pad) {
+      k_pg_pad_rev<T><<<nt, 128, 0, m->stream>>>(a, ti, ac.a0, n, TB, grad);
+      m->launches += 1;
+    }
     // 6: embedding reverse per neighbour row
     for (const RowChunk& rc : rchunks) {
       if (rc.ti != ti || rc.a0 != ac.a0 || rc.R == 0) continue;

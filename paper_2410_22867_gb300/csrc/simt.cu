@@ -50,6 +50,8 @@ struct EmbArgs {
   int switch_kind;
   const T* w;          // theta
   const T* stat;       // davg [nt][4] then 1/dstd [nt][4]
+  const T* pad;        // [nt][nt][4][100] padded-slot term, or null (every davg is 0)
+  int sel[kMaxTypes];
   const int* itype;
   const int* nl_j;
   const void* nl_d;
@@ -188,6 +190,19 @@ __global__ void __launch_bounds__(EB<T>::v) k_embed_fwd(EmbArgs<T> a) {
           }
         }
         __syncthreads();
+      }
+    }
+    if (a.pad) {  // padded slots: (sel - count) copies of the normalised zero row
+      for (int tj = 0; tj < a.ntypes; ++tj) {
+        const T np = T(a.sel[tj] - a.nl_count[(size_t)i * a.ntypes + tj]);
+        const T* P = a.pad + (size_t)(ti * a.ntypes + tj) * 4 * kN3;
+#pragma unroll
+        for (int u = 0; u < NCOL; ++u) {
+          const int col = tid + u * NB;
+          if (col < kN3)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[u][c] += np * P[c * kN3 + col];
+        }
       }
     }
 #pragma unroll
@@ -365,6 +380,37 @@ __global__ void __launch_bounds__(EB<T>::v) k_embed_bwd(EmbArgs<T> a) {
   }
 }
 
+// One padded neighbour slot per (ti, tj), block ti * nt + tj: the normalised zero row
+// R_pad = (0 - davg[ti]) / dstd[ti], its embedding G = N_{ti,tj}(R_pad_0), and the product
+// R_pad[c] G[a] that every padded slot of segment tj adds to S*T.  FP64, stored in FP64 and FP32.
+__global__ void __launch_bounds__(128) k_pad_rows(int nt, const double* __restrict__ w,
+                                                  const double* __restrict__ stat, double* pad64, float* pad32) {
+  const int ti = blockIdx.x / nt, tj = blockIdx.x % nt, tid = threadIdx.x;
+  const double* W = w + (size_t)(ti * nt + tj) * kEmbParams;
+  __shared__ double Rp[4], h1[kN1], h2[kN2];
+  if (tid < 4) Rp[tid] = (0.0 - stat[ti * 4 + tid]) * stat[(nt + ti) * 4 + tid];
+  __syncthreads();
+  const double x = Rp[0];
+  if (tid < kN1) h1[tid] = tanh(x * W[kEW1 + tid] + W[kEb1 + tid]);
+  __syncthreads();
+  if (tid < kN2) {
+    double z = W[kEb2 + tid];
+    for (int k = 0; k < kN1; ++k) z += h1[k] * W[kEW2 + k * kN2 + tid];
+    h2[tid] = h1[tid % kN1] + tanh(z);
+  }
+  __syncthreads();
+  if (tid < kN3) {
+    double z = W[kEb3 + tid];
+    for (int mm = 0; mm < kN2; ++mm) z += h2[mm] * W[kEW3 + mm * kN3 + tid];
+    const double g = h2[tid % kN2] + tanh(z);
+    for (int c = 0; c < 4; ++c) {
+      const size_t o = ((size_t)(ti * nt + tj) * 4 + c) * kN3 + tid;
+      pad64[o] = Rp[c] * g;
+      pad32[o] = (float)(Rp[c] * g);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ fitting net
 enum EpiMode { EPI_TANH = 0, EPI_RES_TANH = 1, EPI_BWD = 2, EPI_NONE = 3 };
 
@@ -527,6 +573,9 @@ EmbArgs<T> make_emb_args(Model* m, int N) {
   a.rc = (T)m->rc; a.rs = (T)m->rs; a.invS = T(1) / (T)m->S; a.switch_kind = m->switch_kind;
   a.w = (sizeof(T) == 8) ? reinterpret_cast<const T*>(m->w64) : reinterpret_cast<const T*>(m->w32);
   a.stat = (sizeof(T) == 8) ? reinterpret_cast<const T*>(m->stat64) : reinterpret_cast<const T*>(m->stat32);
+  a.pad = !m->has_pad ? nullptr
+                      : (sizeof(T) == 8) ? reinterpret_cast<const T*>(m->pad64) : reinterpret_cast<const T*>(m->pad32);
+  for (int t = 0; t < m->ntypes; ++t) a.sel[t] = m->sel[t];
   a.itype = m->itype; a.nl_j = m->nl_j; a.nl_d = m->nl_d; a.nl_count = m->nl_count;
   a.Tm = static_cast<T*>(m->Tm); a.Dm = static_cast<T*>(m->Dm); a.dD = static_cast<const T*>(m->dD);
   a.force = m->force; a.vir_atom = m->vir_atom;
@@ -566,6 +615,16 @@ dp_status run_embed_backward(Model* m, int N) {
 }
 
 }  // namespace
+
+dp_status launch_pad_rows(Model* m) {
+  m->has_pad = false;
+  for (double v : m->davg_host) m->has_pad = m->has_pad || v != 0.0;
+  if (!m->has_pad) return DP_OK;
+  k_pad_rows<<<m->ntypes * m->ntypes, 128>>>(m->ntypes, m->w64, m->stat64, m->pad64, m->pad32);
+  m->launches += 1;
+  DP_LAUNCH_CHECK(m);
+  return DP_OK;
+}
 
 dp_status launch_descriptor(Model* m, int N) {
   if (is_mixed(m)) return launch_mix_descriptor(m, N);

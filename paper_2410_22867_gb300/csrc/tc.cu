@@ -231,6 +231,43 @@ extern "C" dp_status dp_selftest(int which, double* result) {
 }
 
 // ---------------------------------------------------------------------------
+// Check of the bounded-wait error path: one thread initialises an mbarrier that
+// expects one arrival and waits for its first phase with the kernels' bounded wait
+// routine, which nothing will complete.  No copy or MMA is issued, so nothing is in
+// flight when the wait gives up; the kernel sets the timeout bit and returns.
+
+namespace dpg {
+namespace {
+
+static __device__ int g_wait_selftest_err;
+
+__global__ void k_wait_selftest(uint32_t limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) tc::mbar_wait_limit(&bar, 0, &g_wait_selftest_err, limit);
+  __syncthreads();
+}
+
+}  // namespace
+}  // namespace dpg
+
+extern "C" dp_status dp_wait_selftest(unsigned int spin_limit) {
+  if (spin_limit < 1 || spin_limit > tc::kSpinLimit) return DP_ERR_ARG;
+  if (!tc_available(nullptr)) return DP_ERR_UNSUPPORTED;
+  const int zero = 0;
+  if (cudaMemcpyToSymbol(g_wait_selftest_err, &zero, sizeof(int)) != cudaSuccess) return DP_ERR_CUDA;
+  k_wait_selftest<<<1, 32>>>(spin_limit);
+  if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return DP_ERR_CUDA;
+  int bits = 0;
+  if (cudaMemcpyFromSymbol(&bits, g_wait_selftest_err, sizeof(int)) != cudaSuccess) return DP_ERR_CUDA;
+  return (bits & ERR_TIMEOUT) ? DP_ERR_WAIT_TIMEOUT : DP_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Allocation-free variant of the self check.
 //
 // dp_selftest above takes its 32 bytes of device scratch from cudaMalloc and

@@ -7,6 +7,8 @@ import pytest
 import oracle
 from paper_2410_22867_gb300 import synth
 
+from _parity import errors
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -85,10 +87,18 @@ def test_md_batch_256_replicas_mixed(dp, water_weights):
     e0 = m.compute_batch(torch.tensor(coords, device="cuda"), torch.tensor(types, device="cuda"), offs_c,
                          boxes)["energy"].cpu().numpy()
     orc = oracle.Model(water_weights.to_blob())
-    small = np.argsort([s.natoms for s in reps])[:4]
-    for r in small:
+    # per-replica parity on the four smallest replicas and two of mid size: energy per atom,
+    # force error relative to the force RMS, per-atom energy deviations (see _parity.py)
+    order = np.argsort([s.natoms for s in reps])
+    pick = list(order[:4]) + [order[len(order) // 2], order[len(order) // 2 + 1]]
+    out0 = m.compute_batch(torch.tensor(coords, device="cuda"), torch.tensor(types, device="cuda"), offs_c, boxes)
+    for r in pick:
         ref = orc.compute(reps[r].coords, reps[r].types, reps[r].box)
         assert abs(e0[r] - ref["energy"]) / reps[r].natoms <= 1e-4
+        sl = slice(offs_c[r], offs_c[r + 1])
+        e = errors({"forces": out0["forces"][sl], "atom_energy": out0["atom_energy"][sl]}, ref, reps[r].types)
+        assert e["f_rel"] <= 1e-2, (r, e)
+        assert e["dev_rel"] <= 0.3, (r, e)
     # 25 NVE steps: every replica stays finite and conserves its total energy.  (An untrained
     # model has no short-range repulsion: a few of these replicas see two atoms collapse
     # together after ~35 steps, identically in every precision and in the oracle; see

@@ -8,6 +8,8 @@ import pytest
 import oracle
 from paper_2410_22867_gb300 import synth
 
+from _parity import copper_subbox_masks, errors
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -142,34 +144,20 @@ def test_fp32_matches_oracle(dp, n_mol):
 
 def test_fp32_copper_subbox(dp):
     """Cu 32^3 (131,072 atoms) in FP32; errors on the 4,000 atoms of FCC cells [0,10)^3,
-    with the oracle evaluating only centres within r_c of that sub-box."""
+    with the oracle evaluating only centres within r_c of that sub-box.  The untrained
+    model's forces are ~1e-5 eV/A, so the bars are relative to the signal."""
     s = synth.copper_fcc(32, 0)
     w = synth.copper_weights()
-    a = 3.634
-    sub, centre = _copper_subbox_masks(s, a, w.rcut)
+    sub, centre = copper_subbox_masks(s, 3.634, w.rcut)
     ref = oracle.Model(w.to_blob()).compute(s.coords, s.types, s.box, centre_mask=centre)
     m = dp.DPModel(w, "fp32", max_atoms=s.natoms)
     x, t = _cuda(s)
     out = m.compute(x, t, s.box)
-    F = out["forces"].cpu().numpy()[sub]
-    rmse = np.sqrt(((F - ref["forces"][sub]) ** 2).mean())
-    assert rmse <= 1e-5
-    Ei = out["atom_energy"].cpu().numpy()[sub]
-    assert np.abs(Ei - ref["atom_energy"][sub]).max() <= 1e-5
-
-
-def _copper_subbox_masks(s, a, rcut):
-    """Atoms of FCC cells [0,10)^3 (by lattice site) and all centres within r_c of them."""
-    L = s.box[0]
-    site = np.rint(s.coords / (a / 2)).astype(int)  # half-lattice index of the nearest site
-    sub = np.all((site >= 0) & (site < 20), axis=1)
-    assert sub.sum() == 4000
-    lo, hi = -rcut - 0.5, 10 * a + rcut + 0.5
-    w = s.coords.copy()
-    w = w - L * np.floor(w / L)
-    w[w > L - rcut - 1.0] -= L
-    centre = np.all((w > lo) & (w < hi), axis=1)
-    return sub, centre
+    e = errors(out, ref, s.types, sub)
+    assert e["f_rmse"] <= 1e-5, e
+    assert e["f_rel"] <= 1e-4, e
+    assert e["dev_rel"] <= 0.3, e  # E_i spread 7e-6 eV, FP32 rounding of E_i ~ 1e-7 eV
+    assert e["ei_max"] <= 1e-5, e
 
 
 # ------------------------------------------------------------------ batch / edge cases
@@ -301,6 +289,11 @@ def test_tensor_core_layout_selftest(dp, which):
     assert err == 0.0
 
 
+# measured relative error x margin on the untrained models (force RMSE / force RMS,
+# per-atom energy deviations; see _parity.py)
+MIX_BARS = {"mix_bf16": {"f_rel": 3e-2, "dev_rel": 0.5}, "mix_fp16": {"f_rel": 1e-2, "dev_rel": 0.3}}
+
+
 @pytest.mark.parametrize("prec", ["mix_bf16", "mix_fp16"])
 @pytest.mark.parametrize("n_mol", [64, 1024])
 def test_mixed_matches_oracle_water(dp, prec, n_mol):
@@ -310,33 +303,31 @@ def test_mixed_matches_oracle_water(dp, prec, n_mol):
     m = dp.DPModel(w, prec, max_atoms=s.natoms)
     x, t = _cuda(s)
     out = m.compute(x, t, s.box)
-    F = out["forces"].cpu().numpy()
-    rmse = np.sqrt(((F - ref["forces"]) ** 2).mean())
-    rms = np.sqrt((ref["forces"] ** 2).mean())
-    assert rmse <= 2e-3
-    assert rmse / rms <= 0.05, (rmse, rms)
-    e_atom = abs(out["energy"].item() - ref["energy"]) / s.natoms
-    assert e_atom <= 1e-4
+    e = errors(out, ref, s.types)
+    assert e["f_rmse"] <= 2e-3, e
+    assert e["f_rel"] <= MIX_BARS[prec]["f_rel"], e
+    assert e["dev_rel"] <= MIX_BARS[prec]["dev_rel"], e
+    assert e["e_atom"] <= 1e-4, e
     np.testing.assert_allclose(out["virial"].cpu().numpy(), ref["virial"], rtol=0.05,
-                               atol=0.05 * np.abs(ref["virial"]).max())
+                               atol=3 * MIX_BARS[prec]["f_rel"] * np.abs(ref["virial"]).max())
 
 
 @pytest.mark.parametrize("prec", ["mix_bf16", "mix_fp16"])
 def test_mixed_copper_subbox(dp, prec):
     s = synth.copper_fcc(32, 0)
     w = synth.copper_weights()
-    sub, centre = _copper_subbox_masks(s, 3.634, w.rcut)
+    sub, centre = copper_subbox_masks(s, 3.634, w.rcut)
     ref = oracle.Model(w.to_blob()).compute(s.coords, s.types, s.box, centre_mask=centre)
     m = dp.DPModel(w, prec, max_atoms=s.natoms)
     x, t = _cuda(s)
     out = m.compute(x, t, s.box)
-    F = out["forces"].cpu().numpy()[sub]
-    Fr = ref["forces"][sub]
-    rmse = np.sqrt(((F - Fr) ** 2).mean())
-    assert rmse <= 2e-3
-    assert rmse / np.sqrt((Fr ** 2).mean()) <= 0.05
-    Ei = out["atom_energy"].cpu().numpy()[sub]
-    assert abs(Ei.sum() - ref["atom_energy"][sub].sum()) / 4000 <= 1e-4
+    e = errors(out, ref, s.types, sub)
+    assert e["f_rmse"] <= 2e-3, e
+    assert e["f_rel"] <= MIX_BARS[prec]["f_rel"], e
+    assert e["e_atom"] <= 1e-4, e
+    # the untrained copper E_i spread (7e-6 eV) is below the 16-bit rounding of E_i itself;
+    # the deviation measure is checked on the normalised model (test_gpu_normalised.py)
+    assert e["ei_max"] <= 1e-4, e
 
 
 def test_md_water12k_fp32_tracks_fp64(dp):
