@@ -27,7 +27,7 @@ namespace dpg {
 namespace {
 
 constexpr int kRows = 128;     // rows per tile = threads per CTA = TMEM lanes
-constexpr int kMaxAtoms = 6;   // atom segments per tile
+constexpr int kMaxAtoms = 4;   // atom segments per tile (columns (atom, c) of the T product: 16)
 constexpr uint32_t kTmemCols = 128;  // per CTA: D2/D3 share columns 0..111
 constexpr int kLocWarp = 1;    // the warp that locates tiles (thread 0 issues the MMAs)
 
@@ -232,9 +232,27 @@ __device__ __forceinline__ void load_small(const float* __restrict__ W, float* s
     small[q] = (q & 31) < kN1 ? W[(q < 32 ? kEW1 : kEb1) + (q & 31)] : 0.f;
 }
 
-// Embedding weights of pair (ti, tj) into the MMA operand blocks and small fp32 arrays.
-//   B2: [64 x 64] rows n (layer-2 output), K = layer-1 unit (25 used, bias at 25/26) -> W2[k][n]
-//   B3: [112 x 64] rows a (layer-3 output), K = layer-2 unit (50 used, bias at 50/51) -> W3[m][a]
+// The forward's weights enter the products split into a 16-bit head and the 16-bit rounding of
+// the remainder: z = h W_hi + h W_lo, exact in the weights to about 2^-22 (fp16) or 2^-16 (bf16)
+// relative.  With a single 16-bit copy every neighbour row would see the same rounding error,
+// which does not average out in T and biases the energy (the activations' rounding differs from
+// row to row and mostly does).  Layer 2: W_hi in K slots 0..31 and W_lo in 32..63 of one block,
+// against [h1, 1, 1 | h1] in A (the bias rides in the head half).  Layer 3: a second B3 block.
+template <bool F16>
+__device__ __forceinline__ float lo_part(float w) {
+  return w - split_hi<F16>(w);
+}
+// Element (k, n) of the split layer-2 block (k < 64).
+template <bool F16>
+__device__ __forceinline__ float w2_split_elem(const float* __restrict__ W, int k, int n) {
+  if (k < 32) return split_hi<F16>(w2_elem<F16>(W, k, n));  // bias rows hold head and remainder already
+  return (k - 32 < kN1) ? lo_part<F16>(w2_elem<F16>(W, k - 32, n)) : 0.f;
+}
+// Embedding weights of pair (ti, tj) into the forward's MMA operand blocks and small fp32 arrays.
+//   B2: [64 x 64] rows n (layer-2 output), K slots 0..31 the 16-bit head of W2 (25 units, bias at
+//       25/26), 32..56 the remainder of W2
+//   B3: two [112 x 64] blocks (head, remainder), rows a (layer-3 output), K = layer-2 unit (50
+//       used, bias head and remainder at 50/51 of the head block)
 template <bool F16>
 __device__ void load_fwd_weights(const float* __restrict__ W, unsigned char* sB2, unsigned char* sB3, float* small) {
   const int t = threadIdx.x;
@@ -244,19 +262,27 @@ __device__ void load_fwd_weights(const float* __restrict__ W, unsigned char* sB2
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       int k = k0 + 2 * h;
-      p[h] = tc::pack2<F16>(w2_elem<F16>(W, k, n), w2_elem<F16>(W, k + 1, n));
+      p[h] = tc::pack2<F16>(w2_split_elem<F16>(W, k, n), w2_split_elem<F16>(W, k + 1, n));
     }
     tc::st_chunk(sB2, n, k0, make_uint4(p[0], p[1], p[2], p[3]));
   }
-  for (int q = t; q < 112 * 8; q += kRows) {
-    int n = q >> 3, k0 = (q & 7) * 8;
+  for (int q = t; q < 2 * 112 * 8; q += kRows) {
+    const int part = q / (112 * 8), n = (q >> 3) % 112, k0 = (q & 7) * 8;
     uint32_t p[4];
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       int k = k0 + 2 * h;
-      p[h] = tc::pack2<F16>(w3_elem<F16>(W, k, n), w3_elem<F16>(W, k + 1, n));
+      float v0 = w3_elem<F16>(W, k, n), v1 = w3_elem<F16>(W, k + 1, n);
+      if (part == 0) {
+        v0 = split_hi<F16>(v0);
+        v1 = split_hi<F16>(v1);
+      } else {
+        v0 = k < kN2 ? lo_part<F16>(v0) : 0.f;
+        v1 = k + 1 < kN2 ? lo_part<F16>(v1) : 0.f;
+      }
+      p[h] = tc::pack2<F16>(v0, v1);
     }
-    tc::st_chunk(sB3, n, k0, make_uint4(p[0], p[1], p[2], p[3]));
+    tc::st_chunk(sB3 + part * 14336, n, k0, make_uint4(p[0], p[1], p[2], p[3]));
   }
   load_small(W, small);
 }
@@ -286,11 +312,11 @@ __device__ __forceinline__ void stage_row(const MixArgs& a, const TileInfo& ti, 
   tc::cp_async4(sRep + t, a.irep + ti.a0 + la);
 }
 
-// Thread t's pair vector of tile `ti` copied asynchronously into shared memory.
-__device__ __forceinline__ void stage_pair(const MixArgs& a, const TileInfo& ti, const int* sRow, int t, float4* sNd) {
+// Thread t's pair vector of tile `ti`, loaded into registers (used at the start of the tile).
+__device__ __forceinline__ float4 pair_of(const MixArgs& a, const TileInfo& ti, const int* sRow, int t) {
   const int row = ti.p + t;
   const int la = local_atom(sRow, row);
-  tc::cp_async16(sNd + t, a.nl_d + (size_t)(ti.a0 + la) * a.S + a.sel_off[ti.tj] + (row - sRow[la]));
+  return __ldg(a.nl_d + (size_t)(ti.a0 + la) * a.S + a.sel_off[ti.tj] + (row - sRow[la]));
 }
 
 // 1/r from one reciprocal square root (a few ulp; the row feeds 16-bit operands and FP32
@@ -309,8 +335,8 @@ __device__ __forceinline__ void row_compute(const MixArgs& a, const TileInfo& ti
 }
 
 // h1 = tanh(s_hat W1 + b1) and its 16-bit copy into the A block (K = 32: 25 units, then the
-// two bias ones).
-template <bool F16>
+// two bias ones; with SPLIT the copy again in K slots 32..63 for the remainder of W2).
+template <bool F16, bool SPLIT = false>
 __device__ __forceinline__ void layer1(const float* small, float x, float* h1, unsigned char* sA, int t) {
 #pragma unroll
   for (int k4 = 0; k4 < 7; ++k4) {
@@ -331,6 +357,15 @@ __device__ __forceinline__ void layer1(const float* small, float x, float* h1, u
                             k + 1 < kN1 ? h1[k + 1] : (k + 1 <= kN1 + 1 ? 1.f : 0.f));
     }
     tc::st_chunk(sA, t, k0, make_uint4(p[0], p[1], p[2], p[3]));
+    if (SPLIT) {
+      uint32_t q[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        int k = k0 + 2 * h;
+        q[h] = tc::pack2<F16>(k < kN1 ? h1[k] : 0.f, k + 1 < kN1 ? h1[k + 1] : 0.f);
+      }
+      tc::st_chunk(sA, t, 32 + k0, make_uint4(q[0], q[1], q[2], q[3]));
+    }
   }
 }
 
@@ -386,11 +421,10 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
   unsigned char* sm = align1024(sraw);
   unsigned char* sA = sm;                          // 16 KB operand block (h1, then h2)
   unsigned char* sGt = sm;                         // 32 KB: G^T fp16 (MN-major: [row][feature]), aliases sA after MMA 2
-  unsigned char* sRs = sm + 32768;                 // 8 KB: block-sparse R_hat^T [(atom, c)][row] fp16
-  unsigned char* sB2 = sRs + 8192;                 // 8 KB
-  unsigned char* sB3 = sB2 + 8192;                 // 14 KB
-  float4* sNd = reinterpret_cast<float4*>(sB3 + 14336);  // [kRows] pair vectors of the tile
-  float* small = reinterpret_cast<float*>(sNd + kRows);  // kSmall
+  unsigned char* sRs = sm + 32768;                 // 4 KB: block-sparse R_hat^T [(atom, c)][row] fp16
+  unsigned char* sB2 = sRs + 4096;                 // 8 KB: W2 head | remainder along K
+  unsigned char* sB3 = sB2 + 8192;                 // 2 x 14 KB: W3 head, remainder
+  float* small = reinterpret_cast<float*>(sB3 + 2 * 14336);  // kSmall
   int* sRow = reinterpret_cast<int*>(small + kSmall);    // kMaxAtoms + 1
   int* sWin = sRow + 8;                                  // 32 row offsets (next tile's window)
   __shared__ uint64_t bar;
@@ -432,16 +466,18 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
   // every thread starts the copy of its row's pair vector into shared memory
   if (w == kLocWarp && c0 < c1) locate_tile(a, c0, c0, c1, wk, s_tot, s_tiend, &sti, sRow);
   __syncthreads();
-  if (c0 < c1 && t < sti.nrows) stage_pair(a, sti, sRow, t, sNd);
+  // each thread's pair vector of the next tile is loaded into registers while the current
+  // tile's T product runs (no shared-memory staging)
+  float4 nd = make_float4(0.f, 0.f, 0.f, 1.f);
+  if (c0 < c1 && t < sti.nrows) nd = pair_of(a, sti, sRow, t);
   for (int cur = c0; cur < c1 && ok;) {
     // the R_hat^T operand starts from zero (rows of other atoms stay zero)
     {
       uint4* z = reinterpret_cast<uint4*>(sRs);
-      for (int q = t; q < 8192 / 16; q += kRows) z[q] = make_uint4(0, 0, 0, 0);
+      for (int q = t; q < 4096 / 16; q += kRows) z[q] = make_uint4(0, 0, 0, 0);
     }
     __syncthreads();
     const TileInfo ti = sti;
-    tc::cp_async_wait_all();  // this thread's row, copied during the previous tile
     if (w == kLocWarp && cur + ti.nrows < c1) locate_window(a, cur + ti.nrows, wk, s_tot, sWin);
     // the write-out's facts about this tile's atom slots (from the lookup)
     const int last_la = ti.last_la;
@@ -466,15 +502,15 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     if (valid) {
       f.la = local_atom(sRow, ti.p + t);
       f.atom = ti.a0 + f.la;
-      row_compute(a, ti, sNd[t], winv, f);
+      row_compute(a, ti, nd, winv, f);
     } else {
       f.R[0] = f.R[1] = f.R[2] = f.R[3] = 0.f;
       f.la = 0;
     }
-    layer1<F16>(small, f.R[0], h1, sA, t);
+    layer1<F16, true>(small, f.R[0], h1, sA, t);
     operand_barrier();
     if (t == 0) {
-      tc::mma_kblock(tmem, tc::smem_u32(sA), tc::smem_u32(sB2), tc::idesc_f16(128, 64, F16), false, 2);
+      tc::mma_kblock(tmem, tc::smem_u32(sA), tc::smem_u32(sB2), tc::idesc_f16(128, 64, F16), false, 4);
       tc::mma_commit(&bar);
     }
     mma_sync_wait(&bar, phase, a.err, ok);
@@ -483,6 +519,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     // layer 3 reuses the TMEM columns of layer 2 (already read)
     if (t == 0) {
       tc::mma_kblock(tmem, tc::smem_u32(sA), tc::smem_u32(sB3), tc::idesc_f16(128, 112, F16), false, 4);
+      tc::mma_kblock(tmem, tc::smem_u32(sA), tc::smem_u32(sB3 + 14336), tc::idesc_f16(128, 112, F16), true, 4);
       tc::mma_commit(&bar);
     }
     mma_sync_wait(&bar, phase, a.err, ok);
@@ -513,7 +550,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
       }
       if (valid) {
         const uint32_t kr = (uint32_t)(t & 63);
-        unsigned char* rcol = sRs + (uint32_t)(t >> 6) * 4096u + (kr & 7) * 2;
+        unsigned char* rcol = sRs + (uint32_t)(t >> 6) * 2048u + (kr & 7) * 2;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const int n = f.la * 4 + c;
@@ -525,10 +562,10 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     // T product on the tensor core: D[feature][(slot, c)] over the 128 rows (8 K steps;
     // A = G^T read MN-major, B = R_hat^T K-major)
     if (t == 0) {
-      const uint32_t id = tc::idesc_mn(tc::idesc_f16(128, 32, true), true, false);
+      const uint32_t id = tc::idesc_mn(tc::idesc_f16(128, 4 * kMaxAtoms, true), true, false);
       const uint64_t a0 = tc::sdesc_sw128_mn(tc::smem_u32(sGt), 16384), b0 = tc::sdesc_sw128(tc::smem_u32(sRs));
       for (int k = 0; k < 8; ++k)
-        tc::mma_f16(tmem, tc::sdesc_add(a0, 2048 * k), tc::sdesc_add(b0, (k >> 2) * 4096 + 32 * (k & 3)), id,
+        tc::mma_f16(tmem, tc::sdesc_add(a0, 2048 * k), tc::sdesc_add(b0, (k >> 2) * 2048 + 32 * (k & 3)), id,
                     k > 0 ? 1u : 0u);
       tc::mma_commit(&bar);
     }
@@ -538,13 +575,12 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
       if (w == kLocWarp) locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow, sWin, true);
       __syncthreads();
       const TileInfo nx = sti;
-      if (t < nx.nrows) stage_pair(a, nx, sRow, t, sNd);
+      if (t < nx.nrows) nd = pair_of(a, nx, sRow, t);
     }
     mma_sync_wait(&bar, phase, a.err, ok);
     {
-      float v[32];
+      float v[16];
       tc::tmem_ld16(tl, v);
-      tc::tmem_ld16(tl + 16, v + 16);
       tc::tmem_wait_ld();
 #pragma unroll
       for (int s = 0; s < kMaxAtoms; ++s)
@@ -651,7 +687,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
   unsigned char* sA = sm;                          // 32 KB: h1 / h2 (blk 0), dz3 (blks 0-1), dz2 (blk 0)
   unsigned char* sB2 = sm + 32768;                 // 8 KB
   unsigned char* sB3 = sB2 + 8192;                 // 16 KB (128 rows, backward column order)
-  float4* sdT = reinterpret_cast<float4*>(sB3 + 16384);              // [kMaxAtoms][100]
+  float4* sdT = reinterpret_cast<float4*>(sB3 + 16384);              // [kMaxAtoms][100], paired layout
   float4* sNd = sdT + kMaxAtoms * kN3;                               // [kRows] pair vectors
   int* sNj = reinterpret_cast<int*>(sNd + kRows);                    // [kRows] neighbour index
   int* sRep = sNj + kRows;                                           // [2][kRows] replica, by tile parity
@@ -756,45 +792,61 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
     mma_sync_wait(&bar, phase, a.err, ok);
 
     // layer-3 epilogue over the feature pairs (m, m + 50): G, dR_hat, dG, dz3 -> sA (blk 0:
-    // column m, blk 1: column m + 64), residual dG[m] + dG[m + 50] -> TMEM column 64 + m
+    // column m, blk 1: column m + 64), residual dG[m] + dG[m + 50] -> TMEM column 64 + m.  The
+    // two members of a pair run as packed FP32 pairs against the paired dE/dT layout (entries 2m,
+    // 2m + 1: x, y then z, w of units m and m + 50).  dz3 is stored negated ((t^2 - 1) g instead of
+    // (1 - t^2) g, one instruction less); the layer-2 backward takes the sign back.
     float dR[4] = {0.f, 0.f, 0.f, 0.f};
-    const float4* dTa = sdT + f.la * kN3;
+    {
+      const float4* dTa = sdT + f.la * kN3;
+      const uint64_t m1 = tc::f2(-1.f, -1.f);
+      uint64_t ax = tc::f2(0.f, 0.f), ay = ax, az = ax, aw = ax;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      float za[16], zb[16];
-      tc::tmem_ld16(tl + 16 * c, za);
-      tc::tmem_ld16(tl + 64 + 16 * c, zb);
-      tc::tmem_wait_ld();
-#pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {
+      for (int c = 0; c < 8; ++c) {  // columns 8 c .. 8 c + 7 of each member
+        if (8 * c >= kN2) break;
+        float za[8], zb[8];
+        tc::tmem_ld8(tl + 8 * c, za);
+        tc::tmem_ld8(tl + 64 + 8 * c, zb);
+        tc::tmem_wait_ld();
         float da[8], db[8], r[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          const int m = 16 * c + 8 * hh + u;
+          const int m = 8 * c + u;
           da[u] = db[u] = r[u] = 0.f;
           if (m < kN2) {
-            const float ta = tc::tanh_fast(za[8 * hh + u]);
-            const float tb = tc::tanh_fast(zb[8 * hh + u]);
-            const float Ga = h2[m] + ta, Gb = h2[m] + tb;
-            const float4 pa = dTa[m], pb = dTa[m + kN2];
-            dR[0] = fmaf(pa.x, Ga, fmaf(pb.x, Gb, dR[0]));
-            dR[1] = fmaf(pa.y, Ga, fmaf(pb.y, Gb, dR[1]));
-            dR[2] = fmaf(pa.z, Ga, fmaf(pb.z, Gb, dR[2]));
-            dR[3] = fmaf(pa.w, Ga, fmaf(pb.w, Gb, dR[3]));
-            const float ga = f.R[0] * pa.x + f.R[1] * pa.y + f.R[2] * pa.z + f.R[3] * pa.w;
-            const float gb = f.R[0] * pb.x + f.R[1] * pb.y + f.R[2] * pb.z + f.R[3] * pb.w;
-            da[u] = ga * (1.f - ta * ta);
-            db[u] = gb * (1.f - tb * tb);
-            r[u] = ga + gb;
+            const float ta = tc::tanh_fast(za[u]), tb = tc::tanh_fast(zb[u]);
+            const uint64_t T2 = tc::f2(ta, tb);
+            const uint64_t G2 = tc::f2add(tc::f2(h2[m], h2[m]), T2);
+            const float4 plo = dTa[2 * m], phi = dTa[2 * m + 1];
+            const uint64_t Px = tc::f2(plo.x, plo.y), Py = tc::f2(plo.z, plo.w), Pz = tc::f2(phi.x, phi.y),
+                           Pw = tc::f2(phi.z, phi.w);
+            ax = tc::f2fma(Px, G2, ax);
+            ay = tc::f2fma(Py, G2, ay);
+            az = tc::f2fma(Pz, G2, az);
+            aw = tc::f2fma(Pw, G2, aw);
+            const float ga = fmaf(f.R[3], phi.z, fmaf(f.R[2], phi.x, fmaf(f.R[1], plo.z, f.R[0] * plo.x)));
+            const float gb = fmaf(f.R[3], phi.w, fmaf(f.R[2], phi.y, fmaf(f.R[1], plo.w, f.R[0] * plo.y)));
+            const uint64_t g = tc::f2(ga, gb);
+            const uint64_t dzn = tc::f2mul(g, tc::f2fma(T2, T2, m1));  // -dz3 of (m, m + 50)
+            da[u] = tc::f2lo(dzn);
+            db[u] = tc::f2hi(dzn);
+            r[u] = tc::f2lo(g) + tc::f2hi(g);
           }
         }
-        const int k0 = 16 * c + 8 * hh;
+        const int k0 = 8 * c;
         tc::st_chunk(sA, t, k0, make_uint4(tc::pack2<F16>(da[0], da[1]), tc::pack2<F16>(da[2], da[3]),
                                            tc::pack2<F16>(da[4], da[5]), tc::pack2<F16>(da[6], da[7])));
         tc::st_chunk(sA + 16384, t, k0, make_uint4(tc::pack2<F16>(db[0], db[1]), tc::pack2<F16>(db[2], db[3]),
                                                    tc::pack2<F16>(db[4], db[5]), tc::pack2<F16>(db[6], db[7])));
         tc::tmem_st8(tl + 64 + k0, r);
       }
+      // the last dz3 chunk of each half (columns 56..63 / 120..127) stays zero
+      tc::st_chunk(sA, t, 56, make_uint4(0, 0, 0, 0));
+      tc::st_chunk(sA + 16384, t, 56, make_uint4(0, 0, 0, 0));
+      dR[0] = tc::f2lo(ax) + tc::f2hi(ax);
+      dR[1] = tc::f2lo(ay) + tc::f2hi(ay);
+      dR[2] = tc::f2lo(az) + tc::f2hi(az);
+      dR[3] = tc::f2lo(aw) + tc::f2hi(aw);
     }
     tc::tmem_wait_st();
     operand_barrier();
@@ -836,7 +888,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
         const int m = 16 * c + u;
         d2[u] = 0.f;
         if (m < kN2) {
-          const float g2 = z[u] + rr[u];
+          const float g2 = rr[u] - z[u];  // dh2' comes out negated (dz3 was stored negated)
           const float t2 = h2[m] - h1[m % kN1];
           d2[u] = g2 * (1.f - t2 * t2);
           dh1[m % kN1] += g2;
@@ -1103,9 +1155,10 @@ __global__ void __launch_bounds__(32 * kDescWarps) k_mix_descriptor(int N, int n
   }
 }
 
-// dT[c][a] = (1/S) (sum_b dD[a][b] T[c][b] + [a < 16] sum_a' dD[a'][a] T[c][a']), stored [N][100]
-// float4; dD (dE/dD from the fitting kernel) is fp16 and T is stored feature-major ([N][100]
-// float4 of the four components).
+// dT[c][a] = (1/S) (sum_b dD[a][b] T[c][b] + [a < 16] sum_a' dD[a'][a] T[c][a']), stored per atom
+// as 100 float4 paired for the embedding backward: entries 2m = (x_m, x_m+50, y_m, y_m+50) and
+// 2m + 1 = (z_m, z_m+50, w_m, w_m+50) for m < 50.  dD (dE/dD from the fitting kernel) is fp16 and
+// T is stored feature-major ([N][100] float4 of the four components).
 // One warp per atom at a time: the atom's T and dD are copied into a per-warp double buffer by
 // cp.async one atom ahead, so the copies of the next atom overlap this one's arithmetic.  The
 // second term's 64 outputs (c, a < 16) take lanes (a, half of the a' range) and one shuffle.
@@ -1152,30 +1205,44 @@ __global__ void __launch_bounds__(32 * kDtWarps) k_mix_dT(int N, float invS, con
 #pragma unroll
       for (int c = 0; c < 4; ++c) u[c] += __shfl_xor_sync(0xffffffffu, u[c], 16);
     }
-    // first term: lane -> features a = lane, lane + 32, ...; T[b] for b < 16 held in registers
+    // first term: lane -> pairs m = lane, lane + 32 (units m and m + 50); T[b] for b < 16 held
+    // in registers
     float4 tb[kM2];
 #pragma unroll
     for (int b = 0; b < kM2; ++b) tb[b] = T[b];
-    for (int a = lane; a < kN3; a += 32) {
-      float v[4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) v[c] = (a < kM2) ? u[c] : 0.f;
-      const uint4* Drow = reinterpret_cast<const uint4*>(D + a * kM2);
+    for (int pp = 0; pp < 2; ++pp) {
+      const int m = lane + 32 * pp;
+      float ua[4];  // second term of unit m < 16, held by lane m
 #pragma unroll
-      for (int hc = 0; hc < 2; ++hc) {
-        const uint4 raw = Drow[hc];
-        const uint32_t p[4] = {raw.x, raw.y, raw.z, raw.w};
+      for (int c = 0; c < 4; ++c) ua[c] = __shfl_sync(0xffffffffu, u[c], m & 15);
+      if (m < kN2) {
+        float v[2][4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float2 d2 = __half22float2(*reinterpret_cast<const __half2*>(&p[e]));
-          const float4 t0 = tb[8 * hc + 2 * e], t1 = tb[8 * hc + 2 * e + 1];
-          v[0] = fmaf(d2.x, t0.x, v[0]); v[1] = fmaf(d2.x, t0.y, v[1]);
-          v[2] = fmaf(d2.x, t0.z, v[2]); v[3] = fmaf(d2.x, t0.w, v[3]);
-          v[0] = fmaf(d2.y, t1.x, v[0]); v[1] = fmaf(d2.y, t1.y, v[1]);
-          v[2] = fmaf(d2.y, t1.z, v[2]); v[3] = fmaf(d2.y, t1.w, v[3]);
+        for (int e2 = 0; e2 < 2; ++e2) {
+          const int a = m + kN2 * e2;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) v[e2][c] = (a < kM2) ? ua[c] : 0.f;
+          const uint4* Drow = reinterpret_cast<const uint4*>(D + a * kM2);
+#pragma unroll
+          for (int hc = 0; hc < 2; ++hc) {
+            const uint4 raw = Drow[hc];
+            const uint32_t q[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float2 d2 = __half22float2(*reinterpret_cast<const __half2*>(&q[e]));
+              const float4 t0 = tb[8 * hc + 2 * e], t1 = tb[8 * hc + 2 * e + 1];
+              v[e2][0] = fmaf(d2.x, t0.x, v[e2][0]); v[e2][1] = fmaf(d2.x, t0.y, v[e2][1]);
+              v[e2][2] = fmaf(d2.x, t0.z, v[e2][2]); v[e2][3] = fmaf(d2.x, t0.w, v[e2][3]);
+              v[e2][0] = fmaf(d2.y, t1.x, v[e2][0]); v[e2][1] = fmaf(d2.y, t1.y, v[e2][1]);
+              v[e2][2] = fmaf(d2.y, t1.z, v[e2][2]); v[e2][3] = fmaf(d2.y, t1.w, v[e2][3]);
+            }
+          }
         }
+        float4* o = dT + (size_t)i * kN3 + 2 * m;
+        o[0] = make_float4(v[0][0] * invS, v[1][0] * invS, v[0][1] * invS, v[1][1] * invS);
+        o[1] = make_float4(v[0][2] * invS, v[1][2] * invS, v[0][3] * invS, v[1][3] * invS);
       }
-      dT[(size_t)i * kN3 + a] = make_float4(v[0] * invS, v[1] * invS, v[2] * invS, v[3] * invS);
     }
     __syncwarp();  // every lane is done with this buffer before it is refilled
   }
@@ -1201,7 +1268,7 @@ MixArgs make_mix_args(Model* m, int N) {
 }
 
 // (+ 160: sRow (8 ints) and sWin (32 ints); + 1024: alignment of the operand blocks)
-constexpr size_t kFwdSmem = 32768 + 8192 + 8192 + 14336 + kRows * 16 + kSmall * 4 + 160 + 1024;
+constexpr size_t kFwdSmem = 32768 + 4096 + 8192 + 2 * 14336 + kSmall * 4 + 160 + 1024;
 constexpr size_t kBwdSmem =
     32768 + 8192 + 16384 + kMaxAtoms * kN3 * 16 + kRows * (16 + 4 + 8) + kSmall * 4 + 160 + 1024;
 
