@@ -64,6 +64,8 @@ def lib():
             L.oracle_md_harmonic.argtypes = [_I, _P, _P, _P, _D, _D, _I, _P]
             L.oracle_model_ntypes.argtypes = [_P]
             L.oracle_env_stats.argtypes = [_P, _I, _P, _P, _P, _P]
+            L.oracle_tabulate.argtypes = [_P, _D, _D, _I]
+            L.oracle_emb_eval.argtypes = [_P, _I, _I, _P, _I, _P, _P, _P]
             _lib = L
     return _lib
 
@@ -172,6 +174,20 @@ class Model:
         out = np.zeros((self.ntypes, 5))
         _check(lib().oracle_env_stats(self.h, len(types), _ptr(coords), _ptr(types), _ptr(box), _ptr(out)))
         return out
+
+    def tabulate(self, x0: float, x1: float, n: int) -> None:
+        """Replace every embedding net by its quintic table on n uniform intervals of [x0, x1]
+        (the compressed model); n = 0 goes back to the networks."""
+        _check(lib().oracle_tabulate(self.h, float(x0), float(x1), int(n)))
+
+    def emb_eval(self, pair: int, x, tabulated: bool = False):
+        """Embedding output of pair ti * ntypes + tj at inputs x: (G, G', G''), each [len(x), 100],
+        from the network or from the table."""
+        x = _f64(np.atleast_1d(x))
+        g, g1, g2 = (np.zeros((len(x), 100)) for _ in range(3))
+        _check(lib().oracle_emb_eval(self.h, int(pair), len(x), _ptr(x), int(tabulated), _ptr(g), _ptr(g1),
+                                     _ptr(g2)))
+        return g, g1, g2
 
     def dir_deriv(self, coords, types, box, w):
         coords, types, box, w = _f64(coords), _i32(types), _f64(box), _f64(w)

@@ -65,8 +65,27 @@ inline Dual sqrt(Dual a) { double s = std::sqrt(a.v); return {s, a.d / (2.0 * s)
 inline Dual tanh(Dual a) { double t = std::tanh(a.v); return {t, a.d * (1.0 - t * t)}; }
 inline Dual cos(Dual a) { return {std::cos(a.v), -a.d * std::sin(a.v)}; }
 inline Dual sin(Dual a) { return {std::sin(a.v), a.d * std::cos(a.v)}; }
+// Second-order jets along one input: value, first and second derivative (chain rule written
+// out); used to evaluate the embedding net and its first two derivatives at table nodes.
+struct Jet2 {
+  double v, d, dd;
+  Jet2() : v(0), d(0), dd(0) {}
+  Jet2(double x) : v(x), d(0), dd(0) {}
+  Jet2(double x, double y, double z) : v(x), d(y), dd(z) {}
+};
+inline Jet2 operator+(Jet2 a, Jet2 b) { return {a.v + b.v, a.d + b.d, a.dd + b.dd}; }
+inline Jet2 operator-(Jet2 a, Jet2 b) { return {a.v - b.v, a.d - b.d, a.dd - b.dd}; }
+inline Jet2 operator*(Jet2 a, Jet2 b) {
+  return {a.v * b.v, a.d * b.v + a.v * b.d, a.dd * b.v + 2.0 * a.d * b.d + a.v * b.dd};
+}
+inline Jet2& operator+=(Jet2& a, Jet2 b) { a = a + b; return a; }
+inline Jet2 tanh(Jet2 a) {
+  const double t = std::tanh(a.v), t1 = 1.0 - t * t;  // tanh' = 1 - t^2, tanh'' = -2 t (1 - t^2)
+  return {t, t1 * a.d, t1 * a.dd - 2.0 * t * t1 * a.d * a.d};
+}
 inline double val(double a) { return a; }
 inline double val(Dual a) { return a.v; }
+inline double val(Jet2 a) { return a.v; }
 using std::sqrt;
 using std::tanh;
 using std::cos;
@@ -88,6 +107,12 @@ struct Model {
   std::vector<size_t> emb_off;     // [nt*nt]
   std::vector<size_t> fit_off;     // [nt]
   size_t ebias_off = 0, ntheta = 0;
+  // Tabulated embedding (compressed model): when tab_n > 0 every embedding net is replaced by
+  // a piecewise quintic in its input on tab_n uniform intervals of width tab_h from tab_x0,
+  // coefficients tab[((pair * tab_n + i) * n3 + a) * 6 + p] of u^p, u = (x - x_i) / tab_h.
+  int tab_n = 0;
+  double tab_x0 = 0.0, tab_h = 0.0;
+  std::vector<double> tab;
   size_t emb_size() const { const Sizes& s = sz; return (size_t)s.n1 * 2 + (size_t)s.n1 * s.n2 + s.n2 + (size_t)s.n2 * s.n3 + s.n3; }
   size_t fit_size() const { const Sizes& s = sz; return (size_t)s.n3 * s.m2 * s.f1 + s.f1 + (size_t)s.f1 * s.f2 + s.f2 + (size_t)s.f2 * s.f3 + s.f3 + s.f3 + 1; }
 };
@@ -147,6 +172,7 @@ Model<T> cast_model(const Model<double>& m) {
   o.ntypes = m.ntypes; o.switch_kind = m.switch_kind; o.rc = m.rc; o.rs = m.rs; o.sz = m.sz;
   o.sel = m.sel; o.sel_off = m.sel_off; o.S = m.S; o.davg = m.davg; o.dstd = m.dstd;
   o.emb_off = m.emb_off; o.fit_off = m.fit_off; o.ebias_off = m.ebias_off; o.ntheta = m.ntheta;
+  o.tab_n = m.tab_n; o.tab_x0 = m.tab_x0; o.tab_h = m.tab_h; o.tab = m.tab;
   o.theta.resize(m.theta.size());
   for (size_t i = 0; i < m.theta.size(); ++i) o.theta[i] = T(m.theta[i]);
   return o;
@@ -414,6 +440,63 @@ T emb_backward(const T* p, const Sizes& s, const std::vector<T>& h1, const std::
   return dx;
 }
 
+// Tabulated embedding of pair `pair` at input x: G[a] and dG[a]/dx from the quintic of the
+// interval holding x (inputs below the first node or above the last use the edge interval's
+// polynomial).
+template <class T, class M>
+void tab_eval(const M& m, int pair, T x, std::vector<T>& g, std::vector<T>* dg) {
+  const int n3 = m.sz.n3;
+  g.resize(n3);
+  if (dg) dg->resize(n3);
+  int i = (int)std::floor((val(x) - m.tab_x0) / m.tab_h);
+  i = std::min(std::max(i, 0), m.tab_n - 1);
+  const T u = (x - T(m.tab_x0 + i * m.tab_h)) * T(1.0 / m.tab_h);
+  for (int a = 0; a < n3; ++a) {
+    const double* c = &m.tab[(((size_t)pair * m.tab_n + i) * n3 + a) * 6];
+    g[a] = T(c[0]) + u * (T(c[1]) + u * (T(c[2]) + u * (T(c[3]) + u * (T(c[4]) + u * T(c[5])))));
+    if (dg)
+      (*dg)[a] = (T(c[1]) + u * (T(2.0 * c[2]) + u * (T(3.0 * c[3]) + u * (T(4.0 * c[4]) + u * T(5.0 * c[5]))))) *
+                 T(1.0 / m.tab_h);
+  }
+}
+
+// Build the table: at every node x_i = x0 + i h the embedding net's value, first and second
+// derivative (second-order jets through emb_forward); on each interval the quintic in u with
+// those six end conditions (value, h * first, h^2 * second derivative at u = 0 and u = 1).
+void build_table(Model<double>& m, double x0, double x1, int n) {
+  const Sizes& s = m.sz;
+  const int nt = m.ntypes, n3 = s.n3;
+  m.tab_n = n; m.tab_x0 = x0; m.tab_h = (x1 - x0) / n;
+  const double h = m.tab_h;
+  m.tab.assign((size_t)nt * nt * n * n3 * 6, 0.0);
+  std::vector<Jet2> w(m.emb_size());
+  for (int pair = 0; pair < nt * nt; ++pair) {
+    for (size_t q = 0; q < w.size(); ++q) w[q] = Jet2(m.theta[m.emb_off[pair] + q]);
+    std::vector<double> f((size_t)(n + 1) * n3), f1(f.size()), f2(f.size());
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i <= n; ++i) {
+      std::vector<Jet2> a1, a2, a3, a4, g;
+      emb_forward(w.data(), s, Jet2(x0 + i * h, 1.0, 0.0), a1, a2, a3, a4, g);
+      for (int a = 0; a < n3; ++a) {
+        f[(size_t)i * n3 + a] = g[a].v;
+        f1[(size_t)i * n3 + a] = g[a].d;
+        f2[(size_t)i * n3 + a] = g[a].dd;
+      }
+    }
+    for (int i = 0; i < n; ++i)
+      for (int a = 0; a < n3; ++a) {
+        const size_t l = (size_t)i * n3 + a, r = l + n3;
+        const double c0 = f[l], c1 = h * f1[l], c2 = 0.5 * h * h * f2[l];
+        const double A = f[r] - (c0 + c1 + c2), B = h * f1[r] - (c1 + 2.0 * c2), C = h * h * f2[r] - 2.0 * c2;
+        double* c = &m.tab[(((size_t)pair * n + i) * n3 + a) * 6];
+        c[0] = c0; c[1] = c1; c[2] = c2;
+        c[3] = 10.0 * A - 4.0 * B + 0.5 * C;
+        c[4] = -15.0 * A + 7.0 * B - C;
+        c[5] = 6.0 * A - 3.0 * B + 0.5 * C;
+      }
+  }
+}
+
 // Fitting net forward + reverse: returns E_i (without e_bias) and dE/dD.
 template <class T>
 T fit_forward_backward(const T* p, const Sizes& s, const std::vector<T>& D, std::vector<T>* dD) {
@@ -516,7 +599,8 @@ void evaluate(const Model<T>& m, int N, const T* x, const int* types, const doub
         for (int a = 0; a < 3; ++a) dvec[(size_t)k * 3 + a] = d[a];
         rr[k] = r;
         const int tj = types[j];
-        emb_forward(&m.theta[m.emb_off[ti * nt + tj]], s, R[(size_t)k * 4], h1[k], t2[k], h2[k], t3[k], G[k]);
+        if (m.tab_n > 0) tab_eval(m, ti * nt + tj, R[(size_t)k * 4], G[k], &t3[k]);  // t3: dG/dx
+        else emb_forward(&m.theta[m.emb_off[ti * nt + tj]], s, R[(size_t)k * 4], h1[k], t2[k], h2[k], t3[k], G[k]);
       }
       // T = (1/S) R^T G over all S slots.  A padded slot is the row of an absent
       // neighbour, R_tilde = 0, normalised like every row: R_hat = -davg/dstd, with
@@ -532,7 +616,8 @@ void evaluate(const Model<T>& m, int N, const T* x, const int* types, const doub
         for (int k = m.sel_off[tj]; k < m.sel_off[tj + 1]; ++k) {
           const bool pad = nl.j[(size_t)i * nl.S + k] < 0;
           if (pad && !have_pad) {
-            emb_forward(&m.theta[m.emb_off[ti * nt + tj]], s, Rp[0], ph1, pt2, ph2, pt3, Gp);
+            if (m.tab_n > 0) tab_eval(m, ti * nt + tj, Rp[0], Gp, (std::vector<T>*)nullptr);
+            else emb_forward(&m.theta[m.emb_off[ti * nt + tj]], s, Rp[0], ph1, pt2, ph2, pt3, Gp);
             have_pad = true;
           }
           const T* Rk = pad ? Rp : &R[(size_t)k * 4];
@@ -582,7 +667,11 @@ void evaluate(const Model<T>& m, int N, const T* x, const int* types, const doub
           for (int c = 0; c < 4; ++c) acc += R[(size_t)k * 4 + c] * dT[(size_t)c * n3 + a];
           dG[a] = acc / T((double)S);
         }
-        dR[0] += emb_backward(&m.theta[m.emb_off[ti * nt + tj]], s, h1[k], t2[k], t3[k], dG);
+        if (m.tab_n > 0) {
+          for (int a = 0; a < n3; ++a) dR[0] += dG[a] * t3[k][a];
+        } else {
+          dR[0] += emb_backward(&m.theta[m.emb_off[ti * nt + tj]], s, h1[k], t2[k], t3[k], dG);
+        }
         // undo normalisation, then the analytic Jacobian of (s, s d/r) w.r.t. d
         for (int c = 0; c < 4; ++c) dR[c] = dR[c] / T(m.dstd[ti * 4 + c]);
         T r = rr[k];
@@ -736,6 +825,46 @@ int oracle_compute(const void* h, int N, const double* x, const int* types, cons
   Inter in{interT, interD, interdD};
   evaluate<double>(m, N, xw.data(), types, L, nl, centre_mask, want_force != 0, energy, atom_energy,
                    force, virial, &in);
+  return 0;
+}
+
+// Tabulate every embedding net of the model (compressed model): n uniform intervals on
+// [x0, x1] (n = 0 goes back to the networks).  Returns 1 for bad arguments.
+int oracle_tabulate(void* h, double x0, double x1, int n) {
+  Model<double>& m = *static_cast<Model<double>*>(h);
+  if (n < 0 || (n > 0 && !(x1 > x0))) return 1;
+  if (n == 0) { m.tab_n = 0; m.tab.clear(); return 0; }
+  build_table(m, x0, x1, n);
+  return 0;
+}
+
+// The embedding output of pair (ti, tj) at nx inputs x: G [nx][n3] and its first and second
+// derivatives, from the network (second-order jets, tabulated = 0) or from the table
+// (tabulated = 1; second derivative of the quintic).
+int oracle_emb_eval(const void* h, int pair, int nx, const double* x, int tabulated, double* g, double* g1,
+                    double* g2) {
+  const Model<double>& m = *static_cast<const Model<double>*>(h);
+  const int n3 = m.sz.n3;
+  if (pair < 0 || pair >= m.ntypes * m.ntypes || (tabulated && m.tab_n == 0)) return 1;
+  std::vector<Jet2> w(m.emb_size());
+  for (size_t q = 0; q < w.size(); ++q) w[q] = Jet2(m.theta[m.emb_off[pair] + q]);
+  for (int k = 0; k < nx; ++k) {
+    if (tabulated) {
+      std::vector<Jet2> gj;
+      Model<Jet2> mj;  // the table in jet arithmetic: second derivative of the quintic
+      mj.sz = m.sz; mj.tab_n = m.tab_n; mj.tab_x0 = m.tab_x0; mj.tab_h = m.tab_h; mj.tab = m.tab;
+      tab_eval(mj, pair, Jet2(x[k], 1.0, 0.0), gj, (std::vector<Jet2>*)nullptr);
+      for (int a = 0; a < n3; ++a) {
+        g[(size_t)k * n3 + a] = gj[a].v; g1[(size_t)k * n3 + a] = gj[a].d; g2[(size_t)k * n3 + a] = gj[a].dd;
+      }
+    } else {
+      std::vector<Jet2> a1, a2, a3, a4, gj;
+      emb_forward(w.data(), m.sz, Jet2(x[k], 1.0, 0.0), a1, a2, a3, a4, gj);
+      for (int a = 0; a < n3; ++a) {
+        g[(size_t)k * n3 + a] = gj[a].v; g1[(size_t)k * n3 + a] = gj[a].d; g2[(size_t)k * n3 + a] = gj[a].dd;
+      }
+    }
+  }
   return 0;
 }
 

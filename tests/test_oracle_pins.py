@@ -598,3 +598,85 @@ def test_golden_water64_regression(water_oracle, water64):
             np.testing.assert_allclose(r["forces"][int(tok[1])], [float(v) for v in tok[2:]], rtol=1e-10, atol=1e-16)
         elif tok[0] == "virial":
             np.testing.assert_allclose(r["virial"].ravel(), [float(v) for v in tok[1:]], rtol=1e-10, atol=1e-16)
+
+
+# ----------------------------------------------------------------- tabulated embedding
+def _table_range(w):
+    """Input range of the tables: from the padded value (a neighbour at r_c) to the input of a
+    neighbour at 0.5 A, with a margin."""
+    x0 = min(-w.davg[t][0] / w.dstd[t][0] for t in range(w.ntypes)) - 0.05
+    x1 = max((2.0 - w.davg[t][0]) / w.dstd[t][0] for t in range(w.ntypes)) + 0.05
+    return x0, x1
+
+
+def test_embedding_jets_match_central_differences():
+    # the first and second derivatives that feed the table nodes against differences of G
+    w = _normalised_water()
+    m = oracle.Model(w.to_blob())
+    x = np.array([-0.3, 0.7, 2.9, 6.1])
+    h = 1e-4
+    g, g1, g2 = m.emb_eval(1, x)
+    gp, _, _ = m.emb_eval(1, x + h)
+    gm, _, _ = m.emb_eval(1, x - h)
+    np.testing.assert_allclose(g1, (gp - gm) / (2 * h), rtol=1e-6, atol=1e-9)
+    np.testing.assert_allclose(g2, (gp - 2 * g + gm) / (h * h), rtol=1e-4, atol=1e-5)
+
+
+def test_table_reproduces_net_at_nodes_and_is_c2():
+    w = _normalised_water()
+    m = oracle.Model(w.to_blob())
+    x0, x1 = _table_range(w)
+    n = 128
+    m.tabulate(x0, x1, n)
+    step = (x1 - x0) / n
+    nodes = x0 + step * np.array([1, 17, 64, 127])
+    for pair in range(4):
+        g, g1, g2 = m.emb_eval(pair, nodes)
+        t, t1, t2 = m.emb_eval(pair, nodes, tabulated=True)
+        np.testing.assert_allclose(t, g, rtol=1e-13, atol=1e-14)
+        np.testing.assert_allclose(t1, g1, rtol=1e-10, atol=1e-11)
+        np.testing.assert_allclose(t2, g2, rtol=1e-8, atol=1e-9)
+        # value, slope and curvature agree from both sides of a node
+        eps = 1e-9 * step
+        l, l1, l2 = m.emb_eval(pair, nodes - eps, tabulated=True)
+        r, r1, r2 = m.emb_eval(pair, nodes + eps, tabulated=True)
+        np.testing.assert_allclose(l, r, atol=1e-11)
+        np.testing.assert_allclose(l1, r1, rtol=1e-7, atol=1e-9)
+        np.testing.assert_allclose(l2, r2, rtol=1e-5, atol=1e-7)
+
+
+def test_table_error_falls_at_sixth_order():
+    # the quintic Hermite interpolant's error is O(h^6): halving the interval divides it by ~64
+    w = _normalised_water()
+    m = oracle.Model(w.to_blob())
+    x0, x1 = _table_range(w)
+    xs = np.linspace(x0, x1, 3001)
+    g, _, _ = m.emb_eval(2, xs)
+    err = []
+    for n in (64, 128):
+        m.tabulate(x0, x1, n)
+        t, _, _ = m.emb_eval(2, xs, tabulated=True)
+        err.append(np.abs(t - g).max())
+    assert err[0] < 1e-6
+    assert 40.0 < err[0] / err[1] < 90.0, err
+
+
+def test_tabulated_model_forces_and_energy():
+    w = _normalised_water()
+    m = oracle.Model(w.to_blob())
+    s = synth.water_box(16, 4)
+    e_net = m.compute(s.coords, s.types, s.box)
+    m.tabulate(*_table_range(w), 256)
+    r = m.compute(s.coords, s.types, s.box)
+    # the table changes E by no more than its interpolation error carried through the descriptor
+    assert abs(r["energy"] - e_net["energy"]) / s.natoms < 1e-8
+    assert np.abs(r["forces"] - e_net["forces"]).max() < 1e-7
+    # forces are the gradient of the tabulated energy
+    h = 1e-5
+    rng = np.random.default_rng(8)
+    for i in rng.choice(s.natoms, 4, replace=False):
+        for a in range(3):
+            xp = s.coords.copy(); xp[i, a] += h
+            xm = s.coords.copy(); xm[i, a] -= h
+            fd = -(m.energy(xp, s.types, s.box) - m.energy(xm, s.types, s.box)) / (2 * h)
+            assert fd == pytest.approx(r["forces"][i, a], rel=1e-6, abs=1e-8)
