@@ -412,12 +412,18 @@ def run_mine(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
-def md_rate(w, s, v0, prec, stream, steps, dt=DT_FS, warm=3):
-    """NVE MD throughput of one box (graph replay); returns (ms per step, model kept open)."""
+TAB_INTERVALS = 256
+
+
+def md_rate(w, s, v0, prec, stream, steps, dt=DT_FS, warm=3, tabulate=0):
+    """NVE MD throughput of one box (graph replay); returns (ms per step, model kept open).
+    tabulate > 0: the embedding nets replaced by tables of that many intervals (dp_tabulate)."""
     import torch
     import paper_2410_22867_gb300 as dp
     with torch.cuda.stream(stream):
         m = dp.DPModel(w, prec, max_atoms=s.natoms, skin=2.0, stream=stream)
+        if tabulate:
+            m.tabulate(tabulate)
         x = torch.tensor(s.coords, device="cuda")
         v = torch.tensor(v0, device="cuda")
         t = torch.tensor(s.types, device="cuda")
@@ -484,6 +490,21 @@ def ladder(args, stream, alu):
             m.close()
             res["mix_fp16_dt1fs"] = {"value": s.natoms / (ms * 1e-3), "unit": "atom-steps/s", "ms_per_step": ms,
                                      "ns_per_day_1fs": (1e3 / ms) * 1.0 * 86400 * 1e-6, "steps": args.ladder_steps}
+        # the compressed model: embedding nets replaced by quintic tables (dp_tabulate)
+        for prec in ("fp32", "mix_fp16"):
+            steps = min(args.ladder_steps, args.water_steps or args.ladder_steps) if wl == "water12k" \
+                else args.ladder_steps
+            ms, m = md_rate(w, s, v0, prec, stream, steps, tabulate=TAB_INTERVALS)
+            ph = m.phase_times(3)
+            kern = kernel_times(ph)
+            with torch.cuda.stream(stream):
+                r = m.compute(x, t, s.box)
+            res[prec + "_tabulated"] = {"value": s.natoms / (ms * 1e-3), "unit": "atom-steps/s", "ms_per_step": ms,
+                                        "steps": steps, "ns_per_day_0.5fs": (1e3 / ms) * 0.5 * 86400 * 1e-6,
+                                        "intervals": TAB_INTERVALS,
+                                        "kernels_ms": {k: round(v, 4) for k, v in kern.items()},
+                                        "error_vs_fp64_gpu": force_errors(r, ref)}
+            m.close()
         out[wl] = {"workload": WORKLOADS[wl], **res}
     return out
 
@@ -507,14 +528,17 @@ def normalised_errors(stream):
         ref = None
         res = {}
         with torch.cuda.stream(stream):
-            for prec in ("fp64", "fp32", "mix_bf16", "mix_fp16"):
+            for prec, tab in (("fp64", 0), ("fp32", 0), ("mix_bf16", 0), ("mix_fp16", 0), ("fp64", TAB_INTERVALS),
+                              ("fp32", TAB_INTERVALS), ("mix_fp16", TAB_INTERVALS)):
                 m = dp.DPModel(w, prec, max_atoms=s.natoms, stream=stream)
+                if tab:
+                    m.tabulate(tab)
                 r = m.compute(x, t, s.box)
-                if prec == "fp64":
+                if prec == "fp64" and not tab:
                     ref = {k: v.clone() for k, v in r.items()}
                     res["fp64_force_rms_eV_per_A"] = float(torch.sqrt((ref["forces"] ** 2).mean()).item())
                 else:
-                    res[prec] = force_errors(r, ref)
+                    res[prec + ("_tabulated" if tab else "")] = force_errors(r, ref)
                 m.close()
         out[wl] = res
     return out

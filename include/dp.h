@@ -29,10 +29,10 @@
  *    (off-diagonal entries must be 0, else DP_ERR_UNSUPPORTED).
  *  - Atom arrays are in the caller's order; the library sorts atoms by type
  *    internally and un-permutes every output.
- *  - No call allocates device memory after dp_create: all buffers are sized
- *    there from max_atoms and max_replicas (preallocated memory, Section
- *    III-B1 "allocated in the initial phase").  Larger inputs return
- *    DP_ERR_CAPACITY.
+ *  - No call allocates device memory after dp_create (except dp_tabulate, a set-up
+ *    call that allocates its tables): all buffers are sized there from max_atoms
+ *    and max_replicas (preallocated memory, Section III-B1 "allocated in the
+ *    initial phase").  Larger inputs return DP_ERR_CAPACITY.
  */
 #ifndef DP_GB300_H
 #define DP_GB300_H
@@ -187,6 +187,23 @@ dp_status dp_autotune(dp_model* m, int repeats, int* grids);
 dp_status dp_param_grad(dp_model* m, int natoms, const double* coords, const int* types,
                         const double* box, double E0, const double* F0, double cE, double cF,
                         double* grad, double* loss);
+
+/*
+ * dp_tabulate -- replace every embedding net by its table (the compressed model of Section
+ * II-A): each of the 100 outputs of each net (ti, tj) becomes a piecewise quintic in the net's
+ * input s_hat on n_intervals uniform intervals of [x_min, x_max], matching the net's value,
+ * first and second derivative at both ends of every interval (C2; the error falls as h^6 with
+ * the interval width h).  Inputs outside [x_min, x_max] use the edge interval's polynomial, so
+ * the range should cover the normalised input of a neighbour at r_c (-davg/dstd) up to that of
+ * the closest approach expected.  Forward and force backward then evaluate the table instead
+ * of the net, in every precision (mixed precisions keep the 16-bit fitting net and T product).
+ * n_intervals = 0 goes back to the nets.  The tables are built on the device in FP64 from the
+ * current parameters (rebuilt by dp_set_params) and kept in FP64 and FP32.  Unlike the other
+ * calls this one allocates device memory (the tables: 36 n bytes per output and pair).  Drops
+ * captured MD graphs; synchronous.  dp_param_grad returns DP_ERR_UNSUPPORTED while a table is
+ * in use.  Errors: DP_ERR_ARG (n_intervals < 0 or > 2^20, x_min >= x_max), DP_ERR_OOM, DP_ERR_CUDA.
+ */
+dp_status dp_tabulate(dp_model* m, double x_min, double x_max, int n_intervals);
 
 /* Number of parameters in theta (the length of dp_param_grad's grad). */
 long long dp_ntheta(const dp_model* m);

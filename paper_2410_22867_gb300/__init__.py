@@ -32,7 +32,7 @@ STATUS = {0: "DP_OK", 1: "DP_ERR_ARG", 2: "DP_ERR_CUDA", 3: "DP_ERR_OOM", 4: "DP
 EXPORTS = ("dp_create", "dp_compute", "dp_compute_batch", "dp_verlet_step", "dp_md_run_batch", "dp_param_grad",
            "dp_ntheta", "dp_get_nlist", "dp_phase_times", "dp_kernel_launches", "dp_sync", "dp_last_error",
            "dp_destroy", "dp_version", "dp_selftest", "dp_selftest_noalloc", "dp_set_params", "dp_autotune",
-           "dp_wait_selftest", "dp_measure_peak")
+           "dp_wait_selftest", "dp_measure_peak", "dp_tabulate")
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -90,10 +90,11 @@ def lib():
             L.dp_autotune.argtypes = [_P, _I, _P]
             L.dp_wait_selftest.argtypes = [ctypes.c_uint]
             L.dp_measure_peak.argtypes = [_I, _P]
+            L.dp_tabulate.argtypes = [_P, _D, _D, _I]
             for name in ("dp_create", "dp_compute", "dp_compute_batch", "dp_verlet_step", "dp_md_run_batch",
                          "dp_param_grad", "dp_get_nlist", "dp_phase_times", "dp_sync", "dp_selftest",
                          "dp_selftest_noalloc", "dp_set_params", "dp_autotune", "dp_wait_selftest",
-                         "dp_measure_peak"):
+                         "dp_measure_peak", "dp_tabulate"):
                 getattr(L, name).restype = _I
             _lib = L
     return _lib
@@ -290,6 +291,19 @@ class DPModel:
         ms = (ctypes.c_float * 8)()
         self._check(lib().dp_phase_times(self.h, int(repeats), ctypes.cast(ms, _P)))
         return list(ms)[:7]
+
+    def tabulate(self, n_intervals: int = 256, x_min: float | None = None, x_max: float | None = None):
+        """dp_tabulate: replace the embedding nets by their quintic tables (the compressed model).
+        The default range runs from the normalised input of a neighbour at r_c (-davg/dstd) to that
+        of a neighbour at 0.5 A, over all centre types, with a margin of 0.05; n_intervals = 0 goes
+        back to the nets.  Returns (x_min, x_max, n_intervals)."""
+        w = self.weights
+        if x_min is None:
+            x_min = min(-w.davg[t][0] / w.dstd[t][0] for t in range(w.ntypes)) - 0.05
+        if x_max is None:
+            x_max = max((2.0 - w.davg[t][0]) / w.dstd[t][0] for t in range(w.ntypes)) + 0.05
+        self._check(lib().dp_tabulate(self.h, float(x_min), float(x_max), int(n_intervals)))
+        return float(x_min), float(x_max), int(n_intervals)
 
     def autotune(self, repeats: int = 3):
         """dp_autotune: choose the launch grids of the mixed kernels on the current state;

@@ -255,7 +255,7 @@ unsigned long long tune_key(const Model* m, int N) {
   unsigned long long k = 1469598103934665603ull;
   auto mix = [&](unsigned long long v) { k = (k ^ v) * 1099511628211ull; };
   mix((unsigned long long)m->prec); mix((unsigned long long)N); mix((unsigned long long)m->nrep);
-  mix((unsigned long long)m->ntypes); mix((unsigned long long)num_sms());
+  mix((unsigned long long)m->ntypes); mix((unsigned long long)num_sms()); mix((unsigned long long)m->tab_n);
   return k == 0 ? 1 : k;
 }
 
@@ -638,7 +638,21 @@ dp_status dp_set_params(dp_model* h, const double* theta, long long ntheta) {
   m->theta_host.assign(theta, theta + ntheta);
   DP_TRY(upload_weights(m));
   DP_CUDA_TRY(m, cudaDeviceSynchronize());
+  if (m->tab_n > 0) DP_TRY(launch_tabulate(m, m->tab_x0, m->tab_x0 + m->tab_n * m->tab_h, m->tab_n));
   return DP_OK;
+}
+
+dp_status dp_tabulate(dp_model* h, double x_min, double x_max, int n_intervals) {
+  if (!h) return DP_ERR_ARG;
+  Model* m = &h->m;
+  if (n_intervals < 0 || n_intervals > (1 << 20) ||
+      (n_intervals > 0 && (!(x_max > x_min) || !std::isfinite(x_min) || !std::isfinite(x_max)))) {
+    m->last_error = "need 0 <= n_intervals <= 2^20 and finite x_min < x_max";
+    return DP_ERR_ARG;
+  }
+  drop_graphs(m);
+  m->tuned_key = 0;
+  return launch_tabulate(m, x_min, x_max, n_intervals);
 }
 
 long long dp_ntheta(const dp_model* h) { return h ? h->m.ntheta : 0; }
@@ -725,6 +739,8 @@ void dp_destroy(dp_model* h) {
   m->dev_allocs.clear();
   m->host_allocs.clear();
   mix_fit_release(m);
+  if (m->tab_mem) cudaFree(m->tab_mem);
+  m->tab_mem = nullptr;
   delete h;
 }
 
@@ -738,6 +754,10 @@ extern "C" dp_status dp_param_grad(dp_model* h, int natoms, const double* coords
   if (!coords || !types || !box || !F0 || !grad) { m->last_error = "null argument"; return DP_ERR_ARG; }
   if (natoms < 1) { m->last_error = "natoms < 1"; return DP_ERR_ARG; }
   if (natoms > m->max_atoms) { m->last_error = "natoms out of range"; return DP_ERR_CAPACITY; }
+  if (m->tab_n > 0) {
+    m->last_error = "the parameter gradient needs the embedding networks, not their tables";
+    return DP_ERR_UNSUPPORTED;
+  }
   const int offs[2] = {0, natoms};
   m->md_valid = false;
   DP_TRY(setup_replicas(m, 1, offs, box, natoms));

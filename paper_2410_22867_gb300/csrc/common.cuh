@@ -92,6 +92,13 @@ struct Model {
   double* pad64 = nullptr;
   float* pad32 = nullptr;
   bool has_pad = false;
+  // Tabulated embedding (dp_tabulate): tab_n > 0 intervals of width tab_h from tab_x0; quintic
+  // coefficients [pair][interval][100][8] in FP64 and FP32 (tab.cu).  tab_mem owns both.
+  int tab_n = 0;
+  double tab_x0 = 0.0, tab_h = 0.0;
+  double* tab64 = nullptr;
+  float* tab32 = nullptr;
+  void* tab_mem = nullptr;
   // 16-bit operand copies for the tensor-core kernels (per type), laid out by those kernels
   void* tc_weights = nullptr;
   size_t tc_weights_bytes = 0;
@@ -281,6 +288,8 @@ dp_status launch_rebuild(Model* m, int N);
 dp_status launch_delta(Model* m, int N);
 dp_status launch_format(Model* m, int N);
 dp_status launch_get_nlist(Model* m, int N, int* nlist, int* images);
+// tab.cu
+dp_status launch_tabulate(Model* m, double x0, double x1, int n);  // synchronous; n = 0 drops the table
 // simt.cu
 dp_status launch_pad_rows(Model* m);  // pad64 / pad32 from the current weights (synchronous caller)
 dp_status launch_descriptor(Model* m, int N);

@@ -50,6 +50,9 @@ struct MixArgs {
   double* vir_atom;      // [N][9] (unused by the mixed backward)
   double* vir_rep;       // [nrep][9] per-replica virial
   const int* irep;       // [N] replica of each internal atom
+  const float4* tab;     // tabulated embedding: [pair][interval][100][2] float4 quintic coefficients
+  int tab_n;
+  float tab_x0, tab_ih;  // first node, 1 / interval width
   int* err;
 };
 
@@ -319,6 +322,22 @@ __device__ __forceinline__ float4 pair_of(const MixArgs& a, const TileInfo& ti, 
   return __ldg(a.nl_d + (size_t)(ti.a0 + la) * a.S + a.sel_off[ti.tj] + (row - sRow[la]));
 }
 
+// Tabulated embedding: coefficient rows (two float4 per output: c0..c3, c4, c5, 0, 0) of the
+// interval holding x (edge intervals beyond the ends) and u = (x - x_i) / h.
+__device__ __forceinline__ const float4* tab_rows(const MixArgs& a, int pair, float x, float& u) {
+  const float f = (x - a.tab_x0) * a.tab_ih;
+  int i = (int)floorf(f);
+  i = min(max(i, 0), a.tab_n - 1);
+  u = f - (float)i;
+  return a.tab + ((size_t)pair * a.tab_n + i) * (kN3 * 2);
+}
+// G = P(u) and dG/du = P'(u) of output q.
+__device__ __forceinline__ void tab_poly(const float4* rows, int q, float u, float& g, float& gu) {
+  const float4 lo = __ldg(rows + 2 * q), hi = __ldg(rows + 2 * q + 1);
+  g = fmaf(u, fmaf(u, fmaf(u, fmaf(u, fmaf(u, hi.y, hi.x), lo.w), lo.z), lo.y), lo.x);
+  gu = fmaf(u, fmaf(u, fmaf(u, fmaf(u, 5.f * hi.y, 4.f * hi.x), 3.f * lo.w), 2.f * lo.z), lo.y);
+}
+
 // 1/r from one reciprocal square root (a few ulp; the row feeds 16-bit operands and FP32
 // sums), r = r^2 / r, and no divisions on the row's critical path.
 __device__ __forceinline__ void row_compute(const MixArgs& a, const TileInfo& ti, float4 dv, float winv,
@@ -415,7 +434,7 @@ __device__ __forceinline__ void operand_barrier() {
 // Embedding forward and T: per 128-row tile the environment row and layer 1 on the CUDA
 // cores, z2 = h1 W2 and z3 = h2 W3 on the tensor core (biases folded in), G = [h2, h2] +
 // tanh(z3), and the T product of G^T against the block-sparse R_hat^T.
-template <bool F16>
+template <bool F16, bool TAB>
 __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
   extern __shared__ unsigned char sraw[];
   unsigned char* sm = align1024(sraw);
@@ -485,7 +504,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     const unsigned shared_mask = (unsigned)ti.shared_mask;
     const int np = ti.ti * a.ntypes + ti.tj;
     if (np != pair) {
-      load_fwd_weights<F16>(a.w + (size_t)np * kEmbParams, sB2, sB3, small);
+      if (!TAB) load_fwd_weights<F16>(a.w + (size_t)np * kEmbParams, sB2, sB3, small);
       pair = np;
       __syncthreads();  // layer 1 reads biases written by other threads
     }
@@ -507,6 +526,30 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
       f.R[0] = f.R[1] = f.R[2] = f.R[3] = 0.f;
       f.la = 0;
     }
+    if constexpr (TAB) {
+      // the tabulated embedding: G straight from the table into the G^T operand (fp16, MN-major)
+      float u;
+      const float4* rows = tab_rows(a, np, f.R[0], u);
+#pragma unroll 1
+      for (int c = 0; c < 7; ++c) {
+        float g[16];
+#pragma unroll
+        for (int v = 0; v < 16; ++v) {
+          const int q = 16 * c + v;
+          float gu;
+          g[v] = 0.f;
+          if (q < kN3) tab_poly(rows, q, u, g[v], gu);
+        }
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const int q0 = 16 * c + 8 * hh;
+          if (q0 < kN3)
+            *reinterpret_cast<uint4*>(sGt + tc::sw128_mn_off(q0, t, 16384)) =
+                make_uint4(tc::pack2<true>(g[8 * hh], g[8 * hh + 1]), tc::pack2<true>(g[8 * hh + 2], g[8 * hh + 3]),
+                           tc::pack2<true>(g[8 * hh + 4], g[8 * hh + 5]), tc::pack2<true>(g[8 * hh + 6], g[8 * hh + 7]));
+        }
+      }
+    } else {
     layer1<F16, true>(small, f.R[0], h1, sA, t);
     operand_barrier();
     if (t == 0) {
@@ -548,14 +591,16 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
                            tc::pack2<true>(g[8 * hh + 4], g[8 * hh + 5]), tc::pack2<true>(g[8 * hh + 6], g[8 * hh + 7]));
         }
       }
-      if (valid) {
-        const uint32_t kr = (uint32_t)(t & 63);
-        unsigned char* rcol = sRs + (uint32_t)(t >> 6) * 2048u + (kr & 7) * 2;
+    }
+    }
+    // this row's R_hat column of the block-sparse operand
+    if (valid) {
+      const uint32_t kr = (uint32_t)(t & 63);
+      unsigned char* rcol = sRs + (uint32_t)(t >> 6) * 2048u + (kr & 7) * 2;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int n = f.la * 4 + c;
-          *reinterpret_cast<__half*>(rcol + n * 128 + (((kr >> 3) ^ (n & 7)) << 4)) = __float2half_rn(f.R[c]);
-        }
+      for (int c = 0; c < 4; ++c) {
+        const int n = f.la * 4 + c;
+        *reinterpret_cast<__half*>(rcol + n * 128 + (((kr >> 3) ^ (n & 7)) << 4)) = __float2half_rn(f.R[c]);
       }
     }
     operand_barrier();
@@ -680,7 +725,7 @@ __device__ void load_bwd_ops(const float* __restrict__ W, unsigned char* sB2, un
 // features m and m + 50 together, so the residual part dG[m] + dG[m + 50] of dE/dh2 is final
 // when formed; it is parked in the TMEM columns of z3 just read, and added back after the
 // dh2' product.  dR_hat and dG use dE/dT and G in FP32 on the CUDA cores.
-template <bool F16>
+template <bool F16, bool TAB>
 __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
   extern __shared__ unsigned char sraw[];
   unsigned char* sm = align1024(sraw);
@@ -749,7 +794,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
     if (w == kLocWarp && cur + ti.nrows < c1) locate_window(a, cur + ti.nrows, wk, s_tot, sWin);
     const int np = ti.ti * a.ntypes + ti.tj;
     if (np != pair) {
-      load_bwd_ops<F16>(a.w + (size_t)np * kEmbParams, sB2, sB3, small);
+      if (!TAB) load_bwd_ops<F16>(a.w + (size_t)np * kEmbParams, sB2, sB3, small);
       pair = np;
       __syncthreads();
     }
@@ -774,6 +819,47 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
       f.R[0] = f.R[1] = f.R[2] = f.R[3] = 0.f;
       f.la = 0; f.j = 0; f.atom = ti.a0;
     }
+    float dR[4] = {0.f, 0.f, 0.f, 0.f};
+    float ds = 0.f;
+    if constexpr (TAB) {
+      // the tabulated embedding (no tensor-core products): G and dG/dx of each pair (m, m + 50)
+      // from the table, dR_hat += dT G (packed pairs), dG = R_hat . dT, d s_hat += dG dG/dx
+      const float4* dTa = sdT + f.la * kN3;
+      float u;
+      const float4* rows = tab_rows(a, np, f.R[0], u);
+      uint64_t ax = tc::f2(0.f, 0.f), ay = ax, az = ax, aw = ax;
+#pragma unroll 2
+      for (int m = 0; m < kN2; ++m) {
+        float ga_, gua, gb_, gub;
+        tab_poly(rows, m, u, ga_, gua);
+        tab_poly(rows, m + kN2, u, gb_, gub);
+        const uint64_t G2 = tc::f2(ga_, gb_);
+        const float4 plo = dTa[2 * m], phi = dTa[2 * m + 1];
+        ax = tc::f2fma(tc::f2(plo.x, plo.y), G2, ax);
+        ay = tc::f2fma(tc::f2(plo.z, plo.w), G2, ay);
+        az = tc::f2fma(tc::f2(phi.x, phi.y), G2, az);
+        aw = tc::f2fma(tc::f2(phi.z, phi.w), G2, aw);
+        const float ga = fmaf(f.R[3], phi.z, fmaf(f.R[2], phi.x, fmaf(f.R[1], plo.z, f.R[0] * plo.x)));
+        const float gb = fmaf(f.R[3], phi.w, fmaf(f.R[2], phi.y, fmaf(f.R[1], plo.w, f.R[0] * plo.y)));
+        ds = fmaf(ga, gua, fmaf(gb, gub, ds));
+      }
+      dR[0] = tc::f2lo(ax) + tc::f2hi(ax);
+      dR[1] = tc::f2lo(ay) + tc::f2hi(ay);
+      dR[2] = tc::f2lo(az) + tc::f2hi(az);
+      dR[3] = tc::f2lo(aw) + tc::f2hi(aw);
+      ds *= a.tab_ih;
+      __syncthreads();  // every thread is done with sdT and sRow before the next tile's lookup
+      if (w == kLocWarp && cur + ti.nrows < c1) {
+        locate_tile(a, cur + ti.nrows, c0, c1, wk, s_tot, s_tiend, &sti, sRow, sWin, true, &sNat);
+        if (lane == 0) fetch_dT(a, sti.a0, sNat, sdT, &dbar);
+      }
+      if (cur + ti.nrows < c1) {
+        dT_pending = true;
+        __syncthreads();  // the next tile's sti / sRow
+        const TileInfo nx = sti;
+        if (t < nx.nrows) stage_row(a, nx, sRow, t, sNd, sNj, sRep + ((it + 1) & 1) * kRows);
+      }
+    } else {
     layer1<F16>(small, f.R[0], h1, sA, t);
     operand_barrier();
     if (t == 0) {
@@ -796,7 +882,6 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
     // two members of a pair run as packed FP32 pairs against the paired dE/dT layout (entries 2m,
     // 2m + 1: x, y then z, w of units m and m + 50).  dz3 is stored negated ((t^2 - 1) g instead of
     // (1 - t^2) g, one instruction less); the layer-2 backward takes the sign back.
-    float dR[4] = {0.f, 0.f, 0.f, 0.f};
     {
       const float4* dTa = sdT + f.la * kN3;
       const uint64_t m1 = tc::f2(-1.f, -1.f);
@@ -911,7 +996,6 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
     }
     __syncwarp();
     mma_sync_wait(&bar, phase, a.err, ok);
-    float ds = 0.f;
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       float z[16];
@@ -931,6 +1015,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
         }
       }
     }
+    }  // network path
     // chain rule through the normalisation and the environment row.  Per-row terms,
     // the per-warp partial sums and the force accumulation are FP32 (FP64 arithmetic
     // runs at a small fraction of the FP32 rate on this GPU; ~180 terms per atom add
@@ -1260,6 +1345,10 @@ MixArgs make_mix_args(Model* m, int N) {
   for (int t = 0; t <= m->ntypes; ++t) a.sel_off[t] = m->sel_off[t];
   a.rc = (float)m->rc; a.rs = (float)m->rs; a.invS = 1.f / (float)m->S; a.switch_kind = m->switch_kind;
   a.w = m->w32; a.stat = m->stat32; a.itype = m->itype; a.type_off = m->type_off; a.rowoff = m->rowoff;
+  a.tab = reinterpret_cast<const float4*>(m->tab32);
+  a.tab_n = m->tab_n;
+  a.tab_x0 = (float)m->tab_x0;
+  a.tab_ih = m->tab_n ? (float)(1.0 / m->tab_h) : 0.f;
   a.nl_j = m->nl_j; a.nl_d = static_cast<const float4*>(m->nl_d);
   a.Tseg = m->Tseg; a.dT = static_cast<const float4*>(m->dTm);
   a.force = m->force; a.force32 = m->force32; a.vir_atom = m->vir_atom; a.err = m->err;
@@ -1281,12 +1370,13 @@ dp_status launch_mix_descriptor(Model* m, int N) {
   DP_CUDA_TRY(m, cudaMemsetAsync(m->Tseg, 0, sizeof(float) * 400 * (size_t)N * m->ntypes, m->stream));
   MixArgs a = make_mix_args(m, N);
   const bool f16 = m->prec == DP_MIX_FP16;
-  const void* fn = f16 ? reinterpret_cast<const void*>(k_mix_embed_fwd<true>)
-                       : reinterpret_cast<const void*>(k_mix_embed_fwd<false>);
+  const bool tab = m->tab_n > 0;
+  auto fk = f16 ? (tab ? k_mix_embed_fwd<true, true> : k_mix_embed_fwd<true, false>)
+                : (tab ? k_mix_embed_fwd<false, true> : k_mix_embed_fwd<false, false>);
+  const void* fn = reinterpret_cast<const void*>(fk);
   DP_CUDA_TRY(m, ensure_smem(fn, kFwdSmem));
   const int grid = tuned_grid(m, 0, num_sms() * blocks_per_sm(fn, kRows, kFwdSmem, kTmemCols));
-  if (f16) k_mix_embed_fwd<true><<<grid, kRows, kFwdSmem, m->stream>>>(a);
-  else k_mix_embed_fwd<false><<<grid, kRows, kFwdSmem, m->stream>>>(a);
+  fk<<<grid, kRows, kFwdSmem, m->stream>>>(a);
   if (m->sub_ev[0]) DP_CUDA_TRY(m, cudaEventRecord(m->sub_ev[0], m->stream));
   const int dgrid = std::max(1, std::min((N + kDescWarps - 1) / kDescWarps, tuned_grid(m, 3, 8 * num_sms())));
   const size_t dsm = (size_t)kDescWarps * 2 * m->ntypes * kN3 * sizeof(float4);
@@ -1321,12 +1411,13 @@ dp_status launch_mix_embed_backward(Model* m, int N) {
   if (m->sub_ev[1]) DP_CUDA_TRY(m, cudaEventRecord(m->sub_ev[1], m->stream));
   MixArgs a = make_mix_args(m, N);
   const bool f16 = m->prec == DP_MIX_FP16;
-  const void* fn = f16 ? reinterpret_cast<const void*>(k_mix_embed_bwd<true>)
-                       : reinterpret_cast<const void*>(k_mix_embed_bwd<false>);
+  const bool tab = m->tab_n > 0;
+  auto bk = f16 ? (tab ? k_mix_embed_bwd<true, true> : k_mix_embed_bwd<true, false>)
+                : (tab ? k_mix_embed_bwd<false, true> : k_mix_embed_bwd<false, false>);
+  const void* fn = reinterpret_cast<const void*>(bk);
   DP_CUDA_TRY(m, ensure_smem(fn, kBwdSmem));
   const int grid = tuned_grid(m, 1, num_sms() * blocks_per_sm(fn, kRows, kBwdSmem, kTmemCols));
-  if (f16) k_mix_embed_bwd<true><<<grid, kRows, kBwdSmem, m->stream>>>(a);
-  else k_mix_embed_bwd<false><<<grid, kRows, kBwdSmem, m->stream>>>(a);
+  bk<<<grid, kRows, kBwdSmem, m->stream>>>(a);
   k_fold_force32<<<cdiv(3L * N, 256), 256, 0, m->stream>>>(3 * N, m->force32, m->force);
   m->launches += 3;
   DP_LAUNCH_CHECK(m);

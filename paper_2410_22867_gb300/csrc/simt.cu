@@ -52,6 +52,9 @@ struct EmbArgs {
   const T* stat;       // davg [nt][4] then 1/dstd [nt][4]
   const T* pad;        // [nt][nt][4][100] padded-slot term, or null (every davg is 0)
   int sel[kMaxTypes];
+  const T* tab;        // tabulated embedding: [pair][interval][100][8] quintic coefficients (TAB kernels)
+  int tab_n;
+  T tab_x0, tab_ih;    // first node, 1 / interval width
   const int* itype;
   const int* nl_j;
   const void* nl_d;
@@ -79,6 +82,23 @@ template <>
 __device__ __forceinline__ void load_pair_vec<double>(const void* nl_d, size_t idx, double* d) {
   dvec4 v = static_cast<const dvec4*>(nl_d)[idx];
   d[0] = v.x; d[1] = v.y; d[2] = v.z;
+}
+
+// Tabulated embedding: the coefficient rows of the interval holding x (edge intervals beyond
+// the ends) and the offset u = (x - x_i) / h in it.
+template <class T>
+__device__ __forceinline__ const T* tab_rows(const EmbArgs<T>& a, int pair, T x, T& u) {
+  const T f = (x - a.tab_x0) * a.tab_ih;
+  int i = (int)floor(f);
+  i = min(max(i, 0), a.tab_n - 1);
+  u = f - T(i);
+  return a.tab + ((size_t)pair * a.tab_n + i) * kN3 * 8;
+}
+// G = P(u) and dG/du = P'(u) of one output from its six coefficients.
+template <class T>
+__device__ __forceinline__ void tab_poly(const T* c, T u, T& g, T& gu) {
+  g = c[0] + u * (c[1] + u * (c[2] + u * (c[3] + u * (c[4] + u * c[5]))));
+  gu = c[1] + u * (T(2) * c[2] + u * (T(3) * c[3] + u * (T(4) * c[4] + u * T(5) * c[5])));
 }
 
 // Layers 1 and 2 of the embedding net for input x: h1 [25], h2 [50] = [h1, h1] + tanh(h1 W2 + b2).
@@ -120,7 +140,7 @@ __device__ __forceinline__ void env_row(const T* d, T rs, T rc, int kind, const 
 // Forward: per atom, R_hat rows and G rows of a chunk of neighbours are staged in
 // shared memory; T = (1/S) R_hat^T G is accumulated by the first 100 threads
 // (one output column each); D = T^T T[:, :16] follows.
-template <class T>
+template <class T, bool TAB>
 __global__ void __launch_bounds__(EB<T>::v) k_embed_fwd(EmbArgs<T> a) {
   constexpr int NB = EB<T>::v;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -160,9 +180,14 @@ __global__ void __launch_bounds__(EB<T>::v) k_embed_fwd(EmbArgs<T> a) {
           env_row<T>(d, a.rs, a.rc, a.switch_kind, avg, isd, R, r, sw, dsw);
 #pragma unroll
           for (int c = 0; c < 4; ++c) sR[tid * 4 + c] = R[c];
+          T* g = sG + tid * kGP;
+          if (TAB) {
+            T u, gu;
+            const T* rows = tab_rows<T>(a, ti * a.ntypes + tj, R[0], u);
+            for (int q = 0; q < kN3; ++q) tab_poly<T>(rows + 8 * q, u, g[q], gu);
+          } else {
           T h1[kN1], h2[kN2];
           emb12<T>(W, R[0], h1, h2);
-          T* g = sG + tid * kGP;
 #pragma unroll
           for (int m = 0; m < kN2; ++m) g[m] = h2[m];  // staged residual, overwritten by G below
           for (int q = 0; q < kN2; ++q) {
@@ -175,6 +200,7 @@ __global__ void __launch_bounds__(EB<T>::v) k_embed_fwd(EmbArgs<T> a) {
             T res = g[q];
             g[q] = res + dtanh<T>(za);
             g[q + kN2] = res + dtanh<T>(zb);
+          }
           }
         }
         __syncthreads();
@@ -245,7 +271,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 // dR_hat = dT G, dG = R_hat dT, reverse through the embedding to d s_hat, the
 // analytic Jacobian of the environment row gives g = dE/dd; F_i += g, F_j -= g
 // (FP64 atomics), per-atom virial -sum g (x) d.
-template <class T>
+template <class T, bool TAB>
 __global__ void __launch_bounds__(EB<T>::v) k_embed_bwd(EmbArgs<T> a) {
   constexpr int NB = EB<T>::v;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -295,11 +321,28 @@ __global__ void __launch_bounds__(EB<T>::v) k_embed_bwd(EmbArgs<T> a) {
           T d[3], R[4], r, sw, dsw;
           load_pair_vec<T>(a.nl_d, e, d);
           env_row<T>(d, a.rs, a.rc, a.switch_kind, avg, isd, R, r, sw, dsw);
+          T dR[4] = {T(0), T(0), T(0), T(0)};
+          if (TAB) {
+            // G and dG/dx from the table: dR_hat = dT G, dG = R_hat . dT, d s_hat = sum dG dG/dx
+            T u, g, gu, ds = T(0);
+            const T* rows = tab_rows<T>(a, ti * a.ntypes + tj, R[0], u);
+            for (int q = 0; q < kN3; ++q) {
+              tab_poly<T>(rows + 8 * q, u, g, gu);
+              T dg = T(0);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                const T dt = sdT[c * kN3 + q];
+                dR[c] += dt * g;
+                dg += R[c] * dt;
+              }
+              ds += dg * gu;
+            }
+            dR[0] += ds * a.tab_ih;
+          } else {
           T h1[kN1], h2[kN2], dh2[kN2];
           emb12<T>(W, R[0], h1, h2);
 #pragma unroll
           for (int m = 0; m < kN2; ++m) { sH[m * NB + tid] = h2[m]; dh2[m] = T(0); }
-          T dR[4] = {T(0), T(0), T(0), T(0)};
           for (int q = 0; q < kN2; ++q) {
             T za = W[kEb3 + q], zb = W[kEb3 + q + kN2];
 #pragma unroll
@@ -340,6 +383,7 @@ __global__ void __launch_bounds__(EB<T>::v) k_embed_bwd(EmbArgs<T> a) {
 #pragma unroll
           for (int k = 0; k < kN1; ++k) ds_in += dh1[k] * (T(1) - h1[k] * h1[k]) * W[kEW1 + k];
           dR[0] += ds_in;
+          }
 #pragma unroll
           for (int c = 0; c < 4; ++c) dR[c] *= isd[c];
           // Jacobian of (s, s d/r) with respect to d
@@ -576,6 +620,11 @@ EmbArgs<T> make_emb_args(Model* m, int N) {
   a.pad = !m->has_pad ? nullptr
                       : (sizeof(T) == 8) ? reinterpret_cast<const T*>(m->pad64) : reinterpret_cast<const T*>(m->pad32);
   for (int t = 0; t < m->ntypes; ++t) a.sel[t] = m->sel[t];
+  a.tab = (m->tab_n == 0) ? nullptr
+          : (sizeof(T) == 8) ? reinterpret_cast<const T*>(m->tab64) : reinterpret_cast<const T*>(m->tab32);
+  a.tab_n = m->tab_n;
+  a.tab_x0 = (T)m->tab_x0;
+  a.tab_ih = m->tab_n ? (T)(1.0 / m->tab_h) : T(0);
   a.itype = m->itype; a.nl_j = m->nl_j; a.nl_d = m->nl_d; a.nl_count = m->nl_count;
   a.Tm = static_cast<T*>(m->Tm); a.Dm = static_cast<T*>(m->Dm); a.dD = static_cast<const T*>(m->dD);
   a.force = m->force; a.vir_atom = m->vir_atom;
@@ -593,9 +642,10 @@ dp_status run_descriptor(Model* m, int N) {
   constexpr int NB = EB<T>::v;
   EmbArgs<T> a = make_emb_args<T>(m, N);
   size_t smem = sizeof(T) * ((size_t)m->ntypes * kEmbParams + NB * kGP + NB * 4 + 4 * kN3);
-  DP_CUDA_TRY(m, ensure_smem(reinterpret_cast<const void*>(k_embed_fwd<T>), smem));
-  int grid = resident_grid(k_embed_fwd<T>, NB, smem, N);
-  k_embed_fwd<T><<<grid, NB, smem, m->stream>>>(a);
+  auto fn = (m->tab_n > 0) ? k_embed_fwd<T, true> : k_embed_fwd<T, false>;
+  DP_CUDA_TRY(m, ensure_smem(reinterpret_cast<const void*>(fn), smem));
+  int grid = resident_grid(fn, NB, smem, N);
+  fn<<<grid, NB, smem, m->stream>>>(a);
   m->launches += 1;
   DP_LAUNCH_CHECK(m);
   return DP_OK;
@@ -606,9 +656,10 @@ dp_status run_embed_backward(Model* m, int N) {
   constexpr int NB = EB<T>::v;
   EmbArgs<T> a = make_emb_args<T>(m, N);
   size_t smem = sizeof(T) * ((size_t)m->ntypes * kEmbParams + 8 * kN3 + kKD + (size_t)kH * NB);
-  DP_CUDA_TRY(m, ensure_smem(reinterpret_cast<const void*>(k_embed_bwd<T>), smem));
-  int grid = resident_grid(k_embed_bwd<T>, NB, smem, N);
-  k_embed_bwd<T><<<grid, NB, smem, m->stream>>>(a);
+  auto fn = (m->tab_n > 0) ? k_embed_bwd<T, true> : k_embed_bwd<T, false>;
+  DP_CUDA_TRY(m, ensure_smem(reinterpret_cast<const void*>(fn), smem));
+  int grid = resident_grid(fn, NB, smem, N);
+  fn<<<grid, NB, smem, m->stream>>>(a);
   m->launches += 1;
   DP_LAUNCH_CHECK(m);
   return DP_OK;
