@@ -213,12 +213,12 @@ TANH_PER_NEIGHBOUR = 175
 # entry names the source file of the kernel and its SHA-1 at the capture: when the file has
 # changed since, the figure no longer describes the kernel and `traffic` is reported as null.
 TRAFFIC_PER_ROW = {
-    ("embedding_backward", "mix_fp16"): {"bytes_per_row": (171.772672e6 + 4.658688e6) / 5726060,
+    ("embedding_backward", "mix_fp16"): {"bytes_per_row": (171.752960e6 + 4.357888e6) / 5726060,
                                          "source": "paper_2410_22867_gb300/csrc/mix_embed.cu",
-                                         "sha1": "1d36283-capture"},
-    ("embedding_forward", "mix_fp16"): {"bytes_per_row": (95.659008e6 + 21.622016e6) / 5726060,
+                                         "sha1": "e859ed66e8863603f9cf708684bee130645f3875"},
+    ("embedding_forward", "mix_fp16"): {"bytes_per_row": (95.665408e6 + 21.460480e6) / 5726060,
                                         "source": "paper_2410_22867_gb300/csrc/mix_embed.cu",
-                                        "sha1": "1d36283-capture"},
+                                        "sha1": "e859ed66e8863603f9cf708684bee130645f3875"},
 }
 
 

@@ -205,6 +205,30 @@ dp_status dp_param_grad(dp_model* m, int natoms, const double* coords, const int
  */
 dp_status dp_tabulate(dp_model* m, double x_min, double x_max, int n_intervals);
 
+/*
+ * dp_rdf -- pair-distance histogram of the last evaluation (dp_compute, dp_compute_batch or
+ * an MD call), behind the radial distribution function of Section IV-A (Fig. 6): for every
+ * centre atom i of type ti and neighbour (j, image n) of type tj at distance r < r_max,
+ * counts[(ti * ntypes + tj) * nbins + floor(r / (r_max / nbins))] += 1.  Each unordered pair is
+ * counted from both ends.  The pairs are those of the formatted neighbour list, so
+ * r_max <= rcut.  g_ab(r) = counts_ab / (N_a rho_b 4 pi r^2 dr) with rho_b = N_b / V (N_b - 1
+ * for a = b).  counts [ntypes * ntypes * nbins] host output.  Distances in the model's
+ * precision of the pair vectors (FP64 for DP_FP64, else FP32).  Synchronous.
+ * Errors: DP_ERR_ARG (no state, nbins < 1, ntypes^2 nbins > 24576, r_max outside (0, rcut]).
+ */
+dp_status dp_rdf(dp_model* m, int nbins, double r_max, unsigned long long* counts);
+
+/*
+ * dp_atom_virial -- per-atom virial of the last evaluation, caller order: atom_virial
+ * [natoms * 9] device, row-major 3 x 3 per atom, W_i = -sum over the neighbours (j, n) of i of
+ * g_ijn (x) d_ijn with g = dE/dd (each pair term assigned to its centre atom i; the W_i sum to
+ * the virial of dp_compute).  FP64 / FP32 models compute it in every evaluation; the mixed
+ * precisions compute it here with a second pass of the force backward on the stored state (the
+ * forces are not touched).  Asynchronous on the model's stream.
+ * Errors: DP_ERR_ARG (null, no state), DP_ERR_CUDA.
+ */
+dp_status dp_atom_virial(dp_model* m, double* atom_virial);
+
 /* Number of parameters in theta (the length of dp_param_grad's grad). */
 long long dp_ntheta(const dp_model* m);
 

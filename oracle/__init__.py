@@ -57,7 +57,8 @@ def lib():
             L.oracle_get_threads.restype = _I
             L.oracle_wrap.argtypes = [_I, _P, _P, _P]
             L.oracle_nlist.argtypes = [_P, _I, _P, _P, _P, _D, _P, _I, _P, _P, _P]
-            L.oracle_compute.argtypes = [_P, _I, _P, _P, _P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _P]
+            L.oracle_compute.argtypes = [_P, _I, _P, _P, _P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P]
+            L.oracle_rdf.argtypes = [_P, _I, _P, _P, _P, _I, _D, _P]
             L.oracle_dir_deriv.argtypes = [_P, _I, _P, _P, _P, _P, _P]
             L.oracle_param_grad.argtypes = [_P, _I, _P, _P, _P, _D, _P, _D, _D, _I, _P, _P, _P, _P]
             L.oracle_md.argtypes = [_P, _I, _P, _P, _P, _P, _P, _D, _I, _I, _D, _P, _P, _P]
@@ -138,7 +139,7 @@ class Model:
 
     # -- evaluation -----------------------------------------------------------
     def compute(self, coords, types, box, method: str = "cell", centre_mask=None, forces: bool = True,
-                intermediates: bool = False):
+                intermediates: bool = False, atom_virial: bool = False):
         coords, types, box = _f64(coords), _i32(types), _f64(box)
         N = len(types)
         E = np.zeros(1)
@@ -151,9 +152,10 @@ class Model:
             D = np.zeros((N, 1600))
             dD = np.zeros((N, 1600)) if forces else None
         mask = None if centre_mask is None else np.ascontiguousarray(centre_mask, dtype=np.uint8)
+        W = np.zeros((N, 3, 3)) if (atom_virial and forces) else None
         st = lib().oracle_compute(self.h, N, _ptr(coords), _ptr(types), _ptr(box),
                                   0 if method == "brute" else 1, _ptr(mask), int(forces), _ptr(E), _ptr(Ei),
-                                  _ptr(F), _ptr(V), _ptr(T), _ptr(D), _ptr(dD))
+                                  _ptr(F), _ptr(V), _ptr(T), _ptr(D), _ptr(dD), _ptr(W))
         _check(st)
         out = {"energy": float(E[0]), "atom_energy": Ei}
         if forces:
@@ -161,6 +163,17 @@ class Model:
             out["virial"] = V.reshape(3, 3)
         if intermediates:
             out.update(T=T, D=D, dD=dD)
+        if W is not None:
+            out["atom_virial"] = W
+        return out
+
+    def rdf(self, coords, types, box, nbins: int, r_max: float):
+        """Pair-distance histogram counts [ntypes, ntypes, nbins] of all pairs within r_max (each
+        pair counted from both ends)."""
+        coords, types, box = _f64(coords), _i32(types), _f64(box)
+        out = np.zeros((self.ntypes, self.ntypes, nbins), dtype=np.uint64)
+        _check(lib().oracle_rdf(self.h, len(types), _ptr(coords), _ptr(types), _ptr(box), int(nbins), float(r_max),
+                                _ptr(out)))
         return out
 
     def energy(self, coords, types, box) -> float:

@@ -551,6 +551,7 @@ struct Inter {            // optional per-atom intermediates
   double* T = nullptr;    // [N][4][n3]
   double* D = nullptr;    // [N][n3*m2]
   double* dD = nullptr;   // [N][n3*m2]
+  double* W = nullptr;    // [N][9] per-atom virial: -sum over atom i's neighbours of g (x) d
 };
 
 // Energy, forces and virial for all atoms whose centre_mask is set (all if null).
@@ -703,7 +704,10 @@ void evaluate(const Model<T>& m, int N, const T* x, const int* types, const doub
         std::vector<T>& F = fbuf[tid];
         for (int a = 0; a < 3; ++a) { F[3 * i + a] += g[a]; F[3 * j + a] -= g[a]; }
         for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b) vbuf[tid][a * 3 + b] -= g[a] * d[b];
+          for (int b = 0; b < 3; ++b) {
+            vbuf[tid][a * 3 + b] -= g[a] * d[b];
+            if (inter && inter->W) inter->W[(size_t)i * 9 + a * 3 + b] -= val(g[a] * d[b]);
+          }
       }
     }
   }
@@ -812,7 +816,7 @@ int oracle_nlist(const void* h, int N, const double* x, const int* types, const 
 int oracle_compute(const void* h, int N, const double* x, const int* types, const double* box,
                    int method, const unsigned char* centre_mask, int want_force, double* energy,
                    double* atom_energy, double* force, double* virial, double* interT,
-                   double* interD, double* interdD) {
+                   double* interD, double* interdD, double* atom_virial) {
   const Model<double>& m = *static_cast<const Model<double>*>(h);
   double L[3];
   if (!box_lengths(box, L)) return 4;
@@ -822,9 +826,40 @@ int oracle_compute(const void* h, int N, const double* x, const int* types, cons
   if (method == 0) nlist_brute(N, xw.data(), types, L, m.rc, m.sel, nl);
   else nlist_cell(N, xw.data(), types, L, m.rc, m.sel, nl);
   if (nl.overflow) return 5;
-  Inter in{interT, interD, interdD};
+  if (atom_virial) for (size_t q = 0; q < (size_t)N * 9; ++q) atom_virial[q] = 0.0;
+  Inter in{interT, interD, interdD, atom_virial};
   evaluate<double>(m, N, xw.data(), types, L, nl, centre_mask, want_force != 0, energy, atom_energy,
                    force, virial, &in);
+  return 0;
+}
+
+// Pair-distance histogram within r_max (<= any r): for every atom i and neighbour (j, n) at
+// distance r < r_max (brute-force cell list, wrapped positions, r^2 in the fixed operation order),
+// counts[(t_i * nt + t_j) * nbins + min(floor(r * nbins / r_max), nbins - 1)] += 1.
+int oracle_rdf(const void* h, int N, const double* x, const int* types, const double* box, int nbins,
+               double r_max, unsigned long long* counts) {
+  const Model<double>& m = *static_cast<const Model<double>*>(h);
+  double L[3];
+  if (!box_lengths(box, L)) return 4;
+  if (nbins < 1 || !(r_max > 0)) return 1;
+  std::vector<double> xw;
+  wrap_all(N, x, L, xw);
+  const int nt = m.ntypes;
+  std::vector<int> big(nt, N * 64);
+  NList nl;
+  nlist_cell(N, xw.data(), types, L, r_max, big, nl);
+  for (size_t q = 0; q < (size_t)nt * nt * nbins; ++q) counts[q] = 0;
+  const double inv = nbins / r_max;
+  for (int i = 0; i < N; ++i)
+    for (int k = 0; k < nl.S; ++k) {
+      const int j = nl.j[(size_t)i * nl.S + k];
+      if (j < 0) continue;
+      int n[3];
+      unpack_img(nl.img[(size_t)i * nl.S + k], n[0], n[1], n[2]);
+      const double r = std::sqrt(dist2(&xw[3 * i], &xw[3 * j], n, L));
+      const int b = std::min((int)std::floor(r * inv), nbins - 1);
+      counts[((size_t)types[i] * nt + types[j]) * nbins + b] += 1;
+    }
   return 0;
 }
 

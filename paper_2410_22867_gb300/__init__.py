@@ -32,7 +32,7 @@ STATUS = {0: "DP_OK", 1: "DP_ERR_ARG", 2: "DP_ERR_CUDA", 3: "DP_ERR_OOM", 4: "DP
 EXPORTS = ("dp_create", "dp_compute", "dp_compute_batch", "dp_verlet_step", "dp_md_run_batch", "dp_param_grad",
            "dp_ntheta", "dp_get_nlist", "dp_phase_times", "dp_kernel_launches", "dp_sync", "dp_last_error",
            "dp_destroy", "dp_version", "dp_selftest", "dp_selftest_noalloc", "dp_set_params", "dp_autotune",
-           "dp_wait_selftest", "dp_measure_peak", "dp_tabulate")
+           "dp_wait_selftest", "dp_measure_peak", "dp_tabulate", "dp_rdf", "dp_atom_virial")
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -91,10 +91,12 @@ def lib():
             L.dp_wait_selftest.argtypes = [ctypes.c_uint]
             L.dp_measure_peak.argtypes = [_I, _P]
             L.dp_tabulate.argtypes = [_P, _D, _D, _I]
+            L.dp_rdf.argtypes = [_P, _I, _D, _P]
+            L.dp_atom_virial.argtypes = [_P, _P]
             for name in ("dp_create", "dp_compute", "dp_compute_batch", "dp_verlet_step", "dp_md_run_batch",
                          "dp_param_grad", "dp_get_nlist", "dp_phase_times", "dp_sync", "dp_selftest",
                          "dp_selftest_noalloc", "dp_set_params", "dp_autotune", "dp_wait_selftest",
-                         "dp_measure_peak", "dp_tabulate"):
+                         "dp_measure_peak", "dp_tabulate", "dp_rdf", "dp_atom_virial"):
                 getattr(L, name).restype = _I
             _lib = L
     return _lib
@@ -305,6 +307,21 @@ class DPModel:
         self._check(lib().dp_tabulate(self.h, float(x_min), float(x_max), int(n_intervals)))
         return float(x_min), float(x_max), int(n_intervals)
 
+    def rdf(self, nbins: int, r_max: float):
+        """dp_rdf: pair-distance histogram [ntypes, ntypes, nbins] (uint64) of the last evaluation."""
+        out = np.zeros((self.ntypes, self.ntypes, int(nbins)), dtype=np.uint64)
+        self._check(lib().dp_rdf(self.h, int(nbins), float(r_max), out.ctypes.data_as(_P)))
+        return out
+
+    def atom_virial(self, sync: bool = True):
+        """dp_atom_virial: per-atom virial [N, 3, 3] (caller order) of the last evaluation."""
+        import torch
+        out = torch.empty(self._last_n, 3, 3, dtype=torch.float64, device=self.device)
+        self._check(lib().dp_atom_virial(self.h, _ptr(out)))
+        if sync:
+            self.sync()
+        return out
+
     def autotune(self, repeats: int = 3):
         """dp_autotune: choose the launch grids of the mixed kernels on the current state;
         returns [embedding forward, embedding backward, dE/dT, descriptor] (0 = not tuned).
@@ -350,6 +367,22 @@ def _remember_n(fn):
 
 DPModel.compute = _remember_n(DPModel.compute)
 DPModel.compute_batch = _remember_n(DPModel.compute_batch)
+
+
+def rdf_g(counts, natoms_by_type, volume: float, r_max: float):
+    """g_ab(r) at the bin centres from dp_rdf counts [nt, nt, nbins]: counts / (N_a rho_b 4 pi r^2 dr),
+    rho_b = N_b / V (N_b - 1 for a = b).  Returns (r, g)."""
+    c = np.asarray(counts, dtype=np.float64)
+    nt, _, nb = c.shape
+    dr = r_max / nb
+    r = (np.arange(nb) + 0.5) * dr
+    shell = 4.0 * np.pi * r * r * dr
+    g = np.zeros_like(c)
+    for a in range(nt):
+        for b in range(nt):
+            nb_ = natoms_by_type[b] - (1 if a == b else 0)
+            g[a, b] = c[a, b] / (natoms_by_type[a] * (nb_ / volume) * shell)
+    return r, g
 
 
 def _make_param_loss():

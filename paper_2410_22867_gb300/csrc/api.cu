@@ -513,6 +513,7 @@ dp_status dp_create(dp_model** out, int ntypes, const char* const* type_map, dou
   A_(stat64, 8 * 8 * nt);
   A_(stat32, 4 * 8 * nt);
   A_(pad64, 8 * (size_t)nt * nt * 4 * kN3);
+  A_(rdf_hist, sizeof(unsigned long long) * kRdfMaxCells);
   A_(pad32, 4 * (size_t)nt * nt * 4 * kN3);
   A_(perm, 4 * N); A_(inv, 4 * N); A_(itype, 4 * N); A_(irep, 4 * N);
   A_(type_count, 4 * (kMaxTypes + 1)); A_(type_off, 4 * (kMaxTypes + 1));
@@ -640,6 +641,33 @@ dp_status dp_set_params(dp_model* h, const double* theta, long long ntheta) {
   DP_CUDA_TRY(m, cudaDeviceSynchronize());
   if (m->tab_n > 0) DP_TRY(launch_tabulate(m, m->tab_x0, m->tab_x0 + m->tab_n * m->tab_h, m->tab_n));
   return DP_OK;
+}
+
+dp_status dp_rdf(dp_model* h, int nbins, double r_max, unsigned long long* counts) {
+  if (!h || !counts) return DP_ERR_ARG;
+  Model* m = &h->m;
+  if (m->natoms < 1) { m->last_error = "no state to analyse"; return DP_ERR_ARG; }
+  if (nbins < 1 || nbins * m->ntypes * m->ntypes > kRdfMaxCells || !(r_max > 0) || r_max > m->rc) {
+    m->last_error = "need 1 <= nbins, ntypes^2 * nbins <= 24576 and 0 < r_max <= rcut";
+    return DP_ERR_ARG;
+  }
+  DP_TRY(launch_rdf(m, nbins, r_max, m->rdf_hist));
+  DP_CUDA_TRY(m, cudaMemcpyAsync(counts, m->rdf_hist, sizeof(unsigned long long) * (size_t)m->ntypes * m->ntypes * nbins,
+                                 cudaMemcpyDeviceToHost, m->stream));
+  DP_CUDA_TRY(m, cudaStreamSynchronize(m->stream));
+  return DP_OK;
+}
+
+dp_status dp_atom_virial(dp_model* h, double* atom_virial) {
+  if (!h || !atom_virial) return DP_ERR_ARG;
+  Model* m = &h->m;
+  if (m->natoms < 1) { m->last_error = "no state to evaluate"; return DP_ERR_ARG; }
+  const int N = m->natoms;
+  if (is_mixed(m)) {
+    DP_CUDA_TRY(m, cudaMemsetAsync(m->vir_atom, 0, sizeof(double) * 9 * (size_t)N, m->stream));
+    DP_TRY(launch_mix_atom_virial(m, N));
+  }
+  return launch_atom_virial_out(m, N, atom_virial);
 }
 
 dp_status dp_tabulate(dp_model* h, double x_min, double x_max, int n_intervals) {

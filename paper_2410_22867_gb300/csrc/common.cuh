@@ -22,6 +22,7 @@ constexpr int kKD = kN3 * kM2;  // 1600, descriptor length
 constexpr int kEmbParams = kN1 + kN1 + kN1 * kN2 + kN2 + kN2 * kN3 + kN3;       // 6450
 constexpr int kFitParams = kKD * kF + kF + kF * kF + kF + kF * kF + kF + kF + 1;  // 500161
 constexpr int kMaxTypes = 4;
+constexpr int kRdfMaxCells = 24576;  // dp_rdf: ntypes^2 * nbins histogram cells at most
 // parameter gradient: centre atoms per chunk, neighbour rows per chunk of the embedding reverse
 constexpr int kPgAtoms = 2048, kPgRows = 16384;
 
@@ -96,6 +97,7 @@ struct Model {
   // coefficients [pair][interval][100][8] in FP64 and FP32 (tab.cu).  tab_mem owns both.
   int tab_n = 0;
   double tab_x0 = 0.0, tab_h = 0.0;
+  unsigned long long* rdf_hist = nullptr;  // [kRdfMaxCells] pair-distance histogram (dp_rdf)
   double* tab64 = nullptr;
   float* tab32 = nullptr;
   void* tab_mem = nullptr;
@@ -289,7 +291,12 @@ dp_status launch_delta(Model* m, int N);
 dp_status launch_format(Model* m, int N);
 dp_status launch_get_nlist(Model* m, int N, int* nlist, int* images);
 // tab.cu
-dp_status launch_tabulate(Model* m, double x0, double x1, int n);  // synchronous; n = 0 drops the table
+dp_status launch_tabulate(Model* m, double x0, double x1, int n);
+// diag.cu
+dp_status launch_rdf(Model* m, int nbins, double r_max, unsigned long long* hist_dev);
+dp_status launch_atom_virial_out(Model* m, int N, double* out);
+// mix_embed.cu: the embedding backward again, accumulating only the per-atom (centre) virial into vir_atom
+dp_status launch_mix_atom_virial(Model* m, int N);  // synchronous; n = 0 drops the table
 // simt.cu
 dp_status launch_pad_rows(Model* m);  // pad64 / pad32 from the current weights (synchronous caller)
 dp_status launch_descriptor(Model* m, int N);

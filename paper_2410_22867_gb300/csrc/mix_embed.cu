@@ -725,7 +725,9 @@ __device__ void load_bwd_ops(const float* __restrict__ W, unsigned char* sB2, un
 // features m and m + 50 together, so the residual part dG[m] + dG[m + 50] of dE/dh2 is final
 // when formed; it is parked in the TMEM columns of z3 just read, and added back after the
 // dh2' product.  dR_hat and dG use dE/dT and G in FP32 on the CUDA cores.
-template <bool F16, bool TAB>
+// ATOMVIR: a second pass over the stored state that accumulates only the per-atom (centre)
+// virial -sum g (x) d into a.vir_atom (FP64) and leaves forces and per-replica virials alone.
+template <bool F16, bool TAB, bool ATOMVIR = false>
 __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
   extern __shared__ unsigned char sraw[];
   unsigned char* sm = align1024(sraw);
@@ -1033,7 +1035,35 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
       const float common = (dR[0] * dsr + dq * proj) * rinv;
 #pragma unroll
       for (int c = 0; c < 3; ++c) g3[c] = common * f.d[c] + qv * dR[1 + c];
+    }
+    if (ATOMVIR) {
+      // this row's -g (x) d, summed over the rows of each centre atom of the warp
+      float vr[9];
 #pragma unroll
+      for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) vr[3 * p + q] = valid ? -g3[p] * f.d[q] : 0.f;
+      const int my = valid ? f.la : -1;
+      unsigned todo = __ballot_sync(0xffffffffu, valid);
+      while (todo) {
+        const int leader = __ffs(todo) - 1;
+        const int seg = __shfl_sync(0xffffffffu, my, leader);
+        const bool in = (my == seg);
+        const unsigned mask = __ballot_sync(0xffffffffu, in);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          float v = in ? vr[q] : 0.f;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == leader) atomicAdd(&a.vir_atom[((size_t)ti.a0 + seg) * 9 + q], (double)v);
+        }
+        todo &= ~mask;
+      }
+      __syncthreads();
+      cur += ti.nrows;
+      continue;
+    }
+    if (valid) {
       tc::red_add_v4(a.force32 + 4 * (size_t)f.j, -g3[0], -g3[1], -g3[2], 0.f);
       const int rep = sRep[(it & 1) * kRows + t];
       if (rep != vrep) {
@@ -1075,7 +1105,7 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
   tc::cp_async_wait_all();
   if (dT_pending) tc::mbar_wait(&dbar, dphase, a.err);
   // flush the virial accumulators: one warp reduction when all lanes hold the same replica
-  {
+  if (!ATOMVIR) {
     const int r0 = __shfl_sync(0xffffffffu, vrep, 0);
     if (__all_sync(0xffffffffu, vrep == r0)) {
       if (r0 >= 0) {
@@ -1420,6 +1450,21 @@ dp_status launch_mix_embed_backward(Model* m, int N) {
   bk<<<grid, kRows, kBwdSmem, m->stream>>>(a);
   k_fold_force32<<<cdiv(3L * N, 256), 256, 0, m->stream>>>(3 * N, m->force32, m->force);
   m->launches += 3;
+  DP_LAUNCH_CHECK(m);
+  return DP_OK;
+}
+
+dp_status launch_mix_atom_virial(Model* m, int N) {
+  MixArgs a = make_mix_args(m, N);
+  const bool f16 = m->prec == DP_MIX_FP16;
+  const bool tab = m->tab_n > 0;
+  auto bk = f16 ? (tab ? k_mix_embed_bwd<true, true, true> : k_mix_embed_bwd<true, false, true>)
+                : (tab ? k_mix_embed_bwd<false, true, true> : k_mix_embed_bwd<false, false, true>);
+  const void* fn = reinterpret_cast<const void*>(bk);
+  DP_CUDA_TRY(m, ensure_smem(fn, kBwdSmem));
+  const int grid = tuned_grid(m, 1, num_sms() * blocks_per_sm(fn, kRows, kBwdSmem, kTmemCols));
+  bk<<<grid, kRows, kBwdSmem, m->stream>>>(a);
+  m->launches += 1;
   DP_LAUNCH_CHECK(m);
   return DP_OK;
 }

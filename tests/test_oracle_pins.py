@@ -680,3 +680,49 @@ def test_tabulated_model_forces_and_energy():
             xm = s.coords.copy(); xm[i, a] -= h
             fd = -(m.energy(xp, s.types, s.box) - m.energy(xm, s.types, s.box)) / (2 * h)
             assert fd == pytest.approx(r["forces"][i, a], rel=1e-6, abs=1e-8)
+
+
+# ----------------------------------------------------------------- per-atom virial and RDF
+def test_atom_virial_is_strain_derivative_of_atom_energy():
+    # E_i depends only on the pair vectors of i's neighbours, so under a homogeneous strain
+    # (1 + eps e_ab) the derivative of E_i is -W_i[a][b] with W_i = -sum_j g_ij (x) d_ij
+    w = _normalised_water()
+    m = oracle.Model(w.to_blob())
+    s = synth.water_box(16, 2)
+    r = m.compute(s.coords, s.types, s.box, atom_virial=True)
+    W = r["atom_virial"]
+    np.testing.assert_allclose(W.sum(0), r["virial"], rtol=1e-12, atol=1e-12)
+    eps = 1e-6
+    for a in range(3):  # normal strain of the periodic box along a
+        def Ei(e):
+            G = np.eye(3); G[a, a] += e
+            return m.compute(s.coords @ G.T, s.types, (s.box.reshape(3, 3) @ G.T).ravel(),
+                             forces=False)["atom_energy"]
+        dE = (Ei(eps) - Ei(-eps)) / (2 * eps)
+        np.testing.assert_allclose(-dE, W[:, a, a], rtol=1e-6, atol=1e-8)
+    # off-diagonal: a free cluster (no box constraint), shear strain applied to the coordinates
+    L = 60.0
+    cl = synth.water_box(4, 5)
+    x = cl.coords - cl.coords.mean(0) + L / 2
+    box = np.diag([L, L, L]).ravel()
+    rc_ = m.compute(x, cl.types, box, atom_virial=True)
+    for a, b in ((0, 1), (1, 2), (2, 0)):
+        def Ei(e):
+            G = np.eye(3); G[a, b] += e
+            return m.compute((x - L / 2) @ G.T + L / 2, cl.types, box, forces=False)["atom_energy"]
+        dE = (Ei(eps) - Ei(-eps)) / (2 * eps)
+        np.testing.assert_allclose(-dE, rc_["atom_virial"][:, a, b], rtol=1e-6, atol=1e-8)
+
+
+def test_rdf_of_perfect_fcc_counts_the_shells():
+    # FCC shells within 8 A (a = 3.634): radii a sqrt(k/2), coordination 12, 6, 24, 12, 24, 8, 48, 6, 36
+    c = synth.copper_fcc(6, 0, sigma=0.0)
+    w = synth.copper_weights()
+    m = oracle.Model(w.to_blob())
+    nbins, rmax = 800, 8.0
+    counts = m.rdf(c.coords, c.types, c.box, nbins, rmax)[0, 0]
+    shells = {1: 12, 2: 6, 3: 24, 4: 12, 5: 24, 6: 8, 7: 48, 8: 6, 9: 36}
+    expect = np.zeros(nbins, dtype=np.int64)
+    for k, n in shells.items():
+        expect[int(3.634 * math.sqrt(k / 2) / (rmax / nbins))] += n * c.natoms
+    np.testing.assert_array_equal(counts.astype(np.int64), expect)
