@@ -24,7 +24,9 @@ template <>
 struct PeakT<P_DFMA> { using type = double; };
 
 template <int OP>
-__device__ __forceinline__ typename PeakT<OP>::type peak_step(typename PeakT<OP>::type x) {
+__device__ __forceinline__ typename PeakT<OP>::type peak_step(typename PeakT<OP>::type x,
+                                                              typename PeakT<OP>::type mul,
+                                                              typename PeakT<OP>::type add) {
   if constexpr (OP == P_TANH) {
     float y;
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -38,9 +40,9 @@ __device__ __forceinline__ typename PeakT<OP>::type peak_step(typename PeakT<OP>
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x + 1.f));
     return y;
   } else if constexpr (OP == P_FFMA) {
-    return fmaf(x, 0.9999f, 1e-4f);
+    return fmaf(x, mul, add);
   } else {
-    return fma(x, 0.9999, 1e-4);
+    return fma(x, mul, add);
   }
 }
 
@@ -49,15 +51,17 @@ __device__ __forceinline__ typename PeakT<OP>::type peak_step(typename PeakT<OP>
 __device__ float g_sink_f;
 __device__ double g_sink_d;
 
+// mul and add arrive as kernel arguments, so the FMA operands are registers (not constants).
 template <int OP>
-__global__ void __launch_bounds__(kPeakThreads) k_peak(int iters) {
+__global__ void __launch_bounds__(kPeakThreads) k_peak(int iters, typename PeakT<OP>::type mul,
+                                                       typename PeakT<OP>::type add) {
   using T = typename PeakT<OP>::type;
   T x[kChains];
 #pragma unroll
   for (int c = 0; c < kChains; ++c) x[c] = T(0.25) + T(0.01) * T((threadIdx.x + c) & 31);
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
-    for (int c = 0; c < kChains; ++c) x[c] = peak_step<OP>(x[c]);
+    for (int c = 0; c < kChains; ++c) x[c] = peak_step<OP>(x[c], mul, add);
   }
   T acc = T(0);
 #pragma unroll
@@ -85,7 +89,8 @@ dp_status time_peak(int iters, double per_instr, double* rate, std::string& why)
   if (status == DP_OK && (e = cudaEventCreate(&e1)) != cudaSuccess) fail("event", e);
   for (int r = 0; r < 4 && status == DP_OK; ++r) {  // launch 0 warms up
     cudaEventRecord(e0, st);
-    k_peak<OP><<<grid, kPeakThreads, 0, st>>>(iters);
+    k_peak<OP><<<grid, kPeakThreads, 0, st>>>(iters, typename PeakT<OP>::type(0.9999),
+                                              typename PeakT<OP>::type(1e-4));
     cudaEventRecord(e1, st);
     if ((e = cudaEventSynchronize(e1)) != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) {
       fail("peak kernel", e);
