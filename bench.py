@@ -373,6 +373,9 @@ def run_mine(args, world, rank, local):
         # errors of every precision on the normalised models (environment statistics, O(1) rows)
         if args.ladder_steps > 0:
             extra["normalised_errors"] = normalised_errors(stream)
+        # latency: the 192-atom water box, microseconds per MD step
+        if args.latency_steps > 0:
+            extra["latency"] = latency_leg(args, stream)
         # the water box of the same model family
         if args.water_steps > 0 and args.workload != "water12k":
             extra["water"] = water_leg(args, stream)
@@ -586,6 +589,45 @@ def batch_leg(args, stream):
             "autotuned_grids": dict(zip(["embedding_forward", "embedding_backward", "dE_dT", "descriptor"], grids))}
 
 
+def latency_leg(args, stream):
+    """Latency of one MD step on the smallest workload, 64 H2O (192 atoms): microseconds per
+    step with graph replay (each step = half kick, drift, list filter or rebuild, force
+    evaluation, half kick), and the kernels launched per step."""
+    import torch
+    import paper_2410_22867_gb300 as dp
+    from paper_2410_22867_gb300 import synth
+    s = synth.water_box(64, 0)
+    w = synth.water_weights(1001)
+    v0 = synth.maxwell_boltzmann(s.masses()[s.types], 300.0, 77)
+    out = {"workload": "64 H2O (192 atoms), r_c 6 A, sel 46/92, NVE dt 0.5 fs, rebuild every 10 steps",
+           "steps": args.latency_steps}
+    for prec in ("mix_fp16", "fp32", "fp64"):
+        with torch.cuda.stream(stream):
+            m = dp.DPModel(w, prec, max_atoms=s.natoms, skin=2.0, stream=stream)
+            x = torch.tensor(s.coords, device="cuda")
+            v = torch.tensor(v0, device="cuda")
+            t = torch.tensor(s.types, device="cuda")
+            st = m.md_state(x, v, t, s.box, s.masses(), rebuild_every=REBUILD)
+            m.verlet(st, DT_FS, 3, capture_graph=True)
+            st.resume = 1
+            k0 = m.kernel_launches()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            m.verlet(st, DT_FS, args.latency_steps, capture_graph=True, sync=False)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            m.sync()
+            us = ev0.elapsed_time(ev1) * 1e3 / args.latency_steps
+            kernels = (m.kernel_launches() - k0) / args.latency_steps
+            ph = m.phase_times(10)
+            m.close()
+        out[prec] = {"us_per_step": us, "kernels_per_step": kernels,
+                     "ns_per_day_0.5fs": (1e6 / us) * 0.5 * 86400 * 1e-6, "atom_steps_per_s": s.natoms / (us * 1e-6),
+                     "phases_us": {k: round(v * 1e3, 1) for k, v in kernel_times(ph).items()}}
+    return out
+
+
 def water_leg(args, stream):
     """Throughput of the 4096-H2O box (12,288 atoms) in the same precision: MD with graph
     replay; the window stays before the first random-weight collapse (step ~31)."""
@@ -691,6 +733,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=22)  # + 3 warm-up: before the first collapse (step ~35)
     ap.add_argument("--water-steps", type=int, default=20)  # + 4 warm-up: before the first collapse (step ~31)
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--latency-steps", type=int, default=25, help="timed MD steps of the 192-atom latency leg "
+                                                                   "(0 skips it)")
     ap.add_argument("--ladder-steps", type=int, default=20, help="timed MD steps per precision of the ladder "
                                                                   "(FP64: a tenth, at least 2); 0 skips the ladder")
     args = ap.parse_args()
