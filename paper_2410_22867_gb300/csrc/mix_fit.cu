@@ -33,7 +33,11 @@ namespace dpg {
 namespace {
 
 constexpr int kFR = 128;                  // rows (atoms) per tile = TMEM lanes
-constexpr int kThreads = 256;             // two warpgroups
+constexpr int kEpi = 256;                 // epilogue threads: warps 0..7, two per TMEM lane quarter
+constexpr int kMmaWarp = 8;               // lane 0 issues every tcgen05.mma
+constexpr int kLoadWarp = 9;              // lane 0 of warps 9..11 issue the TMA loads
+constexpr int kLoaders = 3;
+constexpr int kThreads = kEpi + 32 + 32 * kLoaders;
 constexpr int kBChunk = 160;              // N chunk of the B1 GEMM
 constexpr uint32_t kBlk = 16384;          // one [128 x 64] 16-bit operand block
 constexpr uint32_t kWB = 240 * 128;       // one [240 x 64] 16-bit weight block (30 KB)
@@ -43,18 +47,19 @@ constexpr uint32_t kSt = 8 * kBlk;        // 64 KB: four split staging slots
 constexpr uint32_t kSSlot = 128 * 128;    // split job: [128 x 64] 16-bit weight block (16 KB)
 constexpr int kSSlots = 4;
 constexpr uint32_t kStageRow = kBChunk * 2 + 16;  // padded row of the dE/dD staging tile (bytes)
-constexpr uint32_t kL1Slot = kBlk + kWB;  // L1 job: A block + W1T block (46 KB), slots over [0, kPrm)
-constexpr int kL1Slots = 4;
-constexpr uint32_t kB1Slot = kBChunk * 128;  // B1 job: W1 block [160 x 64] (20 KB), slots over [kXLo, kPrm)
+constexpr uint32_t kL1Slot = kBlk + kWB;  // L1 job: A block + W1T block (46 KB)
+constexpr int kL1Slots = 3;               // slots over [0, kStage)
+constexpr uint32_t kB1Slot = kBChunk * 128;  // B1 job: W1 block [160 x 64] (20 KB), slots over [kXLo, kStage)
 constexpr int kB1Slots = 5;
 // dE/dD of one B1 chunk is staged here [128 rows x 160 fp16] and written out in whole row
-// segments; it overlays L1 slot 3 and the split slots, both idle during B1
+// segments; it overlays the split slots, idle during B1
 constexpr uint32_t kStage = kXLo + kB1Slots * kB1Slot;
 constexpr uint32_t kPrm = kStage + kFR * kStageRow;  // b1, b2, b3, w4
 constexpr int kSplitSlot = 6;             // barrier index of the first split staging slot (6..9)
 constexpr int kSplitJobs = 16;            // per split GEMM: 4 K blocks x 2 N halves x {hi, lo}
 constexpr int kL1Jobs = kKD / 64;         // 25
-constexpr int kB1Jobs = 4 * (kKD / kBChunk);  // 40
+constexpr int kB1Chunks = kKD / kBChunk;  // 10
+constexpr int kB1Jobs = 4 * kB1Chunks;    // 40
 
 struct FitMaps {
   CUtensorMap D;                     // [rows = max_atoms][1600]
@@ -77,22 +82,70 @@ struct FitArgs {
   int* err;
 };
 
-// Staging slots: one full/empty mbarrier pair each; `uses` counts completed jobs per slot.
-struct Slots {
-  uint64_t* full;   // [10]: L1 0..3, B1 0..5, split 6..9
-  uint64_t* empty;  // [10]
-  uint32_t uses[10];
-};
-
 __device__ __forceinline__ unsigned char* align1k(unsigned char* p) {
   uint32_t a = tc::smem_u32(p);
   return p + ((1024u - (a & 1023u)) & 1023u);
 }
 
-// Before loading into slot k: wait until the MMAs of its previous job released it.
-__device__ __forceinline__ void slot_acquire(Slots& s, int k, uint32_t loads_done, int* err, bool& ok) {
-  if (loads_done > 0) ok = tc::mbar_wait(&s.empty[k], (loads_done - 1) & 1u, err) && ok;
-}
+// The staging slots: barrier k (full: data landed; empty: the MMAs that read it completed) for
+// L1 slots 0..2, B1 slots 0..4 and split slots 6..9.  `uses[k]` counts the jobs through slot k.
+//   L1 job j      -> slot j % 3        B1 job j -> slot j % 5        split job i -> slot 6 + i % 4
+//
+// Each TMA thread processes its own copies one after another (about 0.3 us each from L2,
+// whatever the box size), so three loader threads share the slots: slot k belongs to loader
+// k % 3, which keeps the successive uses of a slot in one thread's program order.  The loaders
+// sit in separate warps: lanes of one warp waiting on different barriers would take turns.
+struct Loader {
+  uint64_t* full;
+  uint64_t* empty;
+  unsigned char* sm;
+  const FitMaps* mp;
+  int lane;               // loader index 0..2
+  int* err;
+  bool ok;
+  uint32_t uses[10];
+  uint32_t issued[10];     // copies this lane started into slot k (for the final drain)
+  uint64_t keep, stream;   // L2 policies: weights (evict_last), streamed D (evict_first)
+  // Every CTA walks the shared weight matrices starting at a different block, so the SMs do
+  // not all request the same L2 lines at the same moment.
+  int rot_l1, rot_s, rot_b1;
+
+  __device__ bool begin(int k, uint32_t bytes) {
+    if (k % kLoaders != lane || !ok) return false;
+    if (uses[k] > 0) ok = tc::mbar_wait(&empty[k], (uses[k] - 1) & 1u, err) && ok;
+    if (!ok) return false;
+    tc::mbar_arrive_expect_tx(&full[k], bytes);
+    issued[k] = uses[k] + 1;
+    return true;
+  }
+  // L1 job j: D rows row0.. and the W1T block of K block (j + rot) % 25
+  __device__ void l1(int ty, int row0, int j) {
+    const int k = j % kL1Slots, kb = (j + rot_l1) % kL1Jobs;
+    if (begin(k, kL1Slot)) {
+      unsigned char* a = sm + k * kL1Slot;
+      tc::tma_load_2d_hint(a, &mp->D, &full[k], 64 * kb, row0, stream);
+      tc::tma_load_2d_hint(a + kBlk, &mp->W1T[ty], &full[k], 64 * kb, 0, keep);
+    }
+    uses[k] += 1;
+  }
+  // split job i of GEMM g: weight half i & 1 (0 = hi, 1 = lo), N half (i >> 1) & 1 (rows 0..127
+  // or 128..255; rows past 240 are zero-filled by the TMA) of K block ((i >> 2) + rot) % 4
+  __device__ void split(int ty, int g, int i) {
+    const int k = kSplitSlot + (i & 3);
+    if (begin(k, kSSlot))
+      tc::tma_load_2d_hint(sm + kSt + (i & 3) * kSSlot, &mp->S[ty][g][i & 1], &full[k], 64 * (((i >> 2) + rot_s) & 3),
+                           128 * ((i >> 1) & 1), keep);
+    uses[k] += 1;
+  }
+  // B1 job j: W1 rows of chunk (j / 4 + rot) % 10, K block j % 4
+  __device__ void b1(int ty, int j) {
+    const int k = j % kB1Slots;
+    if (begin(k, kB1Slot))
+      tc::tma_load_2d_hint(sm + kXLo + k * kB1Slot, &mp->W1[ty], &full[k], 64 * (j & 3),
+                           kBChunk * (((j >> 2) + rot_b1) % kB1Chunks), keep);
+    uses[k] += 1;
+  }
+};
 
 template <bool F16>
 __device__ __forceinline__ void store_x16(unsigned char* sm, int row, int col0, const float* v, bool split) {
@@ -147,403 +200,407 @@ __device__ __forceinline__ void unpack_g16(uint4 q0, uint4 q1, float* v) {
   }
 }
 
-// ---- issuing thread (thread 0) helpers
-struct Issuer {
-  Slots* s;
-  unsigned char* sm;
-  const FitMaps* mp;
-  int ty, row0;
-  int* err;
-  bool* ok;
-  uint64_t keep, stream;  // L2 policies: weights (evict_last), streamed D (evict_first)
-  // Every CTA walks the shared weight matrices starting at a different block, so the
-  // SMs do not all request the same L2 lines at the same moment.
-  int rot_l1, rot_s, rot_b1;
-  __device__ int l1_block(int j) const { return (j + rot_l1) % kL1Jobs; }
-  __device__ int split_block(int kb) const { return (kb + rot_s) & 3; }
-  __device__ int b1_chunk(int n) const { return (n + rot_b1) % (kKD / kBChunk); }
-
-  // L1 job j: A (D rows row0.., K block l1_block(j)) + the matching W1T block into slot j % 4
-  __device__ void load_l1(int j) {
-    const int k = j % kL1Slots;
-    slot_acquire(*s, k, s->uses[k], err, *ok);
-    unsigned char* a = sm + k * kL1Slot;
-    const int kb = l1_block(j);
-    tc::mbar_arrive_expect_tx(&s->full[k], kL1Slot);
-    tc::tma_load_2d_hint(a, &mp->D, &s->full[k], 64 * kb, row0, stream);
-    tc::tma_load_2d_hint(a + kBlk, &mp->W1T[ty], &s->full[k], 64 * kb, 0, keep);
-  }
-  // B1 job j: W1 rows of chunk b1_chunk(j / 4), K block j % 4, into slot j % 6 (X_lo + split area)
-  __device__ void load_b1(int j) {
-    const int k = j % kB1Slots;
-    slot_acquire(*s, k, s->uses[k], err, *ok);
-    tc::mbar_arrive_expect_tx(&s->full[k], kB1Slot);
-    tc::tma_load_2d_hint(sm + kXLo + k * kB1Slot, &mp->W1[ty], &s->full[k], 64 * (j & 3), kBChunk * b1_chunk(j >> 2),
-                         keep);
-  }
-  // split job i of GEMM g: weight half i & 1 (0 = hi, 1 = lo), N half (i >> 1) & 1 (rows 0..127
-  // or 128..255; rows past 240 are zero-filled by the TMA) of K block split_block(i >> 2),
-  // into split slot i & 3
-  __device__ void load_split(int g, int i) {
-    const int k = kSplitSlot + (i & 3);
-    slot_acquire(*s, k, s->uses[k], err, *ok);
-    tc::mbar_arrive_expect_tx(&s->full[k], kSSlot);
-    tc::tma_load_2d_hint(sm + kSt + (i & 3) * kSSlot, &mp->S[ty][g][i & 1], &s->full[k], 64 * split_block(i >> 2),
-                         128 * ((i >> 1) & 1), keep);
-  }
-  // the first three jobs of split GEMM g (issued under the preceding epilogue)
-  __device__ void prefetch_split(int g) {
-    for (int i = 0; i < kSSlots - 1; ++i) load_split(g, i);
-  }
-  // wait for the data of the oldest outstanding job in slot k and mark it consumed after the MMAs
-  __device__ void consume_begin(int k) {
-    *ok = tc::mbar_wait(&s->full[k], s->uses[k] & 1u, err) && *ok;
-    tc::tc_fence_after();
-  }
-  __device__ void consume_end(int k) {
-    tc::mma_commit(&s->empty[k]);
-    s->uses[k] += 1;
-  }
+// Tile order shared by every role: tile -> (type, first row, rows).
+struct TileOf {
+  int ty, row0, nrow;
 };
+__device__ __forceinline__ TileOf tile_of(int tile, const int* s_tiles, const FitArgs& a) {
+  int ty = 0;
+  while (ty + 1 < a.ntypes && tile >= s_tiles[ty + 1]) ++ty;
+  const int k = tile - s_tiles[ty];
+  return {ty, a.type_off[ty] + k * kFR, min(kFR, a.type_count[ty] - k * kFR)};
+}
 
+// Three warp roles run each tile's pipeline concurrently:
+//   warps 9..11 (lane 0) TMA loads into the staging slots, as soon as a slot is free and the
+//                        buffer it overlays is no longer read (events rf: L1 MMAs done, B2 MMAs
+//                        done, B1 MMAs done);
+//   warp 8 (lane 0)      the MMAs of each GEMM once its operands landed and the epilogue that
+//                        writes its A operand finished (events epi, alternating barriers);
+//   warps 0..7           the epilogues after each GEMM's accumulator is complete (accb).
+// Each waits only with bounded polls; a role that gives up sets the shared abort flag and the
+// others leave their loops at their next wait.
 template <bool F16>
 __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__ FitMaps maps, FitArgs a) {
   extern __shared__ unsigned char sraw[];
   unsigned char* sm = align1k(sraw);
   float* prm = reinterpret_cast<float*>(sm + kPrm);  // b1, b2, b3, w4 [4][240]
-  __shared__ uint64_t full[10], empty[10], accb[2];
+  __shared__ uint64_t full[10], empty[10], accb[2], epib[2], rf[3], fin;
   __shared__ uint32_t tslot;
   __shared__ int s_tiles[kMaxTypes + 1];
+  __shared__ int s_abort;
   __shared__ float sE[kFR];
-  const int t = threadIdx.x, w = t >> 5;
-  const int row = t & (kFR - 1), half = t >> 7;  // TMEM lane / atom, column half
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
 
   if (t == 0) {
     for (int q = 0; q < 10; ++q) { tc::mbar_init(&full[q], 1); tc::mbar_init(&empty[q], 1); }
-    for (int q = 0; q < 2; ++q) tc::mbar_init(&accb[q], 1);
+    for (int q = 0; q < 2; ++q) { tc::mbar_init(&accb[q], 1); tc::mbar_init(&epib[q], 1); }
+    for (int q = 0; q < 3; ++q) tc::mbar_init(&rf[q], 1);
+    tc::mbar_init(&fin, 1);
     tc::mbar_fence_init();
     int acc = 0;
     for (int ty = 0; ty < a.ntypes; ++ty) { s_tiles[ty] = acc; acc += (a.type_count[ty] + kFR - 1) / kFR; }
     s_tiles[a.ntypes] = acc;
-    tc::tma_prefetch_desc(&maps.D);
+    s_abort = 0;
   }
   if (w == 0) { tc::tmem_alloc(&tslot, 512); tc::tmem_relinquish(); }
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = tslot;
-  const uint32_t lane_off = (uint32_t)(32 * (w & 3)) << 16;
-  const uint32_t acc0 = tmem + lane_off, acc1 = tmem + 256 + lane_off;
-  const uint32_t resid = acc1;
-  Slots sl;
-  sl.full = full; sl.empty = empty;
-  for (int q = 0; q < 10; ++q) sl.uses[q] = 0;
-  uint32_t aph[2] = {0, 0};
-  bool ok = true;
-  int cur_type = -1;
   const int ntiles = s_tiles[a.ntypes];
-  const uint32_t id240 = tc::idesc_f16(128, 240, F16), id160 = tc::idesc_f16(128, kBChunk, F16);
-  const uint32_t id128 = tc::idesc_f16(128, 128, F16);
-  // columns of this thread's half: 16-column chunks [c_beg, c_end) of 15 (240 columns)
-  const int c_beg = half ? 8 : 0, c_end = half ? 15 : 8;
-  Issuer is;
-  is.s = &sl; is.sm = sm; is.mp = &maps; is.err = a.err; is.ok = &ok;
-  is.keep = tc::make_policy_evict_last();
-  is.stream = tc::make_policy_evict_first();
-  is.rot_l1 = blockIdx.x % kL1Jobs;
-  is.rot_s = blockIdx.x & 3;
-  is.rot_b1 = blockIdx.x % (kKD / kBChunk);
+  volatile int* abort_flag = &s_abort;
 
-  auto sync_all = [&]() {
-    tc::fence_async_smem();
-    tc::tc_fence_before();
-    __syncthreads();
-    tc::tc_fence_after();
-  };
-  auto wait_acc = [&](int r) {
-    ok = tc::mbar_wait(&accb[r], aph[r], a.err) && ok;
-    aph[r] ^= 1u;
-    tc::tc_fence_after();
-  };
-  // thread 0: the MMAs of split GEMM g (its first three jobs were prefetched).  Each job is
-  // one N half (128 output columns) of one K block, hi or lo weights; after issuing job i the
-  // slot of job i - 1 is refilled, so three loads stay in flight behind the MMAs.
-  auto issue_split = [&](int g) {
-    for (int i = 0; i < kSplitJobs && ok; ++i) {
-      const int k = kSplitSlot + (i & 3);
-      is.consume_begin(k);
-      const int kx = is.split_block(i >> 2);
-      const uint32_t d = tmem + 128u * (uint32_t)((i >> 1) & 1);
-      const uint32_t xh = tc::smem_u32(sm + kXHi + kx * kBlk), xl = tc::smem_u32(sm + kXLo + kx * kBlk);
-      const uint32_t wv = tc::smem_u32(sm + kSt + (i & 3) * kSSlot);
-      if ((i & 1) == 0) {  // hi weights: x_hi w_hi + x_lo w_hi
-        tc::mma_kblock(d, xh, wv, id128, i >= 4, 4);
-        tc::mma_kblock(d, xl, wv, id128, true, 4);
-      } else {             // lo weights: x_hi w_lo
-        tc::mma_kblock(d, xh, wv, id128, true, 4);
+  if (w >= kLoadWarp) {
+    // ------------------------------------------------------------------ TMA loads
+    if (lane == 0) {
+      if (w == kLoadWarp) tc::tma_prefetch_desc(&maps.D);
+      Loader L;
+      L.full = full; L.empty = empty; L.sm = sm; L.mp = &maps; L.lane = w - kLoadWarp; L.err = a.err; L.ok = true;
+      for (int q = 0; q < 10; ++q) L.uses[q] = L.issued[q] = 0;
+      L.keep = tc::make_policy_evict_last();
+      L.stream = tc::make_policy_evict_first();
+      L.rot_l1 = blockIdx.x % kL1Jobs;
+      L.rot_s = blockIdx.x & 3;
+      L.rot_b1 = blockIdx.x % kB1Chunks;
+      uint32_t rph[3] = {0, 0, 0};
+      auto wait_rf = [&](int r) {
+        L.ok = L.ok && tc::mbar_wait(&rf[r], rph[r] & 1u, a.err);
+        rph[r] += 1;
+      };
+      for (int tile = blockIdx.x; tile < ntiles && L.ok && !*abort_flag; tile += gridDim.x) {
+        const TileOf T = tile_of(tile, s_tiles, a);
+        if (tile != (int)blockIdx.x) wait_rf(2);  // the B1 MMAs of the previous tile read X and the B1 slots
+        for (int j = 0; j < kL1Jobs; ++j) L.l1(T.ty, T.row0, j);
+        wait_rf(0);  // the split slots overlay L1 slot 2
+        for (int g = 0; g < 4; ++g)
+          for (int i = 0; i < kSplitJobs; ++i) L.split(T.ty, g, i);
+        wait_rf(1);  // the B1 slots overlay X_lo (read by the B2 MMAs) and the split slots
+        for (int j = 0; j < kB1Jobs; ++j) L.b1(T.ty, j);
       }
-      is.consume_end(k);
-      if (i + kSSlots - 1 < kSplitJobs) is.load_split(g, i + kSSlots - 1);
+      if (!L.ok) *abort_flag = 1;
+      // copies still in flight land before the CTA can finish
+      for (int q = 0; q < 10; ++q)
+        if (L.issued[q] > 0) tc::mbar_wait(&full[q], (L.issued[q] - 1) & 1u, a.err);
     }
-    tc::mma_commit(&accb[0]);
-  };
-
-  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    int ty = 0;
-    while (ty + 1 < a.ntypes && tile >= s_tiles[ty + 1]) ++ty;
-    const int k = tile - s_tiles[ty];
-    const int row0 = a.type_off[ty] + k * kFR;
-    const int nrow = min(kFR, a.type_count[ty] - k * kFR);
-    const bool valid = row < nrow;
-    const size_t grow = (size_t)row0 + row;
-    const float* P = a.w + a.fit_base + (long)ty * kFitParams;
-    is.ty = ty; is.row0 = row0;
-    if (ty != cur_type) {
-      for (int q = t; q < 4 * kF; q += kThreads) {
-        const int which = q / kF, c = q - which * kF;
-        const long off = which == 0 ? kFb1 : which == 1 ? kFb2 : which == 2 ? kFb3 : kFw4;
-        prm[q] = P[off + c];
-      }
-      cur_type = ty;
-      __syncthreads();
-    }
-    const float* b1 = prm;
-    const float* b2 = prm + kF;
-    const float* b3 = prm + 2 * kF;
-    const float* w4 = prm + 3 * kF;
-
-    // ---- L1: z1 = D W1, 4 slots over [0, kPrm), three jobs ahead
-    if (t == 0) {
-      for (int j = 0; j < kL1Slots - 1; ++j) is.load_l1(j);
-      for (int j = 0; j < kL1Jobs && ok; ++j) {
-        const int s = j % kL1Slots;
-        is.consume_begin(s);
-        unsigned char* st = sm + s * kL1Slot;
-        tc::mma_kblock(tmem, tc::smem_u32(st), tc::smem_u32(st + kBlk), id240, j > 0, 4);
-        is.consume_end(s);
-        // refill the slot of job j - 1 (MMAs of job j stay queued meanwhile)
-        if (j + kL1Slots - 1 < kL1Jobs) is.load_l1(j + kL1Slots - 1);
-      }
-      tc::mma_commit(&accb[0]);
-    }
-    __syncwarp();  // lanes 1..31 of warp 0 wait here, not in a polling loop beside the issuer
-    wait_acc(0);
-    if (t == 0) is.prefetch_split(0);  // prefetch under the epilogue
     __syncwarp();
-    // f1/f2 factors of this row are fetched ahead of the TMEM loop below
-#pragma unroll 1
-    for (int c = c_beg; c < c_end; ++c) {
-      float z[16], h[16], f[16];
-      tc::tmem_ld16(acc0 + 16 * c, z);
-      tc::tmem_wait_ld();
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        h[u] = tc::tanh_exp(z[u] + b1[16 * c + u]);
-        f[u] = 1.f - h[u] * h[u];
-      }
-      store_x16<F16>(sm, row, 16 * c, h, true);
-      tc::tmem_st16(resid + 16 * c, h);
-      if (valid) store_g16<F16>(a.f1 + grow * kF + 16 * c, f);
-    }
-    if (half == 1) {  // K columns 240..255 stay zero (hi and lo)
-      tc::st_chunk(sm + kXHi + 3 * kBlk, row, 48, make_uint4(0, 0, 0, 0));
-      tc::st_chunk(sm + kXHi + 3 * kBlk, row, 56, make_uint4(0, 0, 0, 0));
-      tc::st_chunk(sm + kXLo + 3 * kBlk, row, 48, make_uint4(0, 0, 0, 0));
-      tc::st_chunk(sm + kXLo + 3 * kBlk, row, 56, make_uint4(0, 0, 0, 0));
-    }
-    tc::tmem_wait_st();
-    sync_all();
-
-    // ---- L2: h2 = h1 + tanh(h1 W2 + b2)
-    if (t == 0) issue_split(0);
-    __syncwarp();
-    wait_acc(0);
-    if (t == 0) is.prefetch_split(1);
-    __syncwarp();
-#pragma unroll 1
-    for (int c = c_beg; c < c_end; ++c) {
-      float z[16], r[16], f[16];
-      tc::tmem_ld16(acc0 + 16 * c, z);
-      tc::tmem_ld16(resid + 16 * c, r);
-      tc::tmem_wait_ld();
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const float t2 = tc::tanh_exp(z[u] + b2[16 * c + u]);
-        r[u] += t2;
-        f[u] = 1.f - t2 * t2;
-      }
-      store_x16<F16>(sm, row, 16 * c, r, true);
-      tc::tmem_st16(resid + 16 * c, r);
-      if (valid) store_g16<F16>(a.f2 + grow * kF + 16 * c, f);
-    }
-    tc::tmem_wait_st();
-    sync_all();
-
-    // ---- L3: h3 = h2 + tanh(h2 W3 + b3), E_i, dz3
-    if (t == 0) issue_split(1);
-    __syncwarp();
-    wait_acc(0);
-    if (t == 0) is.prefetch_split(2);
-    __syncwarp();
-    float e = 0.f;
-#pragma unroll 1
-    for (int c = c_beg; c < c_end; ++c) {
-      float z[16], r[16], dz[16];
-      tc::tmem_ld16(acc0 + 16 * c, z);
-      tc::tmem_ld16(resid + 16 * c, r);
-      tc::tmem_wait_ld();
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const float t3 = tc::tanh_exp(z[u] + b3[16 * c + u]);
-        const float wv = w4[16 * c + u];
-        e = fmaf(r[u] + t3, wv, e);
-        dz[u] = wv * (1.f - t3 * t3);
-      }
-      store_x16<F16>(sm, row, 16 * c, dz, true);
-    }
-    if (half == 1) sE[row] = e;
-    sync_all();
-    if (half == 0 && valid)
-      a.e_atom[grow] = (double)e + (double)sE[row] + (double)P[kFb4] + (double)a.w[a.ebias_off + ty];
-
-    // ---- B3: dh2 = w4 + dz3 W3^T ; dz2 = dh2 (1 - t2^2)
-    if (t == 0) issue_split(2);
-    __syncwarp();
-    {  // fetch this row's 1 - t2^2 factors while the MMAs run
-      uint4 fq[16];
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const int cc = c_beg + c;
-        if (valid && cc < c_end) {
-          const uint4* src = reinterpret_cast<const uint4*>(a.f2 + grow * kF + 16 * cc);
-          fq[2 * c] = src[0];
-          fq[2 * c + 1] = src[1];
-        } else {
-          fq[2 * c] = fq[2 * c + 1] = make_uint4(0, 0, 0, 0);
-        }
-      }
-      wait_acc(0);
-      if (t == 0) is.prefetch_split(3);
-      __syncwarp();
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const int cc = c_beg + c;
-        if (cc < c_end) {
-          float z[16], f[16];
-          tc::tmem_ld16(acc0 + 16 * cc, z);
-          tc::tmem_wait_ld();
-          unpack_g16<F16>(fq[2 * c], fq[2 * c + 1], f);
-#pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            z[u] += w4[16 * cc + u];  // dh2
-            f[u] *= z[u];             // dz2
+  } else if (w == kMmaWarp) {
+    // ------------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      const uint32_t id240 = tc::idesc_f16(128, 240, F16), id160 = tc::idesc_f16(128, kBChunk, F16);
+      const uint32_t id128 = tc::idesc_f16(128, 128, F16);
+      const int rot_s = blockIdx.x & 3;
+      uint32_t uses[10];
+      for (int q = 0; q < 10; ++q) uses[q] = 0;
+      bool ok = true;
+      uint32_t ev = 0;
+      auto consume = [&](int k) {
+        ok = ok && tc::mbar_wait(&full[k], uses[k] & 1u, a.err);
+        tc::tc_fence_after();
+        return ok;
+      };
+      auto release = [&](int k) {
+        tc::mma_commit(&empty[k]);
+        uses[k] += 1;
+      };
+      auto wait_epi = [&]() {
+        ok = ok && tc::mbar_wait(&epib[ev & 1], (ev >> 1) & 1u, a.err);
+        ev += 1;
+        tc::tc_fence_after();
+        return ok;
+      };
+      // split GEMM: job i is one N half (128 output columns) of one K block with the hi or the lo
+      // weights
+      auto issue_split = [&]() {
+        for (int i = 0; i < kSplitJobs; ++i) {
+          const int k = kSplitSlot + (i & 3);
+          if (!consume(k)) return;
+          const int kx = ((i >> 2) + rot_s) & 3;
+          const uint32_t d = tmem + 128u * (uint32_t)((i >> 1) & 1);
+          const uint32_t xh = tc::smem_u32(sm + kXHi + kx * kBlk), xl = tc::smem_u32(sm + kXLo + kx * kBlk);
+          const uint32_t wv = tc::smem_u32(sm + kSt + (i & 3) * kSSlot);
+          if ((i & 1) == 0) {  // hi weights: x_hi w_hi + x_lo w_hi
+            tc::mma_kblock(d, xh, wv, id128, i >= 4, 4);
+            tc::mma_kblock(d, xl, wv, id128, true, 4);
+          } else {             // lo weights: x_hi w_lo
+            tc::mma_kblock(d, xh, wv, id128, true, 4);
           }
-          tc::tmem_st16(resid + 16 * cc, z);
-          store_x16<F16>(sm, row, 16 * cc, f, true);
+          release(k);
+        }
+      };
+      // B1 chunk n (TMEM region n & 1): four K blocks of dz1 (X_hi) against W1 rows
+      auto issue_b1 = [&](int n) {
+        for (int kb = 0; kb < 4; ++kb) {
+          const int k = (4 * n + kb) % kB1Slots;
+          if (!consume(k)) return;
+          tc::mma_kblock(tmem + 256 * (n & 1), tc::smem_u32(sm + kXHi + kb * kBlk),
+                         tc::smem_u32(sm + kXLo + k * kB1Slot), id160, kb > 0, 4);
+          release(k);
+        }
+        tc::mma_commit(&accb[n & 1]);
+      };
+      for (int tile = blockIdx.x; tile < ntiles && ok && !*abort_flag; tile += gridDim.x) {
+        // L1: z1 = D W1 into columns 0..239 (free: the previous tile's B1 drains are done)
+        for (int j = 0; j < kL1Jobs && ok; ++j) {
+          const int k = j % kL1Slots;
+          if (!consume(k)) break;
+          unsigned char* st = sm + k * kL1Slot;
+          tc::mma_kblock(tmem, tc::smem_u32(st), tc::smem_u32(st + kBlk), id240, j > 0, 4);
+          release(k);
+        }
+        tc::mma_commit(&accb[0]);
+        tc::mma_commit(&rf[0]);
+        // L2, L3, B3, B2: each after the epilogue that wrote its A operand
+        for (int g = 0; g < 4 && ok; ++g) {
+          if (!wait_epi()) break;
+          issue_split();
+          tc::mma_commit(&accb[0]);
+          if (g == 3) tc::mma_commit(&rf[1]);
+        }
+        // B1 in ten chunks over two TMEM regions: chunk n + 2 once chunk n has been drained
+        if (ok && wait_epi()) {
+          issue_b1(0);
+          issue_b1(1);
+          for (int n = 0; n < kB1Chunks && ok; ++n) {
+            if (!wait_epi()) break;
+            if (n + 2 < kB1Chunks) issue_b1(n + 2);
+            if (n + 2 == kB1Chunks - 1) tc::mma_commit(&rf[2]);
+          }
         }
       }
+      if (!ok) *abort_flag = 1;
+      // every MMA has completed before the TMEM is released
+      tc::mma_commit(&fin);
+      tc::mbar_wait(&fin, 0, a.err);
     }
-    tc::tmem_wait_st();
-    sync_all();
-
-    // ---- B2: dh1 = dh2 + dz2 W2^T ; dz1 = dh1 (1 - h1^2)
-    if (t == 0) issue_split(3);
     __syncwarp();
-    {
-      uint4 fq[16];
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const int cc = c_beg + c;
-        if (valid && cc < c_end) {
-          const uint4* src = reinterpret_cast<const uint4*>(a.f1 + grow * kF + 16 * cc);
-          fq[2 * c] = src[0];
-          fq[2 * c + 1] = src[1];
-        } else {
-          fq[2 * c] = fq[2 * c + 1] = make_uint4(0, 0, 0, 0);
-        }
-      }
-      wait_acc(0);
-      // the B1 slots overlay X_lo and the split staging, both free once B2's MMAs are done;
-      // its weights stream in under this epilogue
-      if (t == 0)
-        for (int j = 0; j < kB1Slots - 1; ++j) is.load_b1(j);
-      __syncwarp();
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const int cc = c_beg + c;
-        if (cc < c_end) {
-          float z[16], r[16], f[16];
-          tc::tmem_ld16(acc0 + 16 * cc, z);
-          tc::tmem_ld16(resid + 16 * cc, r);
-          tc::tmem_wait_ld();
-          unpack_g16<F16>(fq[2 * c], fq[2 * c + 1], f);
-#pragma unroll
-          for (int u = 0; u < 16; ++u) f[u] *= (z[u] + r[u]);
-          store_x16<F16>(sm, row, 16 * cc, f, false);  // B1 is a plain 16-bit GEMM
-        }
-      }
-    }
-    sync_all();
-
-    // ---- B1: dE/dD = dz1 W1^T in N chunks of 160 (4 K jobs each); TMEM regions alternate,
-    //      chunk n + 2 is issued once chunk n has been drained
-    constexpr int nch = kKD / kBChunk;
-    int next_load = kB1Slots - 1;
-    auto issue_b1_chunk = [&](int n) {
-      for (int kb = 0; kb < 4 && ok; ++kb) {
-        const int j = 4 * n + kb;
-        const int s = j % kB1Slots;
-        is.consume_begin(s);
-        tc::mma_kblock(tmem + 256 * (n & 1), tc::smem_u32(sm + kXHi + kb * kBlk),
-                       tc::smem_u32(sm + kXLo + s * kB1Slot), id160, kb > 0, 4);
-        is.consume_end(s);
-        // refill freed slots (the slot of job j - 1 at the latest) while job j's MMAs run
-        while (next_load < kB1Jobs && next_load <= j + kB1Slots - 1) is.load_b1(next_load++);
-      }
-      tc::mma_commit(&accb[n & 1]);
+  } else {
+    // ------------------------------------------------------------------ epilogues
+    const int row = t & (kFR - 1), half = t >> 7;  // TMEM lane / atom, column half
+    const uint32_t lane_off = (uint32_t)(32 * (w & 3)) << 16;
+    const uint32_t acc0 = tmem + lane_off, acc1 = tmem + 256 + lane_off;
+    const uint32_t resid = acc1;
+    // columns of this thread's half: 16-column chunks [c_beg, c_end) of 15 (240 columns)
+    const int c_beg = half ? 8 : 0, c_end = half ? 15 : 8;
+    uint32_t aph[2] = {0, 0};
+    uint32_t ev = 0;
+    bool ok = true;
+    int cur_type = -1;
+    auto wait_acc = [&](int r) {
+      ok = tc::mbar_wait(&accb[r], aph[r], a.err) && ok;
+      aph[r] ^= 1u;
+      tc::tc_fence_after();
     };
-    if (t == 0) {
-      issue_b1_chunk(0);
-      issue_b1_chunk(1);
-    }
-    __syncwarp();
-    for (int n = 0; n < nch; ++n) {
-      const int rg = n & 1;
-      wait_acc(rg);
-      const uint32_t src = rg ? acc1 : acc0;
-      // this thread's 80 columns of its row into the staging tile (fp16): five TMEM loads in
-      // flight, one wait
-      {
-        const int cb = half ? 5 : 0;
-        float z[5][16];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) tc::tmem_ld16(src + 16 * (cb + c), z[c]);
+    // all epilogue threads: shared-memory and TMEM writes done, abort decided uniformly
+    auto sync_epi = [&]() {
+      tc::fence_async_smem();
+      tc::tc_fence_before();
+      ok = tc::bar_and(1, kEpi, ok && !*abort_flag);
+      return ok;
+    };
+    // ... and the MMA issuer may go on
+    auto signal = [&]() {
+      if (t == 0) tc::mbar_arrive(&epib[ev & 1]);
+      ev += 1;
+    };
+
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      const TileOf T = tile_of(tile, s_tiles, a);
+      const int ty = T.ty, row0 = T.row0, nrow = T.nrow;
+      const bool valid = row < nrow;
+      const size_t grow = (size_t)row0 + row;
+      const float* P = a.w + a.fit_base + (long)ty * kFitParams;
+      if (ty != cur_type) {
+        for (int q = t; q < 4 * kF; q += kEpi) {
+          const int which = q / kF, c = q - which * kF;
+          const long off = which == 0 ? kFb1 : which == 1 ? kFb2 : which == 2 ? kFb3 : kFw4;
+          prm[q] = P[off + c];
+        }
+        cur_type = ty;
+        if (!sync_epi()) break;
+      }
+      const float* b1 = prm;
+      const float* b2 = prm + kF;
+      const float* b3 = prm + 2 * kF;
+      const float* w4 = prm + 3 * kF;
+
+      // ---- L1 epilogue: h1 = tanh(z1 + b1)
+      wait_acc(0);
+#pragma unroll 1
+      for (int c = c_beg; c < c_end; ++c) {
+        float z[16], h[16], f[16];
+        tc::tmem_ld16(acc0 + 16 * c, z);
         tc::tmem_wait_ld();
 #pragma unroll
-        for (int c = 0; c < 5; ++c) {
-          uint32_t p[8];
+        for (int u = 0; u < 16; ++u) {
+          h[u] = tc::tanh_exp(z[u] + b1[16 * c + u]);
+          f[u] = 1.f - h[u] * h[u];
+        }
+        store_x16<F16>(sm, row, 16 * c, h, true);
+        tc::tmem_st16(resid + 16 * c, h);
+        if (valid) store_g16<F16>(a.f1 + grow * kF + 16 * c, f);
+      }
+      if (half == 1) {  // K columns 240..255 stay zero (hi and lo)
+        tc::st_chunk(sm + kXHi + 3 * kBlk, row, 48, make_uint4(0, 0, 0, 0));
+        tc::st_chunk(sm + kXHi + 3 * kBlk, row, 56, make_uint4(0, 0, 0, 0));
+        tc::st_chunk(sm + kXLo + 3 * kBlk, row, 48, make_uint4(0, 0, 0, 0));
+        tc::st_chunk(sm + kXLo + 3 * kBlk, row, 56, make_uint4(0, 0, 0, 0));
+      }
+      tc::tmem_wait_st();
+      if (!sync_epi()) break;
+      signal();
+
+      // ---- L2 epilogue: h2 = h1 + tanh(h1 W2 + b2)
+      wait_acc(0);
+#pragma unroll 1
+      for (int c = c_beg; c < c_end; ++c) {
+        float z[16], r[16], f[16];
+        tc::tmem_ld16(acc0 + 16 * c, z);
+        tc::tmem_ld16(resid + 16 * c, r);
+        tc::tmem_wait_ld();
 #pragma unroll
-          for (int h = 0; h < 8; ++h) p[h] = tc::pack2<true>(z[c][2 * h], z[c][2 * h + 1]);
-          uint4* d = reinterpret_cast<uint4*>(sm + kStage + row * kStageRow + 32 * (cb + c));
-          d[0] = make_uint4(p[0], p[1], p[2], p[3]);
-          d[1] = make_uint4(p[4], p[5], p[6], p[7]);
+        for (int u = 0; u < 16; ++u) {
+          const float t2 = tc::tanh_exp(z[u] + b2[16 * c + u]);
+          r[u] += t2;
+          f[u] = 1.f - t2 * t2;
+        }
+        store_x16<F16>(sm, row, 16 * c, r, true);
+        tc::tmem_st16(resid + 16 * c, r);
+        if (valid) store_g16<F16>(a.f2 + grow * kF + 16 * c, f);
+      }
+      tc::tmem_wait_st();
+      if (!sync_epi()) break;
+      signal();
+
+      // ---- L3 epilogue: h3 = h2 + tanh(h2 W3 + b3), E_i, dz3
+      wait_acc(0);
+      float e = 0.f;
+#pragma unroll 1
+      for (int c = c_beg; c < c_end; ++c) {
+        float z[16], r[16], dz[16];
+        tc::tmem_ld16(acc0 + 16 * c, z);
+        tc::tmem_ld16(resid + 16 * c, r);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const float t3 = tc::tanh_exp(z[u] + b3[16 * c + u]);
+          const float wv = w4[16 * c + u];
+          e = fmaf(r[u] + t3, wv, e);
+          dz[u] = wv * (1.f - t3 * t3);
+        }
+        store_x16<F16>(sm, row, 16 * c, dz, true);
+      }
+      if (half == 1) sE[row] = e;
+      if (!sync_epi()) break;
+      signal();
+      if (half == 0 && valid)
+        a.e_atom[grow] = (double)e + (double)sE[row] + (double)P[kFb4] + (double)a.w[a.ebias_off + ty];
+
+      // ---- B3 epilogue: dh2 = w4 + dz3 W3^T ; dz2 = dh2 (1 - t2^2)
+      {  // this row's 1 - t2^2 factors are fetched while the MMAs run
+        uint4 fq[16];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int cc = c_beg + c;
+          if (valid && cc < c_end) {
+            const uint4* src = reinterpret_cast<const uint4*>(a.f2 + grow * kF + 16 * cc);
+            fq[2 * c] = src[0];
+            fq[2 * c + 1] = src[1];
+          } else {
+            fq[2 * c] = fq[2 * c + 1] = make_uint4(0, 0, 0, 0);
+          }
+        }
+        wait_acc(0);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int cc = c_beg + c;
+          if (cc < c_end) {
+            float z[16], f[16];
+            tc::tmem_ld16(acc0 + 16 * cc, z);
+            tc::tmem_wait_ld();
+            unpack_g16<F16>(fq[2 * c], fq[2 * c + 1], f);
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              z[u] += w4[16 * cc + u];  // dh2
+              f[u] *= z[u];             // dz2
+            }
+            tc::tmem_st16(resid + 16 * cc, z);
+            store_x16<F16>(sm, row, 16 * cc, f, true);
+          }
         }
       }
-      __syncthreads();
-      // whole row segments (320 B) to dE/dD: warp w writes rows w, w + 8, ...; lanes 0..19
+      tc::tmem_wait_st();
+      if (!sync_epi()) break;
+      signal();
+
+      // ---- B2 epilogue: dh1 = dh2 + dz2 W2^T ; dz1 = dh1 (1 - h1^2), X_hi only (B1 is a plain
+      //      16-bit GEMM; its weights stream into X_lo meanwhile)
       {
-        const int col0 = kBChunk * is.b1_chunk(n);
-        for (int r = w; r < nrow; r += kThreads / 32)
-          if ((t & 31) < kBChunk / 8) {
-            const uint4 v = *reinterpret_cast<const uint4*>(sm + kStage + r * kStageRow + 16 * (t & 31));
-            __stcs(reinterpret_cast<uint4*>(a.dD + (size_t)(row0 + r) * kKD + col0 + 8 * (t & 31)), v);
+        uint4 fq[16];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int cc = c_beg + c;
+          if (valid && cc < c_end) {
+            const uint4* src = reinterpret_cast<const uint4*>(a.f1 + grow * kF + 16 * cc);
+            fq[2 * c] = src[0];
+            fq[2 * c + 1] = src[1];
+          } else {
+            fq[2 * c] = fq[2 * c + 1] = make_uint4(0, 0, 0, 0);
           }
+        }
+        wait_acc(0);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int cc = c_beg + c;
+          if (cc < c_end) {
+            float z[16], r[16], f[16];
+            tc::tmem_ld16(acc0 + 16 * cc, z);
+            tc::tmem_ld16(resid + 16 * cc, r);
+            tc::tmem_wait_ld();
+            unpack_g16<F16>(fq[2 * c], fq[2 * c + 1], f);
+#pragma unroll
+            for (int u = 0; u < 16; ++u) f[u] *= (z[u] + r[u]);
+            store_x16<F16>(sm, row, 16 * cc, f, false);
+          }
+        }
       }
-      tc::tc_fence_before();
-      __syncthreads();
-      tc::tc_fence_after();
-      if (t == 0 && n + 2 < nch && ok) issue_b1_chunk(n + 2);
-      __syncwarp();
+      if (!sync_epi()) break;
+      signal();
+
+      // ---- B1 drains: dE/dD = dz1 W1^T, chunk n from TMEM region n & 1 through the staging tile
+      for (int n = 0; n < kB1Chunks; ++n) {
+        const int rg = n & 1;
+        wait_acc(rg);
+        const uint32_t src = rg ? acc1 : acc0;
+        {  // this thread's 80 columns of its row (fp16): five TMEM loads in flight, one wait
+          const int cb = half ? 5 : 0;
+          float z[5][16];
+#pragma unroll
+          for (int c = 0; c < 5; ++c) tc::tmem_ld16(src + 16 * (cb + c), z[c]);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int c = 0; c < 5; ++c) {
+            uint32_t p[8];
+#pragma unroll
+            for (int h = 0; h < 8; ++h) p[h] = tc::pack2<true>(z[c][2 * h], z[c][2 * h + 1]);
+            uint4* d = reinterpret_cast<uint4*>(sm + kStage + row * kStageRow + 32 * (cb + c));
+            d[0] = make_uint4(p[0], p[1], p[2], p[3]);
+            d[1] = make_uint4(p[4], p[5], p[6], p[7]);
+          }
+        }
+        if (!sync_epi()) break;
+        // whole row segments (320 B) to dE/dD: warp w writes rows w, w + 8, ...; lanes 0..19
+        {
+          const int col0 = kBChunk * (((blockIdx.x % kB1Chunks) + n) % kB1Chunks);
+          for (int r = w; r < nrow; r += kEpi / 32)
+            if (lane < kBChunk / 8) {
+              const uint4 v = *reinterpret_cast<const uint4*>(sm + kStage + r * kStageRow + 16 * lane);
+              __stcs(reinterpret_cast<uint4*>(a.dD + (size_t)(row0 + r) * kKD + col0 + 8 * lane), v);
+            }
+        }
+        if (!sync_epi()) break;
+        signal();
+      }
     }
   }
   tc::tc_fence_before();
@@ -627,7 +684,7 @@ FitMaps* maps_of(Model* m) {
 }
 
 constexpr size_t kFitSmem = kPrm + 4 * kF * 4 + 1024;
-static_assert(kL1Slots * kL1Slot <= kPrm, "L1 slots exceed the staging area");
+static_assert(kL1Slots * kL1Slot <= kStage, "L1 slots overlap the dE/dD staging tile");
 static_assert(kXLo + kB1Slots * kB1Slot <= kStage, "B1 slots overlap the dE/dD staging tile");
 static_assert(kSt + kSSlots * kSSlot <= kPrm, "split slots exceed the staging area");
 

@@ -62,6 +62,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
   return mbar_wait_limit(bar, parity, err, kSpinLimit);
 }
 
+// Named barrier `id` (1..15) over `count` threads (a multiple of 32) that also returns the AND of
+// every participant's `pred`.
+__device__ __forceinline__ bool bar_and(int id, int count, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(count)
+      : "memory");
+  return r != 0;
+}
+
 __device__ __forceinline__ void fence_async_smem() {
   // make generic-proxy shared-memory writes visible to the async proxy (tensor core, TMA)
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
