@@ -7,7 +7,7 @@
 //
 // Per tile (one TMEM lane per atom; two warpgroups split the 240 columns):
 //   L1  z1 = D W1 + b1          16-bit operands, A (D) and B by TMA      h1 = tanh(z1)
-//   L2  h2 = h1 + tanh(h1 W2 + b2)                 split 16-bit (3 MMAs)
+//   L2  h2 = h1 + tanh(h1 W2 + b2)                 split 16-bit (3 MMAs of N = 240)
 //   L3  h3 = h2 + tanh(h2 W3 + b3);  E_i = h3 . w4 + b4 + e_bias   split
 //   B3  dh2 = w4 + dz3 W3^T,  dz3 = w4 (1 - t3^2)  split
 //   B2  dh1 = dh2 + dz2 W2^T, dz2 = dh2 (1 - t2^2) split
@@ -43,9 +43,9 @@ constexpr uint32_t kBlk = 16384;          // one [128 x 64] 16-bit operand block
 constexpr uint32_t kWB = 240 * 128;       // one [240 x 64] 16-bit weight block (30 KB)
 constexpr uint32_t kXHi = 0;              // X_hi: 4 blocks
 constexpr uint32_t kXLo = 4 * kBlk;       // X_lo: 4 blocks
-constexpr uint32_t kSt = 8 * kBlk;        // 64 KB: four split staging slots
-constexpr uint32_t kSSlot = 128 * 128;    // split job: [128 x 64] 16-bit weight block (16 KB)
-constexpr int kSSlots = 4;
+constexpr uint32_t kSt = 8 * kBlk;        // 90 KB: three split staging slots
+constexpr uint32_t kSSlot = kWB;          // split job: [240 x 64] 16-bit weight block (30 KB)
+constexpr int kSSlots = 3;
 constexpr uint32_t kStageRow = kBChunk * 2 + 16;  // padded row of the dE/dD staging tile (bytes)
 constexpr uint32_t kL1Slot = kBlk + kWB;  // L1 job: A block + W1T block (46 KB)
 constexpr int kL1Slots = 3;               // slots over [0, kStage)
@@ -54,9 +54,9 @@ constexpr int kB1Slots = 5;
 // dE/dD of one B1 chunk is staged here [128 rows x 160 fp16] and written out in whole row
 // segments; it overlays the split slots, idle during B1
 constexpr uint32_t kStage = kXLo + kB1Slots * kB1Slot;
-constexpr uint32_t kPrm = kStage + kFR * kStageRow;  // b1, b2, b3, w4
-constexpr int kSplitSlot = 6;             // barrier index of the first split staging slot (6..9)
-constexpr int kSplitJobs = 16;            // per split GEMM: 4 K blocks x 2 N halves x {hi, lo}
+constexpr uint32_t kPrm = kSt + kSSlots * kSSlot;  // b1, b2, b3, w4
+constexpr int kSplitSlot = 6;             // barrier index of the first split staging slot (6..8)
+constexpr int kSplitJobs = 8;             // per split GEMM: 4 K blocks x {hi, lo}, all 240 output columns
 constexpr int kL1Jobs = kKD / 64;         // 25
 constexpr int kB1Chunks = kKD / kBChunk;  // 10
 constexpr int kB1Jobs = 4 * kB1Chunks;    // 40
@@ -88,8 +88,8 @@ __device__ __forceinline__ unsigned char* align1k(unsigned char* p) {
 }
 
 // The staging slots: barrier k (full: data landed; empty: the MMAs that read it completed) for
-// L1 slots 0..2, B1 slots 0..4 and split slots 6..9.  `uses[k]` counts the jobs through slot k.
-//   L1 job j      -> slot j % 3        B1 job j -> slot j % 5        split job i -> slot 6 + i % 4
+// L1 slots 0..2, B1 slots 0..4 and split slots 6..8.  `uses[k]` counts the jobs through slot k.
+//   L1 job j      -> slot j % 3        B1 job j -> slot j % 5        split job i -> slot 6 + i % 3
 //
 // Each TMA thread processes its own copies one after another (about 0.3 us each from L2,
 // whatever the box size), so three loader threads share the slots: slot k belongs to loader
@@ -128,13 +128,13 @@ struct Loader {
     }
     uses[k] += 1;
   }
-  // split job i of GEMM g: weight half i & 1 (0 = hi, 1 = lo), N half (i >> 1) & 1 (rows 0..127
-  // or 128..255; rows past 240 are zero-filled by the TMA) of K block ((i >> 2) + rot) % 4
+  // split job i of GEMM g: weight half i & 1 (0 = hi, 1 = lo) of K block ((i >> 1) + rot) % 4,
+  // all 240 rows
   __device__ void split(int ty, int g, int i) {
-    const int k = kSplitSlot + (i & 3);
+    const int s = i % kSSlots, k = kSplitSlot + s;
     if (begin(k, kSSlot))
-      tc::tma_load_2d_hint(sm + kSt + (i & 3) * kSSlot, &mp->S[ty][g][i & 1], &full[k], 64 * (((i >> 2) + rot_s) & 3),
-                           128 * ((i >> 1) & 1), keep);
+      tc::tma_load_2d_hint(sm + kSt + s * kSSlot, &mp->S[ty][g][i & 1], &full[k], 64 * (((i >> 1) + rot_s) & 3), 0,
+                           keep);
     uses[k] += 1;
   }
   // B1 job j: W1 rows of chunk (j / 4 + rot) % 10, K block j % 4
@@ -288,7 +288,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
     // ------------------------------------------------------------------ MMA issue
     if (lane == 0) {
       const uint32_t id240 = tc::idesc_f16(128, 240, F16), id160 = tc::idesc_f16(128, kBChunk, F16);
-      const uint32_t id128 = tc::idesc_f16(128, 128, F16);
       const int rot_s = blockIdx.x & 3;
       uint32_t uses[10];
       for (int q = 0; q < 10; ++q) uses[q] = 0;
@@ -309,21 +308,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
         tc::tc_fence_after();
         return ok;
       };
-      // split GEMM: job i is one N half (128 output columns) of one K block with the hi or the lo
-      // weights
+      // split GEMM: job i is one K block with the hi or the lo weights, N = 240 (one read of
+      // the A operand serves all output columns: a 128 x 128 product would need as many shared
+      // memory bytes per clock as the SM has)
       auto issue_split = [&]() {
         for (int i = 0; i < kSplitJobs; ++i) {
-          const int k = kSplitSlot + (i & 3);
+          const int s = i % kSSlots, k = kSplitSlot + s;
           if (!consume(k)) return;
-          const int kx = ((i >> 2) + rot_s) & 3;
-          const uint32_t d = tmem + 128u * (uint32_t)((i >> 1) & 1);
+          const int kx = ((i >> 1) + rot_s) & 3;
           const uint32_t xh = tc::smem_u32(sm + kXHi + kx * kBlk), xl = tc::smem_u32(sm + kXLo + kx * kBlk);
-          const uint32_t wv = tc::smem_u32(sm + kSt + (i & 3) * kSSlot);
+          const uint32_t wv = tc::smem_u32(sm + kSt + s * kSSlot);
           if ((i & 1) == 0) {  // hi weights: x_hi w_hi + x_lo w_hi
-            tc::mma_kblock(d, xh, wv, id128, i >= 4, 4);
-            tc::mma_kblock(d, xl, wv, id128, true, 4);
+            tc::mma_kblock(tmem, xh, wv, id240, i >= 2, 4);
+            tc::mma_kblock(tmem, xl, wv, id240, true, 4);
           } else {             // lo weights: x_hi w_lo
-            tc::mma_kblock(d, xh, wv, id128, true, 4);
+            tc::mma_kblock(tmem, xh, wv, id240, true, 4);
           }
           release(k);
         }
@@ -589,6 +588,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
           }
         }
         if (!sync_epi()) break;
+        // TMEM region n & 1 is free: chunk n + 2 may start under the write-out
+        if (n + 1 < kB1Chunks) signal();
         // whole row segments (320 B) to dE/dD: warp w writes rows w, w + 8, ...; lanes 0..19
         {
           const int col0 = kBChunk * (((blockIdx.x % kB1Chunks) + n) % kB1Chunks);
@@ -599,7 +600,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
             }
         }
         if (!sync_epi()) break;
-        signal();
+        // the last chunk's signal also frees the staging tile, which the next tile's split
+        // slots overlay
+        if (n + 1 == kB1Chunks) signal();
       }
     }
   }
@@ -685,8 +688,9 @@ FitMaps* maps_of(Model* m) {
 
 constexpr size_t kFitSmem = kPrm + 4 * kF * 4 + 1024;
 static_assert(kL1Slots * kL1Slot <= kStage, "L1 slots overlap the dE/dD staging tile");
+static_assert(kStage + kFR * kStageRow <= kPrm, "dE/dD staging tile overlaps the parameters");
 static_assert(kXLo + kB1Slots * kB1Slot <= kStage, "B1 slots overlap the dE/dD staging tile");
-static_assert(kSt + kSSlots * kSSlot <= kPrm, "split slots exceed the staging area");
+
 
 }  // namespace
 
@@ -724,7 +728,7 @@ dp_status mix_fit_setup(Model* m) {
     ok = ok && make_map(&fm->W1[ty], W1, f16, kF, kKD, kBChunk);
     for (int g = 0; g < 4; ++g)
       for (int h = 0; h < 2; ++h)
-        ok = ok && make_map(&fm->S[ty][g][h], S + (size_t)(2 * g + h) * kF * kF, f16, kF, kF, 128);
+        ok = ok && make_map(&fm->S[ty][g][h], S + (size_t)(2 * g + h) * kF * kF, f16, kF, kF, kF);
   }
   if (!ok) {
     m->last_error = "cuTensorMapEncodeTiled failed";
