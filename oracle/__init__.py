@@ -67,6 +67,7 @@ def lib():
             L.oracle_env_stats.argtypes = [_P, _I, _P, _P, _P, _P]
             L.oracle_tabulate.argtypes = [_P, _D, _D, _I]
             L.oracle_emb_eval.argtypes = [_P, _I, _I, _P, _I, _P, _P, _P]
+            L.oracle_set_truncation.argtypes = [_P, _I]
             _lib = L
     return _lib
 
@@ -121,6 +122,11 @@ class Model:
         if h and _lib is not None:
             _lib.oracle_model_free(h)
             self.h = None
+
+    def set_truncation(self, nearest: bool):
+        """Neighbour overflow policy: False = more than sel_t neighbours of a type is an error,
+        True = keep the sel_t nearest (r^2, then neighbour index, then image)."""
+        lib().oracle_set_truncation(self.h, 1 if nearest else 0)
 
     # -- neighbour list -------------------------------------------------------
     def nlist(self, coords, types, box, method: str = "cell", rcut: float = 0.0, sel=None):

@@ -113,6 +113,9 @@ struct Model {
   int tab_n = 0;
   double tab_x0 = 0.0, tab_h = 0.0;
   std::vector<double> tab;
+  // Nearest-first truncation: a neighbour type with more than sel_t neighbours within r_c keeps
+  // its sel_t nearest instead of raising the overflow error.
+  bool nearest = false;
   size_t emb_size() const { const Sizes& s = sz; return (size_t)s.n1 * 2 + (size_t)s.n1 * s.n2 + s.n2 + (size_t)s.n2 * s.n3 + s.n3; }
   size_t fit_size() const { const Sizes& s = sz; return (size_t)s.n3 * s.m2 * s.f1 + s.f1 + (size_t)s.f1 * s.f2 + s.f2 + (size_t)s.f2 * s.f3 + s.f3 + s.f3 + 1; }
 };
@@ -172,7 +175,7 @@ Model<T> cast_model(const Model<double>& m) {
   o.ntypes = m.ntypes; o.switch_kind = m.switch_kind; o.rc = m.rc; o.rs = m.rs; o.sz = m.sz;
   o.sel = m.sel; o.sel_off = m.sel_off; o.S = m.S; o.davg = m.davg; o.dstd = m.dstd;
   o.emb_off = m.emb_off; o.fit_off = m.fit_off; o.ebias_off = m.ebias_off; o.ntheta = m.ntheta;
-  o.tab_n = m.tab_n; o.tab_x0 = m.tab_x0; o.tab_h = m.tab_h; o.tab = m.tab;
+  o.tab_n = m.tab_n; o.tab_x0 = m.tab_x0; o.tab_h = m.tab_h; o.tab = m.tab; o.nearest = m.nearest;
   o.theta.resize(m.theta.size());
   for (size_t i = 0; i < m.theta.size(); ++i) o.theta[i] = T(m.theta[i]);
   return o;
@@ -218,11 +221,34 @@ inline double dist2(const double* xi, const double* xj, const int* n, const doub
   return r2;
 }
 
-struct Cand { int t, j, img; };
+struct Cand { int t, j, img; double r2; };
 inline bool cand_less(const Cand& a, const Cand& b) {
   if (a.t != b.t) return a.t < b.t;
   if (a.j != b.j) return a.j < b.j;
   return a.img < b.img;
+}
+// Distance rank for nearest-first truncation: r^2, then the canonical key (j, image).
+inline bool cand_nearer(const Cand& a, const Cand& b) {
+  if (a.r2 != b.r2) return a.r2 < b.r2;
+  if (a.j != b.j) return a.j < b.j;
+  return a.img < b.img;
+}
+
+// Nearest-first truncation of one atom's candidates (sorted canonically): every type with more
+// than sel_t candidates keeps its sel_t nearest (cand_nearer), still in canonical order.
+void keep_nearest(std::vector<Cand>& c, const std::vector<int>& sel, int nt) {
+  std::vector<Cand> out;
+  for (int t = 0; t < nt; ++t) {
+    std::vector<Cand> ct;
+    for (const Cand& x : c) if (x.t == t) ct.push_back(x);
+    if ((int)ct.size() > sel[t]) {
+      std::sort(ct.begin(), ct.end(), cand_nearer);
+      ct.resize(sel[t]);
+      std::sort(ct.begin(), ct.end(), cand_less);
+    }
+    out.insert(out.end(), ct.begin(), ct.end());
+  }
+  c.swap(out);
 }
 
 // Emit candidate list of atom i (already sorted) into the padded per-type layout.
@@ -241,7 +267,7 @@ void emit(NList& nl, int i, const std::vector<Cand>& c, const std::vector<int>& 
 
 // Brute force: every j and every image n in [-nmax, nmax]^3, nmax = ceil(rcut / L).
 void nlist_brute(int N, const double* xw, const int* types, const double* L, double rcut,
-                 const std::vector<int>& sel, NList& nl) {
+                 const std::vector<int>& sel, NList& nl, bool nearest = false) {
   int nt = (int)sel.size();
   std::vector<int> sel_off(nt + 1, 0);
   for (int t = 0; t < nt; ++t) sel_off[t + 1] = sel_off[t] + sel[t];
@@ -262,9 +288,10 @@ void nlist_brute(int N, const double* xw, const int* types, const double* L, dou
             if (j == i && nx == 0 && ny == 0 && nz == 0) continue;
             int n[3] = {nx, ny, nz};
             double r2 = dist2(&xw[3 * i], &xw[3 * j], n, L);
-            if (r2 < rc2) c.push_back({types[j], j, pack_img(nx, ny, nz)});
+            if (r2 < rc2) c.push_back({types[j], j, pack_img(nx, ny, nz), r2});
           }
     std::sort(c.begin(), c.end(), cand_less);
+    if (nearest) keep_nearest(c, sel, nt);
     emit(nl, i, c, sel, sel_off, nt);
     for (int t = 0; t < nt; ++t) if (nl.count[(size_t)i * nt + t] > sel[t]) ovf = 1;
   }
@@ -275,7 +302,7 @@ void nlist_brute(int N, const double* xw, const int* types, const double* L, dou
 // +-m cells with m = ceil(rcut / edge); virtual cell c + o maps to cell (c+o) mod nc
 // with image shift floor((c+o) / nc).  Each (j, n) is visited at most once.
 void nlist_cell(int N, const double* xw, const int* types, const double* L, double rcut,
-                const std::vector<int>& sel, NList& nl) {
+                const std::vector<int>& sel, NList& nl, bool nearest = false) {
   int nt = (int)sel.size();
   std::vector<int> sel_off(nt + 1, 0);
   for (int t = 0; t < nt; ++t) sel_off[t + 1] = sel_off[t] + sel[t];
@@ -324,10 +351,11 @@ void nlist_cell(int N, const double* xw, const int* types, const double* L, doub
           for (int j : members[cid]) {
             if (j == i && n[0] == 0 && n[1] == 0 && n[2] == 0) continue;
             double r2 = dist2(&xw[3 * i], &xw[3 * j], n, L);
-            if (r2 < rc2) c.push_back({types[j], j, pack_img(n[0], n[1], n[2])});
+            if (r2 < rc2) c.push_back({types[j], j, pack_img(n[0], n[1], n[2]), r2});
           }
         }
     std::sort(c.begin(), c.end(), cand_less);
+    if (nearest) keep_nearest(c, sel, nt);
     emit(nl, i, c, sel, sel_off, nt);
     for (int t = 0; t < nt; ++t) if (nl.count[(size_t)i * nt + t] > sel[t]) ovf = 1;
   }
@@ -335,9 +363,11 @@ void nlist_cell(int N, const double* xw, const int* types, const double* L, doub
 }
 
 // Keep, in order, the entries of a (rcut + skin) list whose current distance is
-// below rcut.  Positions are those of the current step (not re-wrapped).
+// below rcut.  Positions are those of the current step (not re-wrapped).  With `nearest`, a type
+// with more than sel_t such entries keeps its sel_t nearest (r^2, then j, then image).
 void nlist_filter(const NList& big, int N, const double* x, const double* L, double rcut,
-                  const std::vector<int>& sel, const std::vector<int>& big_sel, NList& nl) {
+                  const std::vector<int>& sel, const std::vector<int>& big_sel, NList& nl,
+                  bool nearest = false) {
   int nt = (int)sel.size();
   std::vector<int> sel_off(nt + 1, 0), bsel_off(nt + 1, 0);
   for (int t = 0; t < nt; ++t) { sel_off[t + 1] = sel_off[t] + sel[t]; bsel_off[t + 1] = bsel_off[t] + big_sel[t]; }
@@ -349,7 +379,7 @@ void nlist_filter(const NList& big, int N, const double* x, const double* L, dou
 #pragma omp parallel for schedule(static) reduction(| : ovf)
   for (int i = 0; i < N; ++i) {
     for (int t = 0; t < nt; ++t) {
-      int k = 0;
+      std::vector<Cand> c;
       for (int q = 0; q < big_sel[t]; ++q) {
         size_t e = (size_t)i * big.S + bsel_off[t] + q;
         int j = big.j[e];
@@ -357,10 +387,21 @@ void nlist_filter(const NList& big, int N, const double* x, const double* L, dou
         int n[3];
         unpack_img(big.img[e], n[0], n[1], n[2]);
         double r2 = dist2(&x[3 * i], &x[3 * j], n, L);
-        if (r2 < rc2) {
-          if (k < sel[t]) { nl.j[(size_t)i * nl.S + sel_off[t] + k] = j; nl.img[(size_t)i * nl.S + sel_off[t] + k] = big.img[e]; }
-          ++k;
-        }
+        if (r2 < rc2) c.push_back({t, j, big.img[e], r2});
+      }
+      if (nearest && (int)c.size() > sel[t]) {
+        std::vector<Cand> byr = c;
+        std::sort(byr.begin(), byr.end(), cand_nearer);
+        const Cand& last = byr[sel[t] - 1];
+        std::vector<Cand> kept;
+        for (const Cand& y : c)
+          if (!cand_nearer(last, y)) kept.push_back(y);  // y ranks at or before the sel_t-th
+        c.swap(kept);
+      }
+      int k = 0;
+      for (const Cand& y : c) {
+        if (k < sel[t]) { nl.j[(size_t)i * nl.S + sel_off[t] + k] = y.j; nl.img[(size_t)i * nl.S + sel_off[t] + k] = y.img; }
+        ++k;
       }
       nl.count[(size_t)i * nt + t] = k;
       if (k > sel[t]) ovf = 1;
@@ -757,6 +798,13 @@ void* oracle_model_load(const void* blob, size_t nbytes) {
 
 void oracle_model_free(void* h) { delete static_cast<Model<double>*>(h); }
 
+// Neighbour overflow policy: 0 = a type with more than sel_t neighbours is an error (status 5),
+// 1 = nearest-first truncation (keep the sel_t nearest by r^2, then j, then image).
+int oracle_set_truncation(void* h, int nearest) {
+  static_cast<Model<double>*>(h)->nearest = nearest != 0;
+  return 0;
+}
+
 long long oracle_model_ntheta(const void* h) { return (long long)static_cast<const Model<double>*>(h)->ntheta; }
 int oracle_model_ntypes(const void* h) { return static_cast<const Model<double>*>(h)->ntypes; }
 int oracle_model_S(const void* h) { return static_cast<const Model<double>*>(h)->S; }
@@ -801,8 +849,8 @@ int oracle_nlist(const void* h, int N, const double* x, const int* types, const 
   if (sel_override) for (int t = 0; t < m.ntypes; ++t) sel[t] = sel_override[t];
   NList nl;
   double rc = rcut > 0 ? rcut : m.rc;
-  if (method == 0) nlist_brute(N, xw.data(), types, L, rc, sel, nl);
-  else nlist_cell(N, xw.data(), types, L, rc, sel, nl);
+  if (method == 0) nlist_brute(N, xw.data(), types, L, rc, sel, nl, m.nearest);
+  else nlist_cell(N, xw.data(), types, L, rc, sel, nl, m.nearest);
   if (nlist) std::memcpy(nlist, nl.j.data(), sizeof(int) * nl.j.size());
   if (images) std::memcpy(images, nl.img.data(), sizeof(int) * nl.img.size());
   if (counts) std::memcpy(counts, nl.count.data(), sizeof(int) * nl.count.size());
@@ -823,8 +871,8 @@ int oracle_compute(const void* h, int N, const double* x, const int* types, cons
   std::vector<double> xw;
   wrap_all(N, x, L, xw);
   NList nl;
-  if (method == 0) nlist_brute(N, xw.data(), types, L, m.rc, m.sel, nl);
-  else nlist_cell(N, xw.data(), types, L, m.rc, m.sel, nl);
+  if (method == 0) nlist_brute(N, xw.data(), types, L, m.rc, m.sel, nl, m.nearest);
+  else nlist_cell(N, xw.data(), types, L, m.rc, m.sel, nl, m.nearest);
   if (nl.overflow) return 5;
   if (atom_virial) for (size_t q = 0; q < (size_t)N * 9; ++q) atom_virial[q] = 0.0;
   Inter in{interT, interD, interdD, atom_virial};
@@ -916,7 +964,7 @@ int oracle_env_stats(const void* h, int N, const double* x, const int* types, co
   std::vector<double> xw;
   wrap_all(N, x, L, xw);
   NList nl;
-  nlist_cell(N, xw.data(), types, L, m.rc, m.sel, nl);
+  nlist_cell(N, xw.data(), types, L, m.rc, m.sel, nl, m.nearest);
   if (nl.overflow) return 5;
   for (int q = 0; q < 5 * m.ntypes; ++q) sums[q] = 0.0;
   for (int i = 0; i < N; ++i) {
@@ -950,7 +998,7 @@ int oracle_dir_deriv(const void* h, int N, const double* x, const int* types, co
   std::vector<double> xw;
   wrap_all(N, x, L, xw);
   NList nl;
-  nlist_cell(N, xw.data(), types, L, md.rc, md.sel, nl);
+  nlist_cell(N, xw.data(), types, L, md.rc, md.sel, nl, md.nearest);
   if (nl.overflow) return 5;
   Model<Dual> m = cast_model<Dual>(md);
   std::vector<Dual> xd((size_t)N * 3);
@@ -974,7 +1022,7 @@ int oracle_param_grad(const void* h, int N, const double* x, const int* types, c
   std::vector<double> xw;
   wrap_all(N, x, L, xw);
   NList nl;
-  nlist_cell(N, xw.data(), types, L, md.rc, md.sel, nl);
+  nlist_cell(N, xw.data(), types, L, md.rc, md.sel, nl, md.nearest);
   if (nl.overflow) return 5;
   Model<Dual> m = cast_model<Dual>(md);
   std::vector<Dual> xd((size_t)N * 3), F((size_t)N * 3);
@@ -1082,7 +1130,7 @@ int oracle_md(const void* h, int N, double* x, double* v, const int* types, cons
     return 0;
   };
   auto force = [&](double* E) -> int {
-    nlist_filter(big, N, x, L, m.rc, m.sel, big_sel, nl);
+    nlist_filter(big, N, x, L, m.rc, m.sel, big_sel, nl, m.nearest);
     if (nl.overflow) return 5;
     double vir[9];
     evaluate<double>(m, N, x, types, L, nl, nullptr, true, E, nullptr, F.data(), vir, nullptr);

@@ -107,6 +107,101 @@ def test_nlist_overflow_is_flagged():
     assert ovf and cnt.max() > 10
 
 
+# ----------------------------------------------------------------- nearest-first truncation
+def _py_nearest(coords, types, L, rcut, sel):
+    """Independent Python: per atom and neighbour type, the sel_t candidates of the brute-force
+    list with the smallest (r^2, j, nx, ny, nz), listed in canonical order."""
+    x = oracle.wrap(coords, np.diag([L, L, L]).ravel())
+    full = _py_brute(coords, types, L, rcut, [10 ** 6] * len(sel))
+    out = []
+    for i, c in enumerate(full):
+        def key(e):
+            _, j, nx, ny, nz = e
+            d = [(x[j, a] + n * L) - x[i, a] for a, n in enumerate((nx, ny, nz))]
+            return ((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2], j, nx, ny, nz)
+        keep = []
+        for t in range(len(sel)):
+            keep += sorted(sorted((e for e in c if e[0] == t), key=key)[:sel[t]])
+        out.append(keep)
+    return out
+
+
+@pytest.mark.parametrize("kind", ["water8", "cu_perfect"])
+def test_nearest_truncation_matches_python_selection(kind):
+    # water: 8 molecules in a 6.2 A box (several images of one j); copper: a perfect 2x2x2 FCC
+    # lattice, where whole shells sit at equal distances and the cut falls inside a shell, so
+    # the (j, image) tie-break decides
+    if kind == "water8":
+        s, w, rc, sel = synth.water_box(8, 3), synth.water_weights(), 6.0, (9, 17)
+    else:
+        s, w, rc, sel = synth.copper_fcc(2, 0, sigma=0.0), synth.copper_weights(), 6.0, (30,)
+    m = oracle.Model(w.to_blob())
+    L = s.box[0]
+    ref = _py_nearest(s.coords, s.types, L, rc, sel)
+    full = _py_brute(s.coords, s.types, L, rc, [10 ** 6] * len(sel))
+    assert all(sum(1 for e in c if e[0] == t) > sel[t] for c in full for t in range(len(sel)))  # every row truncates
+    m.set_truncation(True)
+    for method in ("brute", "cell"):
+        nl, im, cnt, ovf = m.nlist(s.coords, s.types, s.box, method, rcut=rc, sel=sel)
+        assert not ovf
+        assert _rows(nl, im, s.types, sel) == ref
+        assert (cnt == np.array(sel)[None, :]).all()
+    if kind == "cu_perfect":  # the third shell (24 at a sqrt(3/2)) is split: ties were broken
+        x = oracle.wrap(s.coords, s.box)
+        r2 = [sorted(((x[j] + np.array(n) * L - x[0]) ** 2).sum() for _, j, *n in full[0])]
+        assert np.isclose(r2[0][sel[0] - 1], r2[0][sel[0]])
+
+
+def test_nearest_truncation_is_identity_without_overflow():
+    s = synth.water_box(64, 0)
+    m = oracle.Model(synth.water_weights().to_blob())
+    a = m.nlist(s.coords, s.types, s.box, "cell")
+    m.set_truncation(True)
+    b = m.nlist(s.coords, s.types, s.box, "cell")
+    assert not a[3] and not b[3]
+    for x, y in zip(a[:3], b[:3]):
+        np.testing.assert_array_equal(x, y)
+    e0 = oracle.Model(synth.water_weights().to_blob()).compute(s.coords, s.types, s.box)["energy"]
+    assert m.compute(s.coords, s.types, s.box)["energy"] == e0
+
+
+def _truncating_water():
+    # sel (20, 40) against about 30 O and 60 H neighbours within 6 A: every atom truncates
+    w = synth.xavier_weights(("O", "H"), 6.0, 0.5, (20, 40), 1001)
+    m = oracle.Model(w.to_blob())
+    m.set_truncation(True)
+    return m
+
+
+def test_nearest_truncation_md_filter_equals_cell_list():
+    # the MD path keeps the nearest entries of the (r_c + skin) list; the force path of a
+    # fresh cell list must give the same energy and forces at step 0
+    s = synth.water_box(64, 0)
+    m = _truncating_water()
+    ref = m.compute(s.coords, s.types, s.box)
+    md = m.md(s.coords, np.zeros_like(s.coords), s.types, s.box, s.masses(), 0.5, 0)
+    assert abs(md["pe"][0] - ref["energy"]) <= 1e-12 * abs(ref["energy"])
+    np.testing.assert_allclose(md["forces"], ref["forces"], rtol=0, atol=1e-12)
+
+
+def test_nearest_truncation_forces_are_energy_gradient():
+    # away from a change of the kept set, E stays smooth: central differences of E match -F
+    s = synth.water_box(64, 0)
+    m = _truncating_water()
+    ref = m.compute(s.coords, s.types, s.box)
+    h = 1e-5
+    rng = np.random.default_rng(3)
+    for k in rng.choice(len(s.types), 6, replace=False):
+        for c in range(3):
+            xp = s.coords.copy()
+            xm = s.coords.copy()
+            xp[k, c] += h
+            xm[k, c] -= h
+            fd = -(m.compute(xp, s.types, s.box, forces=False)["energy"]
+                   - m.compute(xm, s.types, s.box, forces=False)["energy"]) / (2 * h)
+            assert abs(fd - ref["forces"][k, c]) <= 1e-6 + 1e-5 * abs(fd)
+
+
 # ----------------------------------------------------------------- forces / virial
 def test_forces_match_central_differences(water_oracle, water64):
     s = water64
