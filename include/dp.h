@@ -229,6 +229,17 @@ dp_status dp_rdf(dp_model* m, int nbins, double r_max, unsigned long long* count
  */
 dp_status dp_atom_virial(dp_model* m, double* atom_virial);
 
+/*
+ * dp_set_truncation -- neighbour overflow policy.  nearest = 0 (default): a centre with more than
+ * sel[t] neighbours of type t within rcut makes the evaluation fail with DP_ERR_SEL_OVERFLOW.
+ * nearest = 1: such a neighbour type keeps its sel[t] nearest neighbours, DeePMD's convention for
+ * a full neighbour list (Section II-A's fixed-size environment matrix); ranks are by the FP64
+ * squared distance, ties by the caller's index of j, then the image (n_x, n_y, n_z).  The energy
+ * is then discontinuous where two neighbours swap ranks across the cut.  Drops captured MD
+ * graphs.  Errors: DP_ERR_ARG (null model, nearest not 0 or 1).
+ */
+dp_status dp_set_truncation(dp_model* m, int nearest);
+
 /* Number of parameters in theta (the length of dp_param_grad's grad). */
 long long dp_ntheta(const dp_model* m);
 

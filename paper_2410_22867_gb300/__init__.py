@@ -32,7 +32,8 @@ STATUS = {0: "DP_OK", 1: "DP_ERR_ARG", 2: "DP_ERR_CUDA", 3: "DP_ERR_OOM", 4: "DP
 EXPORTS = ("dp_create", "dp_compute", "dp_compute_batch", "dp_verlet_step", "dp_md_run_batch", "dp_param_grad",
            "dp_ntheta", "dp_get_nlist", "dp_phase_times", "dp_kernel_launches", "dp_sync", "dp_last_error",
            "dp_destroy", "dp_version", "dp_selftest", "dp_selftest_noalloc", "dp_set_params", "dp_autotune",
-           "dp_wait_selftest", "dp_measure_peak", "dp_tabulate", "dp_rdf", "dp_atom_virial")
+           "dp_wait_selftest", "dp_measure_peak", "dp_tabulate", "dp_rdf", "dp_atom_virial",
+           "dp_set_truncation")
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -93,10 +94,11 @@ def lib():
             L.dp_tabulate.argtypes = [_P, _D, _D, _I]
             L.dp_rdf.argtypes = [_P, _I, _D, _P]
             L.dp_atom_virial.argtypes = [_P, _P]
+            L.dp_set_truncation.argtypes = [_P, _I]
             for name in ("dp_create", "dp_compute", "dp_compute_batch", "dp_verlet_step", "dp_md_run_batch",
                          "dp_param_grad", "dp_get_nlist", "dp_phase_times", "dp_sync", "dp_selftest",
                          "dp_selftest_noalloc", "dp_set_params", "dp_autotune", "dp_wait_selftest",
-                         "dp_measure_peak", "dp_tabulate", "dp_rdf", "dp_atom_virial"):
+                         "dp_measure_peak", "dp_tabulate", "dp_rdf", "dp_atom_virial", "dp_set_truncation"):
                 getattr(L, name).restype = _I
             _lib = L
     return _lib
@@ -293,6 +295,11 @@ class DPModel:
         ms = (ctypes.c_float * 8)()
         self._check(lib().dp_phase_times(self.h, int(repeats), ctypes.cast(ms, _P)))
         return list(ms)[:7]
+
+    def set_truncation(self, nearest: bool):
+        """dp_set_truncation: False = more than sel_t neighbours of a type within r_c is
+        DP_ERR_SEL_OVERFLOW; True = keep the sel_t nearest (DeePMD's convention)."""
+        self._check(lib().dp_set_truncation(self.h, 1 if nearest else 0))
 
     def tabulate(self, n_intervals: int = 256, x_min: float | None = None, x_max: float | None = None):
         """dp_tabulate: replace the embedding nets by their quintic tables (the compressed model).

@@ -683,6 +683,18 @@ dp_status dp_tabulate(dp_model* h, double x_min, double x_max, int n_intervals) 
   return launch_tabulate(m, x_min, x_max, n_intervals);
 }
 
+dp_status dp_set_truncation(dp_model* h, int nearest) {
+  if (!h) return DP_ERR_ARG;
+  Model* m = &h->m;
+  if (nearest != 0 && nearest != 1) {
+    m->last_error = "nearest must be 0 or 1";
+    return DP_ERR_ARG;
+  }
+  drop_graphs(m);
+  m->nearest = nearest != 0;
+  return DP_OK;
+}
+
 long long dp_ntheta(const dp_model* h) { return h ? h->m.ntheta : 0; }
 
 dp_status dp_get_nlist(dp_model* h, int* nlist, int* images) {

@@ -107,6 +107,7 @@ struct Model {
 
   // atoms (internal, type-sorted order)
   int* perm = nullptr;        // internal -> caller index
+  bool nearest = false;       // nearest-first sel truncation instead of DP_ERR_SEL_OVERFLOW
   int* inv = nullptr;         // caller -> internal index
   int* itype = nullptr;
   int* irep = nullptr;

@@ -379,6 +379,7 @@ struct FormatArgs {
   double rc2;
   float rc2_lo, rc2_hi;
   const int* irep;
+  const int* perm;             // internal -> caller index (truncation tie-break)
   const RepGeom* geom;
   const dvec4* x;
   const float4* delta;
@@ -393,7 +394,74 @@ struct FormatArgs {
   int* err;
 };
 
+// Nearest-first truncation of one overflowing (atom i, type t) segment by its warp: every
+// Verlet entry within r_c is ranked by (exact FP64 r^2, caller index of j, image code), the same
+// order the neighbour list's canonical key uses for ties; the sel_t entries of rank < sel_t are
+// written in Verlet order.  O(n^2 / 32) per lane, taken only when the segment overflows.
 template <bool kFP64>
+__device__ int keep_nearest(const FormatArgs& a, const RepGeom& g, const dvec4& xi, const float4& di, int n,
+                            size_t vb, size_t ob, int sel, int lane) {
+  const unsigned lt = (1u << lane) - 1u;
+  int kept = 0;
+  for (int b = 0; b < n; b += 32) {
+    const int q = b + lane;
+    bool in = false;
+    double r2 = 0.0, dd[3] = {0.0, 0.0, 0.0};
+    unsigned long long tie = 0;
+    int j = 0, code = 0;
+    if (q < n) {
+      j = a.vl_j[vb + q];
+      code = a.vl_img[vb + q];
+      int n0, n1, n2;
+      unpack_img(code, n0, n1, n2);
+      r2 = exact_r2(xi, a.x[j], n0, n1, n2, g.L, dd);
+      in = r2 < a.rc2;
+      tie = ((unsigned long long)(unsigned)a.perm[j] << 32) | (unsigned)code;
+    }
+    int rank = 0;
+    for (int c = 0; c < n; c += 32) {
+      const int p = c + lane;
+      int pin = 0;
+      double pr2 = 0.0, pd[3];
+      unsigned long long ptie = 0;
+      if (p < n) {
+        const int pj = a.vl_j[vb + p], pcode = a.vl_img[vb + p];
+        int m0, m1, m2;
+        unpack_img(pcode, m0, m1, m2);
+        pr2 = exact_r2(xi, a.x[pj], m0, m1, m2, g.L, pd);
+        pin = pr2 < a.rc2;
+        ptie = ((unsigned long long)(unsigned)a.perm[pj] << 32) | (unsigned)pcode;
+      }
+      for (int s = 0; s < 32; ++s) {
+        const double r2s = __shfl_sync(0xffffffffu, pr2, s);
+        const unsigned long long ties = __shfl_sync(0xffffffffu, ptie, s);
+        const int ins = __shfl_sync(0xffffffffu, pin, s);
+        if (ins && (r2s < r2 || (r2s == r2 && ties < tie))) ++rank;
+      }
+    }
+    const bool keep = in && rank < sel;
+    const unsigned mask = __ballot_sync(0xffffffffu, keep);
+    const int pos = kept + __popc(mask & lt);
+    if (keep) {
+      a.nl_j[ob + pos] = j;
+      a.nl_img[ob + pos] = code;
+      if (kFP64) {
+        static_cast<dvec4*>(a.nl_d)[ob + pos] = make_dvec4(dd[0], dd[1], dd[2], 0.0);
+      } else {
+        const float4 d0 = a.vl_d0[vb + q];
+        const float4 dj = a.delta[j];
+        static_cast<float4*>(a.nl_d)[ob + pos] =
+            make_float4(d0.x + (dj.x - di.x), d0.y + (dj.y - di.y), d0.z + (dj.z - di.z), 0.f);
+      }
+    }
+    kept += __popc(mask);
+  }
+  return kept;
+}
+
+// kNearest selects the overflow policy at compile time, so the default (error) variant carries
+// none of the selection's registers.
+template <bool kFP64, bool kNearest>
 __global__ void __launch_bounds__(128) k_format(FormatArgs a) {
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -450,8 +518,12 @@ __global__ void __launch_bounds__(128) k_format(FormatArgs a) {
       cnt += __popc(mask);
     }
     if (cnt > a.sel[t]) {
-      if (lane == 0) set_err(a.err, ERR_SEL);
-      cnt = a.sel[t];
+      if (kNearest) {
+        cnt = keep_nearest<kFP64>(a, g, xi, di, n, vb, ob, a.sel[t], lane);
+      } else {
+        if (lane == 0) set_err(a.err, ERR_SEL);
+        cnt = a.sel[t];
+      }
     }
     if (lane == 0) a.nl_count[(size_t)i * a.ntypes + t] = cnt;
   }
@@ -574,11 +646,17 @@ dp_status launch_format(Model* m, int N) {
   double band = 1e-4 * m->rc * (m->rc + m->skin + 2.0) + 1e-4;
   a.rc2_lo = (float)(a.rc2 - band);
   a.rc2_hi = (float)(a.rc2 + band);
-  a.irep = m->irep; a.geom = m->geom; a.x = m->x; a.delta = m->delta;
+  a.irep = m->irep; a.perm = m->perm; a.geom = m->geom; a.x = m->x; a.delta = m->delta;
   a.vl_j = m->vl_j; a.vl_img = m->vl_img; a.vl_d0 = m->vl_d0; a.vcount = m->vcount;
   a.nl_j = m->nl_j; a.nl_img = m->nl_img; a.nl_d = m->nl_d; a.nl_count = m->nl_count; a.err = m->err;
-  if (m->prec == DP_FP64) k_format<true><<<cdiv(N, 4), 128, 0, m->stream>>>(a);
-  else k_format<false><<<cdiv(N, 4), 128, 0, m->stream>>>(a);
+  const dim3 grid(cdiv(N, 4));
+  if (m->prec == DP_FP64) {
+    if (m->nearest) k_format<true, true><<<grid, 128, 0, m->stream>>>(a);
+    else k_format<true, false><<<grid, 128, 0, m->stream>>>(a);
+  } else {
+    if (m->nearest) k_format<false, true><<<grid, 128, 0, m->stream>>>(a);
+    else k_format<false, false><<<grid, 128, 0, m->stream>>>(a);
+  }
   m->launches += 1;
   DP_LAUNCH_CHECK(m);
   return DP_OK;
