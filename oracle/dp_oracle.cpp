@@ -207,18 +207,44 @@ inline double wrap1(double x, double L) {
   return w;
 }
 
+// Periodic cell: box vectors a, b, c as the rows of H (row-major [9]); an image n = (n0, n1, n2)
+// of atom j sits at x_j + n H.  Orthorhombic when every off-diagonal entry is 0.
+struct Box {
+  double H[9];
+  double Hinv[9];  // s = x Hinv (fractional coordinates, row vector)
+  double L[3];     // diagonal (the edge lengths of an orthorhombic box)
+  double w[3];     // perpendicular widths V / |b x c|, V / |c x a|, V / |a x b|
+  bool tri;
+};
+
+// Component c of the image shift n H, in the fixed order ((n0 H0c + n1 H1c) + n2 H2c); for an
+// orthorhombic box it equals n_c L_c exactly.
+inline double shift(const Box& B, const int* n, int c) {
+  double p0 = (double)n[0] * B.H[c];
+  double p1 = (double)n[1] * B.H[3 + c];
+  double p2 = (double)n[2] * B.H[6 + c];
+  return (p0 + p1) + p2;
+}
+
 // Squared distance of (j, n) seen from i, in the fixed operation order
-// dx = (x_j + n*L) - x_i; r2 = ((dx*dx) + (dy*dy)) + (dz*dz).
-inline double dist2(const double* xi, const double* xj, const int* n, const double* L) {
+// dx = (x_j + (n H)_x) - x_i; r2 = ((dx*dx) + (dy*dy)) + (dz*dz).
+inline double dist2(const double* xi, const double* xj, const int* n, const Box& B) {
   double r2 = 0.0;
   for (int a = 0; a < 3; ++a) {
-    double sh = (double)n[a] * L[a];
+    double sh = shift(B, n, a);
     double p = xj[a] + sh;
     double d = p - xi[a];
     double dd = d * d;
     r2 = (a == 0) ? dd : r2 + dd;
   }
   return r2;
+}
+
+inline void frac(const Box& B, const double* x, double* s) {
+  for (int c = 0; c < 3; ++c) {
+    double p0 = x[0] * B.Hinv[c], p1 = x[1] * B.Hinv[3 + c], p2 = x[2] * B.Hinv[6 + c];
+    s[c] = (p0 + p1) + p2;
+  }
 }
 
 struct Cand { int t, j, img; double r2; };
@@ -266,7 +292,7 @@ void emit(NList& nl, int i, const std::vector<Cand>& c, const std::vector<int>& 
 }
 
 // Brute force: every j and every image n in [-nmax, nmax]^3, nmax = ceil(rcut / L).
-void nlist_brute(int N, const double* xw, const int* types, const double* L, double rcut,
+void nlist_brute(int N, const double* xw, const int* types, const Box& B, double rcut,
                  const std::vector<int>& sel, NList& nl, bool nearest = false) {
   int nt = (int)sel.size();
   std::vector<int> sel_off(nt + 1, 0);
@@ -275,7 +301,9 @@ void nlist_brute(int N, const double* xw, const int* types, const double* L, dou
   nl.j.assign((size_t)N * nl.S, -1); nl.img.assign((size_t)N * nl.S, 0);
   nl.count.assign((size_t)N * nt, 0);
   int nmax[3];
-  for (int a = 0; a < 3; ++a) nmax[a] = (int)std::ceil(rcut / L[a]);
+  // |n_a| <= ceil(rcut / w_a) for positions wrapped into the cell; one more for a triclinic
+  // cell, whose wrapped fractional coordinates may round just outside [0, 1)
+  for (int a = 0; a < 3; ++a) nmax[a] = (int)std::ceil(rcut / B.w[a]) + (B.tri ? 1 : 0);
   double rc2 = rcut * rcut;
   int ovf = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(| : ovf)
@@ -287,7 +315,7 @@ void nlist_brute(int N, const double* xw, const int* types, const double* L, dou
           for (int nz = -nmax[2]; nz <= nmax[2]; ++nz) {
             if (j == i && nx == 0 && ny == 0 && nz == 0) continue;
             int n[3] = {nx, ny, nz};
-            double r2 = dist2(&xw[3 * i], &xw[3 * j], n, L);
+            double r2 = dist2(&xw[3 * i], &xw[3 * j], n, B);
             if (r2 < rc2) c.push_back({types[j], j, pack_img(nx, ny, nz), r2});
           }
     std::sort(c.begin(), c.end(), cand_less);
@@ -298,10 +326,11 @@ void nlist_brute(int N, const double* xw, const int* types, const double* L, dou
   nl.overflow = ovf != 0;
 }
 
-// Cell list: nc = max(1, floor(L / rcut)) cells per axis of edge L/nc, stencil of
-// +-m cells with m = ceil(rcut / edge); virtual cell c + o maps to cell (c+o) mod nc
-// with image shift floor((c+o) / nc).  Each (j, n) is visited at most once.
-void nlist_cell(int N, const double* xw, const int* types, const double* L, double rcut,
+// Cell list: nc = max(1, floor(w / rcut)) cells per axis (w the perpendicular width; L for an
+// orthorhombic box, with cells of edge L/nc), stencil of +-m cells with m = ceil(rcut / (w/nc))
+// (one more for a triclinic cell, binned by fractional coordinate); virtual cell c + o maps to
+// cell (c+o) mod nc with image shift floor((c+o) / nc).  Each (j, n) is visited at most once.
+void nlist_cell(int N, const double* xw, const int* types, const Box& B, double rcut,
                 const std::vector<int>& sel, NList& nl, bool nearest = false) {
   int nt = (int)sel.size();
   std::vector<int> sel_off(nt + 1, 0);
@@ -312,17 +341,19 @@ void nlist_cell(int N, const double* xw, const int* types, const double* L, doub
   int nc[3], m[3];
   double edge[3];
   for (int a = 0; a < 3; ++a) {
-    nc[a] = std::max(1, (int)std::floor(L[a] / rcut));
-    edge[a] = L[a] / nc[a];
-    m[a] = (int)std::ceil(rcut / edge[a]);
+    nc[a] = std::max(1, (int)std::floor(B.w[a] / rcut));
+    edge[a] = B.w[a] / nc[a];
+    m[a] = (int)std::ceil(rcut / edge[a]) + (B.tri ? 1 : 0);
   }
   size_t ncell = (size_t)nc[0] * nc[1] * nc[2];
   std::vector<int> cell_of(N);
   std::vector<std::vector<int>> members(ncell);
   for (int i = 0; i < N; ++i) {
     int c[3];
+    double sf[3];
+    if (B.tri) frac(B, &xw[3 * i], sf);
     for (int a = 0; a < 3; ++a) {
-      c[a] = (int)std::floor(xw[3 * i + a] / edge[a]);
+      c[a] = B.tri ? (int)std::floor(sf[a] * nc[a]) : (int)std::floor(xw[3 * i + a] / edge[a]);
       c[a] = std::min(std::max(c[a], 0), nc[a] - 1);
     }
     size_t id = ((size_t)c[0] * nc[1] + c[1]) * nc[2] + c[2];
@@ -350,7 +381,7 @@ void nlist_cell(int N, const double* xw, const int* types, const double* L, doub
           size_t cid = ((size_t)cc[0] * nc[1] + cc[1]) * nc[2] + cc[2];
           for (int j : members[cid]) {
             if (j == i && n[0] == 0 && n[1] == 0 && n[2] == 0) continue;
-            double r2 = dist2(&xw[3 * i], &xw[3 * j], n, L);
+            double r2 = dist2(&xw[3 * i], &xw[3 * j], n, B);
             if (r2 < rc2) c.push_back({types[j], j, pack_img(n[0], n[1], n[2]), r2});
           }
         }
@@ -365,7 +396,7 @@ void nlist_cell(int N, const double* xw, const int* types, const double* L, doub
 // Keep, in order, the entries of a (rcut + skin) list whose current distance is
 // below rcut.  Positions are those of the current step (not re-wrapped).  With `nearest`, a type
 // with more than sel_t such entries keeps its sel_t nearest (r^2, then j, then image).
-void nlist_filter(const NList& big, int N, const double* x, const double* L, double rcut,
+void nlist_filter(const NList& big, int N, const double* x, const Box& B, double rcut,
                   const std::vector<int>& sel, const std::vector<int>& big_sel, NList& nl,
                   bool nearest = false) {
   int nt = (int)sel.size();
@@ -386,7 +417,7 @@ void nlist_filter(const NList& big, int N, const double* x, const double* L, dou
         if (j < 0) break;
         int n[3];
         unpack_img(big.img[e], n[0], n[1], n[2]);
-        double r2 = dist2(&x[3 * i], &x[3 * j], n, L);
+        double r2 = dist2(&x[3 * i], &x[3 * j], n, B);
         if (r2 < rc2) c.push_back({t, j, big.img[e], r2});
       }
       if (nearest && (int)c.size() > sel[t]) {
@@ -599,7 +630,7 @@ struct Inter {            // optional per-atom intermediates
 // x may be Dual (directional derivatives); positions used for the geometry are
 // x itself, the neighbour list nl is fixed.
 template <class T>
-void evaluate(const Model<T>& m, int N, const T* x, const int* types, const double* L,
+void evaluate(const Model<T>& m, int N, const T* x, const int* types, const Box& B,
               const NList& nl, const unsigned char* centre_mask, bool want_force, T* energy,
               T* atom_energy, T* force, T* virial, const Inter* inter) {
   const Sizes& s = m.sz;
@@ -632,7 +663,7 @@ void evaluate(const Model<T>& m, int N, const T* x, const int* types, const doub
         int n[3];
         unpack_img(nl.img[(size_t)i * nl.S + k], n[0], n[1], n[2]);
         T d[3];
-        for (int a = 0; a < 3; ++a) d[a] = (x[3 * j + a] + T((double)n[a] * L[a])) - x[3 * i + a];
+        for (int a = 0; a < 3; ++a) d[a] = (x[3 * j + a] + T(shift(B, n, a))) - x[3 * i + a];
         T r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         T sw = switch_fn(r, m.rs, m.rc, m.switch_kind);
         T sv = sw / r;
@@ -769,17 +800,53 @@ void evaluate(const Model<T>& m, int N, const T* x, const int* types, const doub
   }
 }
 
-void wrap_all(int N, const double* x, const double* L, std::vector<double>& xw) {
+// Orthorhombic: wrap1 per axis.  Triclinic: t = floor(x Hinv) (fractional coordinates, fixed
+// order) and w = x - t H, each component ((t0 H0c + t1 H1c) + t2 H2c) subtracted from x_c.
+void wrap_all(int N, const double* x, const Box& B, std::vector<double>& xw) {
   xw.resize((size_t)N * 3);
-  for (int i = 0; i < N; ++i)
-    for (int a = 0; a < 3; ++a) xw[3 * i + a] = wrap1(x[3 * i + a], L[a]);
+  for (int i = 0; i < N; ++i) {
+    if (!B.tri) {
+      for (int a = 0; a < 3; ++a) xw[3 * i + a] = wrap1(x[3 * i + a], B.L[a]);
+      continue;
+    }
+    double sf[3];
+    frac(B, &x[3 * i], sf);
+    int t[3] = {(int)std::floor(sf[0]), (int)std::floor(sf[1]), (int)std::floor(sf[2])};
+    for (int c = 0; c < 3; ++c) xw[3 * i + c] = x[3 * i + c] - shift(B, t, c);
+  }
 }
 
-bool box_lengths(const double* box, double* L) {
+// Box from the caller's [9] (rows a, b, c).  Any right-handed cell of positive volume; its
+// inverse is the adjugate over the determinant, each cofactor a difference of two products.
+bool box_geom(const double* box, Box& B) {
+  for (int q = 0; q < 9; ++q) { if (!std::isfinite(box[q])) return false; B.H[q] = box[q]; }
+  B.tri = false;
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b)
-      if (a != b && box[a * 3 + b] != 0.0) return false;
-  for (int a = 0; a < 3; ++a) { L[a] = box[a * 4]; if (!(L[a] > 0.0)) return false; }
+      if (a != b && box[a * 3 + b] != 0.0) B.tri = true;
+  const double* h = B.H;
+  double cof[9];  // cof[3r + c] = cofactor of entry (r, c)
+  cof[0] = h[4] * h[8] - h[5] * h[7];
+  cof[1] = h[5] * h[6] - h[3] * h[8];
+  cof[2] = h[3] * h[7] - h[4] * h[6];
+  cof[3] = h[2] * h[7] - h[1] * h[8];
+  cof[4] = h[0] * h[8] - h[2] * h[6];
+  cof[5] = h[1] * h[6] - h[0] * h[7];
+  cof[6] = h[1] * h[5] - h[2] * h[4];
+  cof[7] = h[2] * h[3] - h[0] * h[5];
+  cof[8] = h[0] * h[4] - h[1] * h[3];
+  const double det = (h[0] * cof[0] + h[1] * cof[1]) + h[2] * cof[2];
+  if (!(det > 0.0)) return false;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) B.Hinv[3 * r + c] = cof[3 * c + r] / det;  // inverse = adj^T / det
+  // |b x c| = norm of cofactor row 0, etc.
+  for (int a = 0; a < 3; ++a) {
+    const double* k = cof + 3 * a;
+    B.w[a] = det / std::sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+    B.L[a] = h[4 * a];
+  }
+  if (!B.tri)
+    for (int a = 0; a < 3; ++a) { B.w[a] = B.L[a]; if (!(B.L[a] > 0.0)) return false; }
   return true;
 }
 
@@ -827,10 +894,10 @@ int oracle_get_threads(void) {
 
 // Wrap positions into the box (same rule as the neighbour list uses).
 int oracle_wrap(int N, const double* x, const double* box, double* xw) {
-  double L[3];
-  if (!box_lengths(box, L)) return 4;
+  Box B;
+  if (!box_geom(box, B)) return 4;
   std::vector<double> w;
-  wrap_all(N, x, L, w);
+  wrap_all(N, x, B, w);
   std::memcpy(xw, w.data(), sizeof(double) * 3 * N);
   return 0;
 }
@@ -841,16 +908,16 @@ int oracle_wrap(int N, const double* x, const double* box, double* xw) {
 int oracle_nlist(const void* h, int N, const double* x, const int* types, const double* box,
                  double rcut, const int* sel_override, int method, int* nlist, int* images, int* counts) {
   const Model<double>& m = *static_cast<const Model<double>*>(h);
-  double L[3];
-  if (!box_lengths(box, L)) return 4;
+  Box B;
+  if (!box_geom(box, B)) return 4;
   std::vector<double> xw;
-  wrap_all(N, x, L, xw);
+  wrap_all(N, x, B, xw);
   std::vector<int> sel = m.sel;
   if (sel_override) for (int t = 0; t < m.ntypes; ++t) sel[t] = sel_override[t];
   NList nl;
   double rc = rcut > 0 ? rcut : m.rc;
-  if (method == 0) nlist_brute(N, xw.data(), types, L, rc, sel, nl, m.nearest);
-  else nlist_cell(N, xw.data(), types, L, rc, sel, nl, m.nearest);
+  if (method == 0) nlist_brute(N, xw.data(), types, B, rc, sel, nl, m.nearest);
+  else nlist_cell(N, xw.data(), types, B, rc, sel, nl, m.nearest);
   if (nlist) std::memcpy(nlist, nl.j.data(), sizeof(int) * nl.j.size());
   if (images) std::memcpy(images, nl.img.data(), sizeof(int) * nl.img.size());
   if (counts) std::memcpy(counts, nl.count.data(), sizeof(int) * nl.count.size());
@@ -866,17 +933,17 @@ int oracle_compute(const void* h, int N, const double* x, const int* types, cons
                    double* atom_energy, double* force, double* virial, double* interT,
                    double* interD, double* interdD, double* atom_virial) {
   const Model<double>& m = *static_cast<const Model<double>*>(h);
-  double L[3];
-  if (!box_lengths(box, L)) return 4;
+  Box B;
+  if (!box_geom(box, B)) return 4;
   std::vector<double> xw;
-  wrap_all(N, x, L, xw);
+  wrap_all(N, x, B, xw);
   NList nl;
-  if (method == 0) nlist_brute(N, xw.data(), types, L, m.rc, m.sel, nl, m.nearest);
-  else nlist_cell(N, xw.data(), types, L, m.rc, m.sel, nl, m.nearest);
+  if (method == 0) nlist_brute(N, xw.data(), types, B, m.rc, m.sel, nl, m.nearest);
+  else nlist_cell(N, xw.data(), types, B, m.rc, m.sel, nl, m.nearest);
   if (nl.overflow) return 5;
   if (atom_virial) for (size_t q = 0; q < (size_t)N * 9; ++q) atom_virial[q] = 0.0;
   Inter in{interT, interD, interdD, atom_virial};
-  evaluate<double>(m, N, xw.data(), types, L, nl, centre_mask, want_force != 0, energy, atom_energy,
+  evaluate<double>(m, N, xw.data(), types, B, nl, centre_mask, want_force != 0, energy, atom_energy,
                    force, virial, &in);
   return 0;
 }
@@ -887,15 +954,15 @@ int oracle_compute(const void* h, int N, const double* x, const int* types, cons
 int oracle_rdf(const void* h, int N, const double* x, const int* types, const double* box, int nbins,
                double r_max, unsigned long long* counts) {
   const Model<double>& m = *static_cast<const Model<double>*>(h);
-  double L[3];
-  if (!box_lengths(box, L)) return 4;
+  Box B;
+  if (!box_geom(box, B)) return 4;
   if (nbins < 1 || !(r_max > 0)) return 1;
   std::vector<double> xw;
-  wrap_all(N, x, L, xw);
+  wrap_all(N, x, B, xw);
   const int nt = m.ntypes;
   std::vector<int> big(nt, N * 64);
   NList nl;
-  nlist_cell(N, xw.data(), types, L, r_max, big, nl);
+  nlist_cell(N, xw.data(), types, B, r_max, big, nl);
   for (size_t q = 0; q < (size_t)nt * nt * nbins; ++q) counts[q] = 0;
   const double inv = nbins / r_max;
   for (int i = 0; i < N; ++i)
@@ -904,7 +971,7 @@ int oracle_rdf(const void* h, int N, const double* x, const int* types, const do
       if (j < 0) continue;
       int n[3];
       unpack_img(nl.img[(size_t)i * nl.S + k], n[0], n[1], n[2]);
-      const double r = std::sqrt(dist2(&xw[3 * i], &xw[3 * j], n, L));
+      const double r = std::sqrt(dist2(&xw[3 * i], &xw[3 * j], n, B));
       const int b = std::min((int)std::floor(r * inv), nbins - 1);
       counts[((size_t)types[i] * nt + types[j]) * nbins + b] += 1;
     }
@@ -959,12 +1026,12 @@ int oracle_emb_eval(const void* h, int pair, int nx, const double* x, int tabula
 //   [3] = sum of (s dx/r)^2 + (s dy/r)^2 + (s dz/r)^2, [4] = number of atoms.
 int oracle_env_stats(const void* h, int N, const double* x, const int* types, const double* box, double* sums) {
   const Model<double>& m = *static_cast<const Model<double>*>(h);
-  double L[3];
-  if (!box_lengths(box, L)) return 4;
+  Box B;
+  if (!box_geom(box, B)) return 4;
   std::vector<double> xw;
-  wrap_all(N, x, L, xw);
+  wrap_all(N, x, B, xw);
   NList nl;
-  nlist_cell(N, xw.data(), types, L, m.rc, m.sel, nl, m.nearest);
+  nlist_cell(N, xw.data(), types, B, m.rc, m.sel, nl, m.nearest);
   if (nl.overflow) return 5;
   for (int q = 0; q < 5 * m.ntypes; ++q) sums[q] = 0.0;
   for (int i = 0; i < N; ++i) {
@@ -977,7 +1044,7 @@ int oracle_env_stats(const void* h, int N, const double* x, const int* types, co
       int n[3];
       unpack_img(nl.img[(size_t)i * nl.S + k], n[0], n[1], n[2]);
       double d[3];
-      for (int a = 0; a < 3; ++a) d[a] = (xw[3 * j + a] + (double)n[a] * L[a]) - xw[3 * i + a];
+      for (int a = 0; a < 3; ++a) d[a] = (xw[3 * j + a] + shift(B, n, a)) - xw[3 * i + a];
       const double r = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
       const double sv = switch_fn(r, m.rs, m.rc, m.switch_kind) / r;
       o[1] += sv;
@@ -993,18 +1060,18 @@ int oracle_env_stats(const void* h, int N, const double* x, const int* types, co
 int oracle_dir_deriv(const void* h, int N, const double* x, const int* types, const double* box,
                      const double* w, double* out) {
   const Model<double>& md = *static_cast<const Model<double>*>(h);
-  double L[3];
-  if (!box_lengths(box, L)) return 4;
+  Box B;
+  if (!box_geom(box, B)) return 4;
   std::vector<double> xw;
-  wrap_all(N, x, L, xw);
+  wrap_all(N, x, B, xw);
   NList nl;
-  nlist_cell(N, xw.data(), types, L, md.rc, md.sel, nl, md.nearest);
+  nlist_cell(N, xw.data(), types, B, md.rc, md.sel, nl, md.nearest);
   if (nl.overflow) return 5;
   Model<Dual> m = cast_model<Dual>(md);
   std::vector<Dual> xd((size_t)N * 3);
   for (size_t q = 0; q < xd.size(); ++q) xd[q] = Dual(xw[q], w[q]);
   Dual E;
-  evaluate<Dual>(m, N, xd.data(), types, L, nl, nullptr, false, &E, nullptr, nullptr, nullptr, nullptr);
+  evaluate<Dual>(m, N, xd.data(), types, B, nl, nullptr, false, &E, nullptr, nullptr, nullptr, nullptr);
   out[0] = E.v; out[1] = E.d;
   return 0;
 }
@@ -1017,12 +1084,12 @@ int oracle_param_grad(const void* h, int N, const double* x, const int* types, c
                       double E0, const double* F0, double cE, double cF, int np, const long long* idx,
                       double* grad, double* dEdtheta, double* loss) {
   const Model<double>& md = *static_cast<const Model<double>*>(h);
-  double L[3];
-  if (!box_lengths(box, L)) return 4;
+  Box B;
+  if (!box_geom(box, B)) return 4;
   std::vector<double> xw;
-  wrap_all(N, x, L, xw);
+  wrap_all(N, x, B, xw);
   NList nl;
-  nlist_cell(N, xw.data(), types, L, md.rc, md.sel, nl, md.nearest);
+  nlist_cell(N, xw.data(), types, B, md.rc, md.sel, nl, md.nearest);
   if (nl.overflow) return 5;
   Model<Dual> m = cast_model<Dual>(md);
   std::vector<Dual> xd((size_t)N * 3), F((size_t)N * 3);
@@ -1031,7 +1098,7 @@ int oracle_param_grad(const void* h, int N, const double* x, const int* types, c
     if (idx[p] < 0 || idx[p] >= (long long)m.ntheta) return 1;
     m.theta[idx[p]].d = 1.0;
     Dual E, vir[9];
-    evaluate<Dual>(m, N, xd.data(), types, L, nl, nullptr, true, &E, nullptr, F.data(), vir, nullptr);
+    evaluate<Dual>(m, N, xd.data(), types, B, nl, nullptr, true, &E, nullptr, F.data(), vir, nullptr);
     m.theta[idx[p]].d = 0.0;
     double g = cE * 2.0 * (E.v - E0) * E.d;
     double lo = cE * (E.v - E0) * (E.v - E0);
@@ -1103,8 +1170,8 @@ int oracle_md(const void* h, int N, double* x, double* v, const int* types, cons
               const double* mass_by_type, double dt, int nsteps, int rebuild_every, double skin,
               double* pe, double* ke, double* force_out) {
   const Model<double>& m = *static_cast<const Model<double>*>(h);
-  double L[3];
-  if (!box_lengths(box, L)) return 4;
+  Box B;
+  if (!box_geom(box, B)) return 4;
   const double rcs = m.rc + skin;
   std::vector<int> big_sel(m.ntypes);
   // Verlet-list capacity per type: generous multiple of sel scaled by volume.
@@ -1114,10 +1181,10 @@ int oracle_md(const void* h, int N, double* x, double* v, const int* types, cons
   for (int i = 0; i < N; ++i) mass[i] = mass_by_type[types[i]];
   NList big, nl;
   auto rebuild = [&]() -> int {
-    wrap_all(N, x, L, xw);
+    wrap_all(N, x, B, xw);
     std::memcpy(x, xw.data(), sizeof(double) * 3 * N);
     std::memcpy(xref.data(), x, sizeof(double) * 3 * N);
-    nlist_cell(N, x, types, L, rcs, big_sel, big);
+    nlist_cell(N, x, types, B, rcs, big_sel, big);
     return big.overflow ? 5 : 0;
   };
   auto check = [&]() -> int {
@@ -1130,10 +1197,10 @@ int oracle_md(const void* h, int N, double* x, double* v, const int* types, cons
     return 0;
   };
   auto force = [&](double* E) -> int {
-    nlist_filter(big, N, x, L, m.rc, m.sel, big_sel, nl, m.nearest);
+    nlist_filter(big, N, x, B, m.rc, m.sel, big_sel, nl, m.nearest);
     if (nl.overflow) return 5;
     double vir[9];
-    evaluate<double>(m, N, x, types, L, nl, nullptr, true, E, nullptr, F.data(), vir, nullptr);
+    evaluate<double>(m, N, x, types, B, nl, nullptr, true, E, nullptr, F.data(), vir, nullptr);
     return 0;
   };
   auto record = [&](int k, double E) {

@@ -202,6 +202,133 @@ def test_nearest_truncation_forces_are_energy_gradient():
             assert abs(fd - ref["forces"][k, c]) <= 1e-6 + 1e-5 * abs(fd)
 
 
+# ----------------------------------------------------------------- triclinic cells
+def _sheared(s, tilt=((0.3, 0.0), (-0.2, 0.25))):
+    """The cubic system s mapped by fractional coordinates into the sheared cell
+    H = L [[1, 0, 0], [t10, 1, 0], [t20, t21, 1]] (same volume, distances distorted)."""
+    L = s.box[0]
+    H = L * np.array([[1.0, 0.0, 0.0], [tilt[0][0], 1.0, 0.0], [tilt[1][0], tilt[1][1], 1.0]])
+    x = (s.coords / L) @ H
+    return x, H.ravel()
+
+
+def _py_brute_tri(coords, types, H, rcut):
+    """Independent Python brute force in a general cell: every (j, n) with
+    d = (x_j + ((n0 H0 + n1 H1) + n2 H2)) - x_i of r^2 < rcut^2, from the oracle's wrapped
+    positions, in canonical order."""
+    x = oracle.wrap(coords, H.ravel())
+    Hm = H.reshape(3, 3)
+    V = np.linalg.det(Hm)
+    w = [V / np.linalg.norm(np.cross(Hm[(a + 1) % 3], Hm[(a + 2) % 3])) for a in range(3)]
+    nmax = [math.ceil(rcut / wa) + 1 for wa in w]
+    out = []
+    for i in range(len(types)):
+        c = []
+        for j in range(len(types)):
+            for nx in range(-nmax[0], nmax[0] + 1):
+                for ny in range(-nmax[1], nmax[1] + 1):
+                    for nz in range(-nmax[2], nmax[2] + 1):
+                        if i == j and nx == ny == nz == 0:
+                            continue
+                        d = [(x[j, a] + ((nx * Hm[0, a] + ny * Hm[1, a]) + nz * Hm[2, a])) - x[i, a] for a in range(3)]
+                        if (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2] < rcut * rcut:
+                            c.append((int(types[j]), j, nx, ny, nz))
+        out.append(sorted(c))
+    return out
+
+
+def test_triclinic_nlist_matches_python_brute_force():
+    s = synth.water_box(8, 3)  # a 6.2 A cell: several images of one j within 6 A
+    x, H = _sheared(s)
+    m = oracle.Model(synth.water_weights().to_blob())
+    sel = (400, 800)
+    ref = _py_brute_tri(x, s.types, H, 6.0)
+    for method in ("brute", "cell"):
+        nl, im, cnt, ovf = m.nlist(x, s.types, H, method, rcut=6.0, sel=sel)
+        assert not ovf
+        assert _rows(nl, im, s.types, sel) == ref
+
+
+def test_triclinic_cell_list_equals_brute():
+    s = synth.water_box(64, 0)
+    x, H = _sheared(s, ((0.45, 0.0), (-0.3, 0.35)))
+    m = oracle.Model(synth.water_weights().to_blob())
+    a = m.nlist(x, s.types, H, "brute")
+    b = m.nlist(x, s.types, H, "cell")
+    assert not a[3] and not b[3]
+    for p, q in zip(a[:3], b[:3]):
+        np.testing.assert_array_equal(p, q)
+
+
+def test_triclinic_cell_of_a_cubic_lattice_gives_the_cubic_result():
+    # rows (a, a + b, b + c) span the same lattice as the cube: the same periodic system
+    s = synth.water_box(64, 0)
+    L = s.box[0]
+    H = np.array([[L, 0, 0], [L, L, 0], [0, L, L]], dtype=np.float64).ravel()
+    m = oracle.Model(synth.water_weights().to_blob())
+    ref = m.compute(s.coords, s.types, s.box)
+    got = m.compute(s.coords, s.types, H)
+    assert got["energy"] == pytest.approx(ref["energy"], rel=1e-12)
+    np.testing.assert_allclose(got["forces"], ref["forces"], rtol=0, atol=1e-11)
+    np.testing.assert_allclose(got["virial"], ref["virial"], rtol=0, atol=1e-10)
+
+
+def test_triclinic_rotation_invariance():
+    s = synth.water_box(64, 0)
+    x, H = _sheared(s)
+    m = oracle.Model(synth.water_weights().to_blob())
+    ref = m.compute(x, s.types, H)
+    R = synth._rand_rotation(np.random.default_rng(11))
+    got = m.compute(x @ R.T, s.types, (H.reshape(3, 3) @ R.T).ravel())
+    assert got["energy"] == pytest.approx(ref["energy"], rel=1e-12)
+    np.testing.assert_allclose(got["forces"], ref["forces"] @ R.T, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(got["virial"], R @ ref["virial"] @ R.T, rtol=0, atol=1e-10)
+
+
+def test_triclinic_forces_and_virial_are_derivatives():
+    s = synth.water_box(64, 0)
+    x, H = _sheared(s)
+    m = oracle.Model(synth.water_weights().to_blob())
+    ref = m.compute(x, s.types, H)
+    # forces: the exact directional derivative (dual numbers) along a random displacement
+    w = np.random.default_rng(5).standard_normal(x.shape)
+    E, dE = m.dir_deriv(x, s.types, H, w)
+    assert E == pytest.approx(ref["energy"], rel=1e-13)
+    assert dE == pytest.approx(-(w * ref["forces"]).sum(), rel=1e-11, abs=1e-14)
+    # every virial component: x -> x (I + e E_ab), H -> H (I + e E_ab) gives -dE/de = V_ba
+    # (central differences at e and 2e, Richardson-extrapolated: error O(e^4))
+    eps = 1e-3
+    Hm = H.reshape(3, 3)
+    for a in range(3):
+        for b in range(3):
+            def E_at(e):
+                S = np.eye(3)
+                S[a, b] += e
+                return m.energy(x @ S, s.types, (Hm @ S).ravel())
+            d1 = (E_at(eps) - E_at(-eps)) / (2 * eps)
+            d2 = (E_at(2 * eps) - E_at(-2 * eps)) / (4 * eps)
+            fd = -(4 * d1 - d2) / 3
+            assert fd == pytest.approx(ref["virial"][b, a], rel=1e-6, abs=1e-9)
+
+
+def test_triclinic_md_filter_equals_cell_list():
+    s = synth.water_box(64, 0)
+    x, H = _sheared(s)
+    m = oracle.Model(synth.water_weights().to_blob())
+    ref = m.compute(x, s.types, H)
+    md = m.md(x, np.zeros_like(x), s.types, H, s.masses(), 0.5, 0)
+    assert abs(md["pe"][0] - ref["energy"]) <= 1e-12 * abs(ref["energy"])
+
+
+def test_left_handed_or_flat_cell_is_rejected():
+    s = synth.water_box(8, 3)
+    m = oracle.Model(synth.water_weights().to_blob())
+    L = s.box[0]
+    for H in (np.diag([L, L, -L]).ravel(), np.array([[L, 0, 0], [L, 0, 0], [0, 0, L]], dtype=np.float64).ravel()):
+        with pytest.raises(oracle.OracleError):
+            m.compute(s.coords, s.types, H)
+
+
 # ----------------------------------------------------------------- forces / virial
 def test_forces_match_central_differences(water_oracle, water64):
     s = water64
