@@ -24,9 +24,12 @@
  *    sticky: dp_sync() waits for the stream and returns them, and clears them.
  *  - Units: Angstrom, eV, fs, amu.  Forces are eV/A; the virial is in eV and
  *    is the negative strain derivative of the energy, Xi = -sum_pairs g (x) d
- *    with g = dE/dd for the pair vector d = x_j + n*L - x_i.
- *  - Boxes are 3x3 row-major; only orthorhombic boxes are supported
- *    (off-diagonal entries must be 0, else DP_ERR_UNSUPPORTED).
+ *    with g = dE/dd for the pair vector d = x_j + n H - x_i.
+ *  - Boxes are 3x3 row-major, the rows the cell vectors a, b, c; an image
+ *    n = (n0, n1, n2) of atom j sits at x_j + n H.  Any right-handed cell of
+ *    positive volume with entries below 2^28 A (else DP_ERR_ARG); orthorhombic
+ *    cells (off-diagonal entries 0) wrap and bin per axis, triclinic ones by
+ *    fractional coordinate s = x H^-1.
  *  - Atom arrays are in the caller's order; the library sorts atoms by type
  *    internally and un-permutes every output.
  *  - No call allocates device memory after dp_create (except dp_tabulate, a set-up
@@ -50,7 +53,7 @@ typedef enum {
   DP_ERR_ARG = 1,           /* bad argument (null pointer, size, mismatch) */
   DP_ERR_CUDA = 2,          /* a CUDA runtime call failed; see dp_last_error */
   DP_ERR_OOM = 3,           /* device allocation failed in dp_create */
-  DP_ERR_UNSUPPORTED = 4,   /* non-orthorhombic box, unsupported network size or precision */
+  DP_ERR_UNSUPPORTED = 4,   /* cell too small for the cutoff, unsupported network size or precision */
   DP_ERR_SEL_OVERFLOW = 5,  /* more real neighbours of one type than sel[type] */
   DP_ERR_SKIN_EXCEEDED = 6, /* an atom moved more than skin/2 since the last neighbour rebuild */
   DP_ERR_WAIT_TIMEOUT = 7,  /* a bounded device-side wait gave up */

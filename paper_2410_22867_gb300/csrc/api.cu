@@ -115,30 +115,52 @@ dp_status setup_replicas(Model* m, int nrep, const int* offs, const double* boxe
     cells = 0;
     for (int r = 0; r < nrep; ++r) {
       const double* b = boxes + 9 * r;
-      for (int a = 0; a < 3; ++a)
-        for (int c = 0; c < 3; ++c)
-          if (a != c && b[3 * a + c] != 0.0) {
-            m->last_error = "only orthorhombic boxes are supported";
-            return DP_ERR_UNSUPPORTED;
-          }
       RepGeom& g = m->geom_host[r];
       std::memset(&g, 0, sizeof(g));
+      // any right-handed cell: finite entries, positive volume; inverse = adjugate / det
+      double cof[9];
+      for (int q = 0; q < 9; ++q) {
+        if (!std::isfinite(b[q]) || std::fabs(b[q]) >= 268435456.0) {
+          m->last_error = "box entries must be finite and below 2^28 A";
+          return DP_ERR_ARG;
+        }
+        g.H[q] = b[q];
+        g.Hf[q] = (float)b[q];
+        g.Hq[q] = std::llrint(b[q] * 4294967296.0);
+      }
+      for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c)
+          if (a != c && b[3 * a + c] != 0.0) g.tri = 1;
+      cof[0] = b[4] * b[8] - b[5] * b[7];
+      cof[1] = b[5] * b[6] - b[3] * b[8];
+      cof[2] = b[3] * b[7] - b[4] * b[6];
+      cof[3] = b[2] * b[7] - b[1] * b[8];
+      cof[4] = b[0] * b[8] - b[2] * b[6];
+      cof[5] = b[1] * b[6] - b[0] * b[7];
+      cof[6] = b[1] * b[5] - b[2] * b[4];
+      cof[7] = b[2] * b[3] - b[0] * b[5];
+      cof[8] = b[0] * b[4] - b[1] * b[3];
+      const double det = (b[0] * cof[0] + b[1] * cof[1]) + b[2] * cof[2];
+      if (!(det > 0.0)) { m->last_error = "the box must be a right-handed cell of positive volume"; return DP_ERR_ARG; }
+      for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) g.Hinv[3 * a + c] = cof[3 * c + a] / det;
       const double eff = rcs * (1.0 + 1e-9);
       int ncr = 1;
       for (int a = 0; a < 3; ++a) {
-        double L = b[4 * a];
-        if (!(L > 0.0) || !std::isfinite(L)) { m->last_error = "box length must be positive"; return DP_ERR_ARG; }
-        g.L[a] = L;
-        g.Lf[a] = (float)L;
-        g.Lq[a] = std::llrint(L * 4294967296.0);
-        int nc = (int)std::floor(div * L / eff);
+        g.L[a] = b[4 * a];
+        if (!g.tri && !(g.L[a] > 0.0)) { m->last_error = "box length must be positive"; return DP_ERR_ARG; }
+        // perpendicular width of the cell along axis a: V / |cross product of the other rows|
+        const double* k = cof + 3 * a;
+        const double width = g.tri ? det / std::sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]) : g.L[a];
+        int nc = (int)std::floor(div * width / eff);
         if (nc < 1) nc = 1;
         if (nc > 1024) nc = 1024;
         g.nc[a] = nc;
-        g.edge[a] = L / nc;
-        g.m[a] = (int)std::ceil(eff / g.edge[a]);
+        // triclinic cells are binned by fractional coordinate, one more stencil layer covers an
+        // atom whose rounded fractional coordinate lands in the neighbouring cell
+        g.edge[a] = g.tri ? 1.0 / nc : g.L[a] / nc;
+        g.m[a] = (int)std::ceil(eff / (width / nc)) + g.tri;
         if (g.m[a] > 200) { m->last_error = "box too small for the cutoff"; return DP_ERR_UNSUPPORTED; }
-        if (L >= 2147483648.0) { m->last_error = "box length too large"; return DP_ERR_UNSUPPORTED; }
         ncr *= nc;
       }
       g.cell_off = cells;

@@ -52,17 +52,22 @@ struct __align__(32) qvec4 {
 };
 
 // Per-replica geometry (orthorhombic box and cell grid).
+// Periodic cell of one replica: cell vectors a, b, c as the rows of H; an image n = (n0, n1, n2)
+// of an atom sits at x + n H, each component summed as ((n0 H0c + n1 H1c) + n2 H2c), which for
+// an orthorhombic cell is n_c L_c exactly.
 struct RepGeom {
-  double L[3];      // box lengths
-  long long Lq[3];  // box lengths in fixed point (L * 2^32, rounded)
-  float Lf[3];      // box lengths in fp32
-  int nc[3];        // cells per axis
-  int m[3];         // stencil half width per axis
-  double edge[3];   // cell edge
-  int cell_off;     // first global cell id of this replica
-  int atom_off;     // first caller-order atom of this replica
+  double H[9];        // cell vectors (rows)
+  double Hinv[9];     // fractional coordinates s = x Hinv (row vector)
+  double L[3];        // diagonal of H: the edges of an orthorhombic cell
+  long long Hq[9];    // H in fixed point (H * 2^32, rounded)
+  float Hf[9];        // H in fp32
+  int nc[3];          // cells per axis
+  int m[3];           // stencil half width per axis
+  double edge[3];     // cell edge (orthorhombic, A) or 1 / nc (triclinic, fractional)
+  int tri;            // 1: some off-diagonal entry of H is nonzero (cells in fractional coordinates)
+  int cell_off;       // first global cell id of this replica
+  int atom_off;       // first caller-order atom of this replica
   int natoms;
-  int pad;
 };
 
 struct Model {

@@ -8,8 +8,10 @@
 // rebuilt every k steps (Section IV).
 //
 // Bit-exactness: a pair (j, n) is in the list iff the FP64 value
-//   r2 = ((dx*dx) + (dy*dy)) + (dz*dz),  dx = (x_j + n*L) - x_i
-// (round-to-nearest, no FMA) is below the squared cutoff.  The kernels first
+//   r2 = ((dx*dx) + (dy*dy)) + (dz*dz),  dx = (x_j + (n H)_x) - x_i,
+//   (n H)_x = ((n0 H00 + n1 H10) + n2 H20)
+// (round-to-nearest, no FMA) is below the squared cutoff; for an orthorhombic cell (n H)_x is
+// n0 L_x exactly.  The kernels first
 // classify in FP32 and fall back to that exact FP64 test whenever the FP32
 // value lies inside a band wider than its worst-case rounding error, so the
 // result equals the FP64 definition while doing FP32 work for almost all pairs
@@ -32,11 +34,19 @@ __device__ __forceinline__ double wrap1(double x, double L) {
 }
 
 // Exact FP64 pair vector and squared length in the fixed operation order.
+// Component c of the image shift n H in the fixed order ((n0 H0c + n1 H1c) + n2 H2c); for an
+// orthorhombic cell (tri = 0) the two zero products drop out and it is n_c L_c, computed as such.
+__device__ __forceinline__ double img_shift(const double* H, int tri, int n0, int n1, int n2, int c) {
+  if (!tri) return __dmul_rn((double)(c == 0 ? n0 : c == 1 ? n1 : n2), H[4 * c]);
+  return __dadd_rn(__dadd_rn(__dmul_rn((double)n0, H[c]), __dmul_rn((double)n1, H[3 + c])),
+                   __dmul_rn((double)n2, H[6 + c]));
+}
+
 __device__ __forceinline__ double exact_r2(const dvec4& xi, const dvec4& xj, int nx, int ny, int nz,
-                                           const double* L, double* d) {
-  d[0] = __dsub_rn(__dadd_rn(xj.x, __dmul_rn((double)nx, L[0])), xi.x);
-  d[1] = __dsub_rn(__dadd_rn(xj.y, __dmul_rn((double)ny, L[1])), xi.y);
-  d[2] = __dsub_rn(__dadd_rn(xj.z, __dmul_rn((double)nz, L[2])), xi.z);
+                                           const RepGeom& g, double* d) {
+  d[0] = __dsub_rn(__dadd_rn(xj.x, img_shift(g.H, g.tri, nx, ny, nz, 0)), xi.x);
+  d[1] = __dsub_rn(__dadd_rn(xj.y, img_shift(g.H, g.tri, nx, ny, nz, 1)), xi.y);
+  d[2] = __dsub_rn(__dadd_rn(xj.z, img_shift(g.H, g.tri, nx, ny, nz, 2)), xi.z);
   return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
 }
 
@@ -141,7 +151,26 @@ __global__ void k_wrap_bin(int N, const int* __restrict__ irep, const int* __res
   if (k >= N) return;
   const RepGeom& g = geom[irep[k]];
   dvec4 p = x[k];
-  double w[3] = {wrap1(p.x, g.L[0]), wrap1(p.y, g.L[1]), wrap1(p.z, g.L[2])};
+  double w[3], sf[3] = {0.0, 0.0, 0.0};
+  if (!g.tri) {
+    w[0] = wrap1(p.x, g.L[0]);
+    w[1] = wrap1(p.y, g.L[1]);
+    w[2] = wrap1(p.z, g.L[2]);
+  } else {
+    // t = floor(x Hinv) (fixed order), w = x - t H; sf = the fractional coordinate minus t
+    const double pc[3] = {p.x, p.y, p.z};
+    int t[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double s = __dadd_rn(__dadd_rn(__dmul_rn(pc[0], g.Hinv[c]), __dmul_rn(pc[1], g.Hinv[3 + c])),
+                                 __dmul_rn(pc[2], g.Hinv[6 + c]));
+      const double f = floor(s);
+      t[c] = (int)f;
+      sf[c] = s - f;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) w[c] = __dsub_rn(pc[c], img_shift(g.H, 1, t[0], t[1], t[2], c));
+  }
   dvec4 q = make_dvec4(w[0], w[1], w[2], 0.0);
   x[k] = q;
   xref[k] = q;
@@ -153,7 +182,7 @@ __global__ void k_wrap_bin(int N, const int* __restrict__ irep, const int* __res
   delta[k] = make_float4(0.f, 0.f, 0.f, 0.f);
   int c[3];
   for (int a = 0; a < 3; ++a) {
-    int ci = (int)floor(w[a] / g.edge[a]);
+    int ci = g.tri ? (int)floor(sf[a] * g.nc[a]) : (int)floor(w[a] / g.edge[a]);
     c[a] = min(max(ci, 0), g.nc[a] - 1);
   }
   int cid = g.cell_off + (c[0] * g.nc[1] + c[1]) * g.nc[2] + c[2];
@@ -222,12 +251,13 @@ struct VerletArgs {
 
 constexpr int kVerletWarps = 4;
 
-// One component of d = x_j + n L - x_i from fixed-point positions (units of 2^-32 A): the
-// integer difference D = hi * 2^32 + lo (lo in [0, 2^32)) is exact; the float result is
-// hi + lo * 2^-32 with one final rounding (within one ulp of d).  Integer work only: FP64
-// runs at a small fraction of the FP32 rate on this GPU.
-__device__ __forceinline__ float fixed_diff(long long qj, long long qi, int n, long long Lq) {
-  const long long D = qj + (long long)n * Lq - qi;
+// One component of d = x_j + n H - x_i from fixed-point positions (units of 2^-32 A; shq is the
+// image shift in the same units): the integer difference D = hi * 2^32 + lo (lo in [0, 2^32)) is
+// exact; the float result is hi + lo * 2^-32 with one final rounding (within one ulp of d, up to
+// the 2^-32 A rounding of H).  Integer work only: FP64 runs at a small fraction of the FP32 rate
+// on this GPU.
+__device__ __forceinline__ float fixed_diff(long long qj, long long qi, long long shq) {
+  const long long D = qj + shq - qi;
   const int hi = (int)(D >> 32);
   const unsigned lo = (unsigned)(D & 0xffffffffll);
   return fmaf((float)lo, 2.3283064365386963e-10f, (float)hi);
@@ -298,8 +328,18 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
           const size_t e = ebase + a.vcap_off[t] + pos;
           a.vl_j[e] = j;
           a.vl_img[e] = code;
-          a.vl_d0[e] = make_float4(fixed_diff(qj.x, qi.x, n0, g.Lq[0]), fixed_diff(qj.y, qi.y, n1, g.Lq[1]),
-                                   fixed_diff(qj.z, qi.z, n2, g.Lq[2]), 0.f);
+          long long shq[3];
+          if (!g.tri) {
+            shq[0] = (long long)n0 * g.Hq[0];
+            shq[1] = (long long)n1 * g.Hq[4];
+            shq[2] = (long long)n2 * g.Hq[8];
+          } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              shq[c] = (long long)n0 * g.Hq[c] + (long long)n1 * g.Hq[3 + c] + (long long)n2 * g.Hq[6 + c];
+          }
+          a.vl_d0[e] = make_float4(fixed_diff(qj.x, qi.x, shq[0]), fixed_diff(qj.y, qi.y, shq[1]),
+                                   fixed_diff(qj.z, qi.z, shq[2]), 0.f);
         }
       }
       __syncwarp();
@@ -320,8 +360,10 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
         const int v = ci[q] + o[q];
         n[q] = floor_div(v, g.nc[q]);
         cc[q] = v - n[q] * g.nc[q];
-        sh[q] = (float)n[q] * g.Lf[q];
       }
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        sh[q] = ((float)n[0] * g.Hf[q] + (float)n[1] * g.Hf[3 + q]) + (float)n[2] * g.Hf[6 + q];
       const int c = g.cell_off + (cc[0] * g.nc[1] + cc[1]) * g.nc[2] + cc[2];
       beg = a.cell_start[c];
       num = a.cell_start[c + 1] - beg;
@@ -414,7 +456,7 @@ __device__ int keep_nearest(const FormatArgs& a, const RepGeom& g, const dvec4& 
       code = a.vl_img[vb + q];
       int n0, n1, n2;
       unpack_img(code, n0, n1, n2);
-      r2 = exact_r2(xi, a.x[j], n0, n1, n2, g.L, dd);
+      r2 = exact_r2(xi, a.x[j], n0, n1, n2, g, dd);
       in = r2 < a.rc2;
       tie = ((unsigned long long)(unsigned)a.perm[j] << 32) | (unsigned)code;
     }
@@ -428,7 +470,7 @@ __device__ int keep_nearest(const FormatArgs& a, const RepGeom& g, const dvec4& 
         const int pj = a.vl_j[vb + p], pcode = a.vl_img[vb + p];
         int m0, m1, m2;
         unpack_img(pcode, m0, m1, m2);
-        pr2 = exact_r2(xi, a.x[pj], m0, m1, m2, g.L, pd);
+        pr2 = exact_r2(xi, a.x[pj], m0, m1, m2, g, pd);
         pin = pr2 < a.rc2;
         ptie = ((unsigned long long)(unsigned)a.perm[pj] << 32) | (unsigned)pcode;
       }
@@ -487,7 +529,7 @@ __global__ void __launch_bounds__(128) k_format(FormatArgs a) {
         if (kFP64) {
           int n0, n1, n2;
           unpack_img(code, n0, n1, n2);
-          in = exact_r2(xi, a.x[j], n0, n1, n2, g.L, dd) < a.rc2;
+          in = exact_r2(xi, a.x[j], n0, n1, n2, g, dd) < a.rc2;
         } else {
           float4 d0 = a.vl_d0[vb + q];
           float4 dj = a.delta[j];
@@ -500,7 +542,7 @@ __global__ void __launch_bounds__(128) k_format(FormatArgs a) {
           } else if (r2f < a.rc2_hi) {
             int n0, n1, n2;
             unpack_img(code, n0, n1, n2);
-            in = exact_r2(xi, a.x[j], n0, n1, n2, g.L, dd) < a.rc2;
+            in = exact_r2(xi, a.x[j], n0, n1, n2, g, dd) < a.rc2;
           }
         }
       }
@@ -590,10 +632,15 @@ dp_status launch_load_positions(Model* m, const double* coords_user, int N) {
   return DP_OK;
 }
 
+// Largest |x| a wrapped coordinate or a single-cell shift can have: max over rows of sum |H_ac|.
 static double max_box_length(const Model* m) {
   double Lmax = 0;
   for (int r = 0; r < m->nrep; ++r)
-    for (int a = 0; a < 3; ++a) Lmax = Lmax > m->geom_host[r].L[a] ? Lmax : m->geom_host[r].L[a];
+    for (int a = 0; a < 3; ++a) {
+      const double* h = m->geom_host[r].H + 3 * a;
+      const double v = std::fabs(h[0]) + std::fabs(h[1]) + std::fabs(h[2]);
+      Lmax = Lmax > v ? Lmax : v;
+    }
   return Lmax;
 }
 

@@ -211,11 +211,11 @@ def test_bad_arguments(dp):
     s = synth.water_box(8, 0)
     m = dp.DPModel(w, "fp64", max_atoms=s.natoms)
     x, t = _cuda(s)
-    tri = s.box.copy()
-    tri[1] = 0.5
+    flat = s.box.copy()
+    flat[3:6] = flat[0:3]  # two equal cell vectors: zero volume
     with pytest.raises(dp.DPError) as e:
-        m.compute(x, t, tri)
-    assert e.value.status == 4
+        m.compute(x, t, flat)
+    assert e.value.status == 1
     big = synth.water_box(16, 0)
     xb, tb = _cuda(big)
     with pytest.raises(dp.DPError) as e:
