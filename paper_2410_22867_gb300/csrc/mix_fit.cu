@@ -49,8 +49,12 @@ constexpr int kSSlots = 3;
 constexpr uint32_t kStageRow = kBChunk * 2 + 16;  // padded row of the dE/dD staging tile (bytes)
 constexpr uint32_t kL1Slot = kBlk + kWB;  // L1 job: A block + W1T block (46 KB)
 constexpr int kL1Slots = 3;               // slots over [0, kStage)
-constexpr uint32_t kB1Slot = kBChunk * 128;  // B1 job: W1 block [160 x 64] (20 KB), slots over [kXLo, kStage)
-constexpr int kB1Slots = 5;
+// B1 job: two W1 blocks [160 x 64] (K blocks 2h and 2h + 1 of one chunk, 40 KB), slots over
+// [kXLo, kStage).  Every job costs the issuing thread a barrier wait and a commit (~0.15-0.2 us
+// each on this GPU), so jobs carry two K blocks: eight products per wait.
+constexpr uint32_t kB1Box = kBChunk * 128;
+constexpr uint32_t kB1Slot = 2 * kB1Box;
+constexpr int kB1Slots = 2;
 // dE/dD of one B1 chunk is staged here [128 rows x 160 fp16] and written out in whole row
 // segments; it overlays the split slots, idle during B1
 constexpr uint32_t kStage = kXLo + kB1Slots * kB1Slot;
@@ -59,7 +63,7 @@ constexpr int kSplitSlot = 6;             // barrier index of the first split st
 constexpr int kSplitJobs = 8;             // per split GEMM: 4 K blocks x {hi, lo}, all 240 output columns
 constexpr int kL1Jobs = kKD / 64;         // 25
 constexpr int kB1Chunks = kKD / kBChunk;  // 10
-constexpr int kB1Jobs = 4 * kB1Chunks;    // 40
+constexpr int kB1Jobs = 2 * kB1Chunks;    // 20
 
 struct FitMaps {
   CUtensorMap D;                     // [rows = max_atoms][1600]
@@ -88,8 +92,8 @@ __device__ __forceinline__ unsigned char* align1k(unsigned char* p) {
 }
 
 // The staging slots: barrier k (full: data landed; empty: the MMAs that read it completed) for
-// L1 slots 0..2, B1 slots 0..4 and split slots 6..8.  `uses[k]` counts the jobs through slot k.
-//   L1 job j      -> slot j % 3        B1 job j -> slot j % 5        split job i -> slot 6 + i % 3
+// L1 slots 0..2, B1 slots 0..1 and split slots 6..8.  `uses[k]` counts the jobs through slot k.
+//   L1 job j      -> slot j % 3        B1 job j -> slot j % 2        split job i -> slot 6 + i % 3
 //
 // Each TMA thread processes its own copies one after another (about 0.3 us each from L2,
 // whatever the box size), so three loader threads share the slots: slot k belongs to loader
@@ -137,12 +141,15 @@ struct Loader {
                            keep);
     uses[k] += 1;
   }
-  // B1 job j: W1 rows of chunk (j / 4 + rot) % 10, K block j % 4
+  // B1 job j: W1 rows of chunk (j / 2 + rot) % 10, K blocks 2 (j % 2) and 2 (j % 2) + 1
   __device__ void b1(int ty, int j) {
     const int k = j % kB1Slots;
-    if (begin(k, kB1Slot))
-      tc::tma_load_2d_hint(sm + kXLo + k * kB1Slot, &mp->W1[ty], &full[k], 64 * (j & 3),
-                           kBChunk * (((j >> 2) + rot_b1) % kB1Chunks), keep);
+    if (begin(k, kB1Slot)) {
+      const int row = kBChunk * (((j >> 1) + rot_b1) % kB1Chunks), kb = 2 * (j & 1);
+      unsigned char* dst = sm + kXLo + k * kB1Slot;
+      tc::tma_load_2d_hint(dst, &mp->W1[ty], &full[k], 64 * kb, row, keep);
+      tc::tma_load_2d_hint(dst + kB1Box, &mp->W1[ty], &full[k], 64 * (kb + 1), row, keep);
+    }
     uses[k] += 1;
   }
 };
@@ -327,13 +334,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_mix_fit(const __grid_constant__
           release(k);
         }
       };
-      // B1 chunk n (TMEM region n & 1): four K blocks of dz1 (X_hi) against W1 rows
+      // B1 chunk n (TMEM region n & 1): four K blocks of dz1 (X_hi) against W1 rows, two jobs
       auto issue_b1 = [&](int n) {
-        for (int kb = 0; kb < 4; ++kb) {
-          const int k = (4 * n + kb) % kB1Slots;
+        for (int h = 0; h < 2; ++h) {
+          const int k = (2 * n + h) % kB1Slots;
           if (!consume(k)) return;
-          tc::mma_kblock(tmem + 256 * (n & 1), tc::smem_u32(sm + kXHi + kb * kBlk),
-                         tc::smem_u32(sm + kXLo + k * kB1Slot), id160, kb > 0, 4);
+          const unsigned char* slot = sm + kXLo + k * kB1Slot;
+#pragma unroll
+          for (int q = 0; q < 2; ++q)
+            tc::mma_kblock(tmem + 256 * (n & 1), tc::smem_u32(sm + kXHi + (2 * h + q) * kBlk),
+                           tc::smem_u32(slot + q * kB1Box), id160, (h | q) > 0, 4);
           release(k);
         }
         tc::mma_commit(&accb[n & 1]);
