@@ -452,7 +452,10 @@ dp_status upload_weights(Model* m) {
   DP_CUDA_TRY(m, cudaMemcpy(m->stat64, stat.data(), 8 * stat.size(), cudaMemcpyHostToDevice));
   DP_CUDA_TRY(m, cudaMemcpy(m->stat32, stat32.data(), 4 * stat32.size(), cudaMemcpyHostToDevice));
   DP_TRY(launch_pad_rows(m));
-  if (m->prec == DP_MIX_BF16 || m->prec == DP_MIX_FP16) DP_TRY(launch_tc_setup(m));
+  if (m->prec == DP_MIX_BF16 || m->prec == DP_MIX_FP16) {
+    DP_TRY(launch_tc_setup(m));
+    DP_TRY(launch_emb_images(m));
+  }
   return DP_OK;
 }
 
@@ -565,6 +568,7 @@ dp_status dp_create(dp_model** out, int ntypes, const char* const* type_map, dou
     A_(force32, 16 * N);
     A_(vir_rep, 72 * R + 64);
     A_(tc_weights, mix_fit_weight_bytes(nt));
+    A_(emb_img, mix_emb_image_bytes(nt));
   }
   m->pg_cap = std::min(max_atoms, kPgAtoms);
   m->pg_roff_cap = 2 * (size_t)nt * N + 64;

@@ -108,6 +108,8 @@ struct Model {
   void* tab_mem = nullptr;
   // 16-bit operand copies for the tensor-core kernels (per type), laid out by those kernels
   void* tc_weights = nullptr;
+  void* emb_img = nullptr;    // mixed precision: per embedding pair, the forward's MMA operand
+                              // blocks in their shared-memory byte layout
   size_t tc_weights_bytes = 0;
 
   // atoms (internal, type-sorted order)
@@ -314,6 +316,8 @@ dp_status launch_mix_embed_backward(Model* m, int N);
 // mix_fit.cu (tensor-core fitting net)
 dp_status mix_fit_setup(Model* m);
 size_t mix_fit_weight_bytes(int ntypes);
+size_t mix_emb_image_bytes(int ntypes);
+dp_status launch_emb_images(Model* m);
 dp_status launch_mix_fitting(Model* m, int N);
 void mix_fit_release(Model* m);
 // grid of a tunable mixed kernel: the autotuned value if set, else the default

@@ -50,6 +50,7 @@ struct MixArgs {
   double* vir_atom;      // [N][9] (unused by the mixed backward)
   double* vir_rep;       // [nrep][9] per-replica virial
   const int* irep;       // [N] replica of each internal atom
+  const unsigned char* img;  // per pair: the operand blocks of load_fwd_weights / load_bwd_ops
   const float4* tab;     // tabulated embedding: [pair][interval][100][2] float4 quintic coefficients
   int tab_n;
   float tab_x0, tab_ih;  // first node, 1 / interval width
@@ -230,6 +231,21 @@ __device__ __forceinline__ float w3_elem(const float* __restrict__ W, int k, int
 // Layer-1 weights in FP32 for the CUDA cores (16-byte aligned slots for vector loads):
 // small[0..31] = W1 (25 used), small[32..63] = b1 (25 used).
 constexpr int kSmall = 64;
+// Forward operand image of one embedding pair (built once per weight upload, copied into shared
+// memory by three bulk copies per pair change): B2 | B3 (head, remainder) | small.
+constexpr uint32_t kImgFwdB3 = 8192, kImgFwdSmall = kImgFwdB3 + 2 * 14336, kImgFwd = kImgFwdSmall + kSmall * 4;
+constexpr uint32_t kImgBytes = kImgFwd;
+
+// The three bulk copies of one operand image (B2 | B3 | small, `b3` and `sm_off` bytes in) into
+// shared memory on mbarrier `bar`; issued by one thread.  Out of line: the kernels' register
+// allocation stays that of their main loops.
+__device__ __noinline__ void fetch_image(const unsigned char* img, uint32_t b3, uint32_t sm_off, uint32_t total,
+                                         unsigned char* sB2, unsigned char* sB3, float* small, uint64_t* bar) {
+  tc::mbar_arrive_expect_tx(bar, total);
+  tc::bulk_load(sB2, img, b3, bar);
+  tc::bulk_load(sB3, img + b3, sm_off - b3, bar);
+  tc::bulk_load(small, img + sm_off, total - sm_off, bar);
+}
 __device__ __forceinline__ void load_small(const float* __restrict__ W, float* small) {
   for (int q = threadIdx.x; q < kSmall; q += blockDim.x)
     small[q] = (q & 31) < kN1 ? W[(q < 32 ? kEW1 : kEb1) + (q & 31)] : 0.f;
@@ -455,7 +471,9 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
 
   int total = 0;
   for (int tj = 0; tj < a.ntypes; ++tj) total += a.rowoff[(size_t)tj * (a.N + 1) + a.N];
-  const int per = (total + gridDim.x - 1) / gridDim.x;
+  // at least one full tile per CTA: with few rows (a small box) the CTAs past the last tile
+  // return at once instead of each paying the weight staging for a sliver of rows
+  const int per = max(kRows, (total + gridDim.x - 1) / gridDim.x);
   const int c0 = min(total, blockIdx.x * per), c1 = min(total, c0 + per);
 
   if (t == 0) { tc::mbar_init(&bar, 1); tc::mbar_fence_init(); }
@@ -504,9 +522,15 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_fwd(MixArgs a) {
     const unsigned shared_mask = (unsigned)ti.shared_mask;
     const int np = ti.ti * a.ntypes + ti.tj;
     if (np != pair) {
-      if (!TAB) load_fwd_weights<F16>(a.w + (size_t)np * kEmbParams, sB2, sB3, small);
+      if (!TAB) {  // the pair's operand blocks from its image, on the product barrier (idle here:
+                   // every earlier product has completed)
+        if (t == 0)
+          fetch_image(a.img + (size_t)np * kImgBytes, kImgFwdB3, kImgFwdSmall, kImgFwd, sB2, sB3, small, &bar);
+        ok = tc::mbar_wait(&bar, phase, a.err) && ok;
+        phase ^= 1u;
+      }
       pair = np;
-      __syncthreads();  // layer 1 reads biases written by other threads
+      __syncthreads();
     }
     const long long key0 = (long long)ti.tj * a.N + ti.a0;
     if (carry != key0) {
@@ -751,7 +775,9 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
 
   int total = 0;
   for (int tj = 0; tj < a.ntypes; ++tj) total += a.rowoff[(size_t)tj * (a.N + 1) + a.N];
-  const int per = (total + gridDim.x - 1) / gridDim.x;
+  // at least one full tile per CTA: with few rows (a small box) the CTAs past the last tile
+  // return at once instead of each paying the weight staging for a sliver of rows
+  const int per = max(kRows, (total + gridDim.x - 1) / gridDim.x);
   const int c0 = min(total, blockIdx.x * per), c1 = min(total, c0 + per);
 
   if (t == 0) { tc::mbar_init(&bar, 1); tc::mbar_init(&dbar, 1); tc::mbar_fence_init(); }
@@ -796,6 +822,8 @@ __global__ void __launch_bounds__(kRows, 3) k_mix_embed_bwd(MixArgs a) {
     if (w == kLocWarp && cur + ti.nrows < c1) locate_window(a, cur + ti.nrows, wk, s_tot, sWin);
     const int np = ti.ti * a.ntypes + ti.tj;
     if (np != pair) {
+      // the backward builds its operand blocks itself: fetching them from the image (bulk or
+      // cooperative copy) changed the register allocation of its main loop and cost 4-8%
       if (!TAB) load_bwd_ops<F16>(a.w + (size_t)np * kEmbParams, sB2, sB3, small);
       pair = np;
       __syncthreads();
@@ -1376,6 +1404,7 @@ MixArgs make_mix_args(Model* m, int N) {
   a.rc = (float)m->rc; a.rs = (float)m->rs; a.invS = 1.f / (float)m->S; a.switch_kind = m->switch_kind;
   a.w = m->w32; a.stat = m->stat32; a.itype = m->itype; a.type_off = m->type_off; a.rowoff = m->rowoff;
   a.tab = reinterpret_cast<const float4*>(m->tab32);
+  a.img = static_cast<const unsigned char*>(m->emb_img);
   a.tab_n = m->tab_n;
   a.tab_x0 = (float)m->tab_x0;
   a.tab_ih = m->tab_n ? (float)(1.0 / m->tab_h) : 0.f;
@@ -1387,11 +1416,35 @@ MixArgs make_mix_args(Model* m, int N) {
 }
 
 // (+ 160: sRow (8 ints) and sWin (32 ints); + 1024: alignment of the operand blocks)
+// The forward operand image of every embedding pair: one CTA per pair runs the forward's
+// shared-memory staging into global memory (the same bytes, swizzle included).
+template <bool F16>
+__global__ void __launch_bounds__(kRows) k_emb_images(const float* __restrict__ w, unsigned char* img) {
+  const float* W = w + (size_t)blockIdx.x * kEmbParams;
+  unsigned char* r = img + (size_t)blockIdx.x * kImgBytes;
+  load_fwd_weights<F16>(W, r, r + kImgFwdB3, reinterpret_cast<float*>(r + kImgFwdSmall));
+}
+static_assert(kImgFwd % 16 == 0 && kImgFwdB3 % 16 == 0 && kImgFwdSmall % 16 == 0,
+              "bulk copies need 16-byte sizes and offsets");
+
 constexpr size_t kFwdSmem = 32768 + 4096 + 8192 + 2 * 14336 + kSmall * 4 + 160 + 1024;
 constexpr size_t kBwdSmem =
     32768 + 8192 + 16384 + kMaxAtoms * kN3 * 16 + kRows * (16 + 4 + 8) + kSmall * 4 + 160 + 1024;
 
 }  // namespace
+
+size_t mix_emb_image_bytes(int ntypes) { return (size_t)ntypes * ntypes * kImgBytes; }
+
+dp_status launch_emb_images(Model* m) {
+  const int npairs = m->ntypes * m->ntypes;
+  if (m->prec == DP_MIX_FP16)
+    k_emb_images<true><<<npairs, kRows, 0, m->stream>>>(m->w32, static_cast<unsigned char*>(m->emb_img));
+  else
+    k_emb_images<false><<<npairs, kRows, 0, m->stream>>>(m->w32, static_cast<unsigned char*>(m->emb_img));
+  m->launches += 1;
+  DP_LAUNCH_CHECK(m);
+  return DP_OK;
+}
 
 dp_status launch_mix_descriptor(Model* m, int N) {
   const int nblk = cdiv(N, 1024);
