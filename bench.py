@@ -209,16 +209,20 @@ def run_reference(args, world, rank):
 TANH_PER_NEIGHBOUR = 175
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
-# the 32,000-atom copper box, per real neighbour row, scaled to a launch by the row count.  Each
-# entry names the source file of the kernel and its SHA-1 at the capture: when the file has
-# changed since, the figure no longer describes the kernel and `traffic` is reported as null.
+# the 32,000-atom copper box, per real neighbour row (embedding kernels) or per atom (fitting),
+# scaled to a launch by the row or atom count.  Each entry names the source file of the kernel
+# and its SHA-1 at the capture: when the file has changed since, the figure no longer describes
+# the kernel and `traffic` is reported as null.
 TRAFFIC_PER_ROW = {
-    ("embedding_backward", "mix_fp16"): {"bytes_per_row": (171.752960e6 + 4.357888e6) / 5726060,
+    ("embedding_backward", "mix_fp16"): {"bytes_per_unit": (171.784448e6 + 4.521984e6) / 5726060, "unit": "row",
                                          "source": "paper_2410_22867_gb300/csrc/mix_embed.cu",
-                                         "sha1": "e859ed66e8863603f9cf708684bee130645f3875"},
-    ("embedding_forward", "mix_fp16"): {"bytes_per_row": (95.665408e6 + 21.460480e6) / 5726060,
+                                         "sha1": "6f6ae8c2452f3221d1e7684b71aefd4ddf1483f5"},
+    ("embedding_forward", "mix_fp16"): {"bytes_per_unit": (95.683328e6 + 21.243904e6) / 5726060, "unit": "row",
                                         "source": "paper_2410_22867_gb300/csrc/mix_embed.cu",
-                                        "sha1": "e859ed66e8863603f9cf708684bee130645f3875"},
+                                        "sha1": "6f6ae8c2452f3221d1e7684b71aefd4ddf1483f5"},
+    ("fitting", "mix_fp16"): {"bytes_per_unit": (106.631680e6 + 75.120640e6) / 32000, "unit": "atom",
+                              "source": "paper_2410_22867_gb300/csrc/mix_fit.cu",
+                              "sha1": "a9afad59b8d8cbab7736d97dcdeeb23fd961956c"},
 }
 
 
@@ -231,11 +235,11 @@ def _sha1(path):
         return None
 
 
-def traffic_per_launch(kernel, prec, rows):
+def traffic_per_launch(kernel, prec, rows, atoms):
     e = TRAFFIC_PER_ROW.get((kernel, prec))
     if e is None or _sha1(e["source"]) != e["sha1"]:
         return None
-    return e["bytes_per_row"] * rows
+    return e["bytes_per_unit"] * (rows if e["unit"] == "row" else atoms)
 
 
 def measured_peaks(dp):
@@ -265,7 +269,7 @@ def roofline(prec, kernel, ms, N, n_neigh, alu):
     pk, src = peaks()
     t = ms * 1e-3
     mixed = prec.startswith("mix")
-    out = {"kernel": kernel, "kernel_ms": ms, "traffic": traffic_per_launch(kernel, prec, n_neigh)}
+    out = {"kernel": kernel, "kernel_ms": ms, "traffic": traffic_per_launch(kernel, prec, n_neigh, N)}
     if kernel in ("embedding_forward", "embedding_backward"):
         flop = n_neigh * (EMB_FWD_FLOP_PER_NEIGHBOUR if kernel == "embedding_forward" else EMB_BWD_FLOP_PER_NEIGHBOUR)
     elif kernel == "fitting":
