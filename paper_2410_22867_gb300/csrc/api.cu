@@ -215,7 +215,7 @@ dp_status map_err_bits(Model* m, int bits) {
 dp_status md_step(Model* m, int N, double dt, bool rebuild) {
   DP_TRY(launch_kick_drift(m, N, dt));
   if (rebuild) {
-    DP_TRY(launch_rebuild(m, N));
+    DP_TRY(launch_rebuild(m, N, true));
   } else {
     DP_TRY(launch_delta(m, N));
   }
@@ -369,7 +369,7 @@ dp_status run_md(Model* m, dp_md_state* st, double dt, int nsteps, int capture, 
     DP_TRY(launch_type_sort(m, st->types, N));
     DP_TRY(launch_load_positions(m, st->x, N));
     DP_TRY(launch_load_state(m, N, st->v, mass_t_dev));
-    DP_TRY(launch_rebuild(m, N));
+    DP_TRY(launch_rebuild(m, N, true));
     DP_TRY(force_eval(m, N));
   }
   Model::GraphCache& gc = m->graphs;
@@ -607,7 +607,7 @@ dp_status dp_compute_batch(dp_model* h, int nrep, const int* atom_offsets, const
   m->natoms = N;
   DP_TRY(launch_type_sort(m, types, N));
   DP_TRY(launch_load_positions(m, coords, N));
-  DP_TRY(launch_rebuild(m, N));
+  DP_TRY(launch_rebuild(m, N, false));
   DP_TRY(force_eval(m, N));
   DP_TRY(launch_outputs(m, N, energies, atom_energy, forces, virials));
   return DP_OK;
@@ -830,7 +830,7 @@ extern "C" dp_status dp_param_grad(dp_model* h, int natoms, const double* coords
   m->natoms = natoms;
   DP_TRY(launch_type_sort(m, types, natoms));
   DP_TRY(launch_load_positions(m, coords, natoms));
-  DP_TRY(launch_rebuild(m, natoms));
+  DP_TRY(launch_rebuild(m, natoms, false));
   DP_TRY(force_eval(m, natoms));
   return launch_param_grad(m, natoms, F0, E0, cE, cF, grad, loss);
 }

@@ -294,7 +294,10 @@ __host__ __device__ __forceinline__ int cdiv_dev(int a, int b) { return (a + b -
 // nlist.cu
 dp_status launch_type_sort(Model* m, const int* types_user, int N);
 dp_status launch_load_positions(Model* m, const double* coords_user, int N);
-dp_status launch_rebuild(Model* m, int N);
+// Cell binning and the Verlet list of every atom.  with_skin: pairs within r_c + skin (MD: the
+// list serves the next steps); otherwise within r_c (a single evaluation: the list is rebuilt on
+// every call, so the skin would only add entries).
+dp_status launch_rebuild(Model* m, int N, bool with_skin);
 dp_status launch_delta(Model* m, int N);
 dp_status launch_format(Model* m, int N);
 dp_status launch_get_nlist(Model* m, int N, int* nlist, int* images);

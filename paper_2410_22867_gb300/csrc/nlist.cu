@@ -246,6 +246,7 @@ struct VerletArgs {
   int* vl_img;
   float4* vl_d0;
   int* vcount;
+  int* cell_flag;              // per cell: 1 = its atoms are left to k_verlet (null: all atoms)
   int* err;
 };
 
@@ -281,6 +282,7 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int i = blockIdx.x * kVerletWarps + w;
   if (i >= a.N) return;
+  if (a.cell_flag && a.cell_flag[a.cell_of[i]] == 0) return;  // done by k_verlet_cell
   if (lane < kMaxTypes) cnt[w][lane] = 0;
   __syncwarp();
   const RepGeom& g = a.geom[a.irep[i]];
@@ -400,6 +402,151 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
       nt_ = a.vcap[lane];
     }
     a.vcount[(size_t)i * a.ntypes + lane] = nt_;
+  }
+}
+
+// Verlet list by cell: one CTA per cell stages the candidates of the cell's whole stencil in
+// shared memory once (index, position plus image shift, stencil slot), and each of its warps
+// tests one of the cell's atoms against them, with the same FP32 test, image codes and fixed-point
+// pair vectors as k_verlet.  A cell's atoms share one stencil, so its candidates are read from L2
+// once per cell instead of once per atom.  Cells whose stencil has more than kMaxStencil cells or
+// more than kCellCap candidates (small or sparse boxes) are flagged and left to k_verlet.
+constexpr int kCellWarps = 4;
+constexpr int kCellCap = 2048;
+constexpr int kMaxStencil = 125;
+constexpr size_t kCellSmem = (size_t)kCellCap * (sizeof(float4) + sizeof(int) + 1);
+
+__global__ void __launch_bounds__(32 * kCellWarps) k_verlet_cell(VerletArgs a) {
+  extern __shared__ float4 s_cx[];                                   // [kCellCap] position + shift, w = type
+  int* s_cj = reinterpret_cast<int*>(s_cx + kCellCap);               // [kCellCap] atom
+  unsigned char* s_ck = reinterpret_cast<unsigned char*>(s_cj + kCellCap);  // [kCellCap] stencil slot
+  __shared__ int s_beg[kMaxStencil], s_off[kMaxStencil + 1], s_code[kMaxStencil];
+  __shared__ float s_sh[kMaxStencil][3];
+  __shared__ long long s_shq[kMaxStencil][3];
+  __shared__ int s_wsum[kCellWarps], s_total;
+  const int cid = blockIdx.x;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int cb = a.cell_start[cid], ce = a.cell_start[cid + 1];
+  if (cb == ce) {
+    if (t == 0) a.cell_flag[cid] = 0;
+    return;
+  }
+  const RepGeom& g = a.geom[a.irep[a.cell_atoms[cb]]];
+  const int sy = 2 * g.m[1] + 1, sz = 2 * g.m[2] + 1;
+  const int ncell = (2 * g.m[0] + 1) * sy * sz;
+  if (ncell > kMaxStencil) {
+    if (t == 0) a.cell_flag[cid] = 1;
+    return;
+  }
+  const int rel = cid - g.cell_off;
+  const int ci[3] = {rel / (g.nc[1] * g.nc[2]), (rel / g.nc[2]) % g.nc[1], rel % g.nc[2]};
+  int num = 0;
+  if (t < ncell) {
+    const int o[3] = {t / (sy * sz) - g.m[0], (t / sz) % sy - g.m[1], t % sz - g.m[2]};
+    int n[3], cc[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int v = ci[q] + o[q];
+      n[q] = floor_div(v, g.nc[q]);
+      cc[q] = v - n[q] * g.nc[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      s_sh[t][q] = ((float)n[0] * g.Hf[q] + (float)n[1] * g.Hf[3 + q]) + (float)n[2] * g.Hf[6 + q];
+      s_shq[t][q] = g.tri ? (long long)n[0] * g.Hq[q] + (long long)n[1] * g.Hq[3 + q] + (long long)n[2] * g.Hq[6 + q]
+                          : (long long)n[q] * g.Hq[4 * q];
+    }
+    const int c = g.cell_off + (cc[0] * g.nc[1] + cc[1]) * g.nc[2] + cc[2];
+    s_beg[t] = a.cell_start[c];
+    num = a.cell_start[c + 1] - s_beg[t];
+    s_code[t] = pack_img(n[0], n[1], n[2]);
+  }
+  // exclusive prefix of the stencil cells' sizes
+  int incl = num;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_wsum[w] = incl;
+  __syncthreads();
+  int base = 0;
+  for (int u = 0; u < w; ++u) base += s_wsum[u];
+  if (t < ncell) s_off[t] = base + incl - num;
+  if (t == 32 * kCellWarps - 1) s_total = base + incl;
+  __syncthreads();
+  const int T = s_total;
+  if (T > kCellCap) {
+    if (t == 0) a.cell_flag[cid] = 1;
+    return;
+  }
+  if (t == 0) {
+    a.cell_flag[cid] = 0;
+    s_off[ncell] = T;
+  }
+  for (int q = t; q < T; q += 32 * kCellWarps) {
+    int lo = 0, hi = ncell - 1;  // the stencil slot holding candidate q
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_off[mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    const int idx = s_beg[lo] + q - s_off[lo];
+    const float4 xf = a.cell_xf[idx];
+    s_cx[q] = make_float4(xf.x + s_sh[lo][0], xf.y + s_sh[lo][1], xf.z + s_sh[lo][2], xf.w);
+    s_cj[q] = a.cell_atoms[idx];
+    s_ck[q] = (unsigned char)lo;
+  }
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+  const int self_code = pack_img(0, 0, 0);
+  for (int ca = cb + w; ca < ce; ca += kCellWarps) {
+    const int i = a.cell_atoms[ca];
+    const float4 xfi = a.xf[i];
+    const qvec4 qi = a.xq[i];
+    const size_t ebase = (size_t)i * a.VS;
+    int cnt[kMaxTypes] = {0, 0, 0, 0};  // the same in every lane
+    for (int b = 0; b < T; b += 32) {
+      const int q = b + lane;
+      bool acc = false;
+      int j = -1, tj = 0, k = 0;
+      if (q < T) {
+        const float4 c4 = s_cx[q];
+        j = s_cj[q];
+        k = s_ck[q];
+        if (!(j == i && s_code[k] == self_code)) {
+          const float dx = c4.x - xfi.x, dy = c4.y - xfi.y, dz = c4.z - xfi.z;
+          acc = dx * dx + dy * dy + dz * dz < a.rcs2_hi;
+          tj = __float_as_int(c4.w);
+        }
+      }
+#pragma unroll
+      for (int tt = 0; tt < kMaxTypes; ++tt) {
+        if (tt >= a.ntypes) break;
+        const unsigned mask = __ballot_sync(0xffffffffu, acc && tj == tt);
+        if (acc && tj == tt) {
+          const int pos = cnt[tt] + __popc(mask & lt);
+          if (pos < a.vcap[tt]) {
+            const qvec4 qj = a.xq[j];
+            const size_t e = ebase + a.vcap_off[tt] + pos;
+            a.vl_j[e] = j;
+            a.vl_img[e] = s_code[k];
+            a.vl_d0[e] = make_float4(fixed_diff(qj.x, qi.x, s_shq[k][0]), fixed_diff(qj.y, qi.y, s_shq[k][1]),
+                                     fixed_diff(qj.z, qi.z, s_shq[k][2]), 0.f);
+          }
+        }
+        cnt[tt] += __popc(mask);
+      }
+    }
+#pragma unroll
+    for (int tt = 0; tt < kMaxTypes; ++tt)
+      if (lane == tt && tt < a.ntypes) {
+        int nt_ = cnt[tt];
+        if (nt_ > a.vcap[tt]) {
+          set_err(a.err, ERR_VCAP);
+          nt_ = a.vcap[tt];
+        }
+        a.vcount[(size_t)i * a.ntypes + tt] = nt_;
+      }
   }
 }
 
@@ -644,7 +791,7 @@ static double max_box_length(const Model* m) {
   return Lmax;
 }
 
-dp_status launch_rebuild(Model* m, int N) {
+dp_status launch_rebuild(Model* m, int N, bool with_skin) {
   cudaStream_t s = m->stream;
   DP_CUDA_TRY(m, cudaMemsetAsync(m->cell_count, 0, sizeof(int) * m->ncells, s));
   DP_CUDA_TRY(m, cudaMemsetAsync(m->cell_fill, 0, sizeof(int) * m->ncells, s));
@@ -660,7 +807,7 @@ dp_status launch_rebuild(Model* m, int N) {
     a.vcap_off[t] = m->vcap_off[t];
   }
   a.vcap_off[m->ntypes] = m->vcap_off[m->ntypes];
-  const double rcs = m->rc + m->skin;
+  const double rcs = m->rc + (with_skin ? m->skin : 0.0);
   a.rcs2 = rcs * rcs;
   // worst-case FP32 error of the prefilter's r^2 is ~1.3e-6 * rcs * Lmax; use 10x that
   double band = 1.25e-5 * rcs * (max_box_length(m) + rcs) + 1e-3;
@@ -668,8 +815,13 @@ dp_status launch_rebuild(Model* m, int N) {
   a.itype = m->itype; a.irep = m->irep; a.geom = m->geom; a.x = m->x; a.xf = m->xf; a.xq = m->xq;
   a.cell_of = m->cell_of; a.cell_start = m->cell_start; a.cell_atoms = m->cell_atoms; a.cell_xf = m->cell_xf;
   a.vl_j = m->vl_j; a.vl_img = m->vl_img; a.vl_d0 = m->vl_d0; a.vcount = m->vcount; a.err = m->err;
+  // cells by k_verlet_cell; the atoms of the cells it flags (cell_fill is free again after the
+  // scatter and holds the flags) by k_verlet
+  a.cell_flag = m->cell_fill;
+  DP_CUDA_TRY(m, ensure_smem(reinterpret_cast<const void*>(k_verlet_cell), kCellSmem));
+  k_verlet_cell<<<m->ncells, 32 * kCellWarps, kCellSmem, s>>>(a);
   k_verlet<<<cdiv(N, kVerletWarps), 32 * kVerletWarps, 0, s>>>(a);
-  m->launches += 4;
+  m->launches += 5;
   DP_LAUNCH_CHECK(m);
   return DP_OK;
 }
