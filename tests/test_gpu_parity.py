@@ -78,6 +78,44 @@ def test_nlist_bit_exact_sparse_box(dp, prec):
     m.close()
 
 
+def _stencil_candidates(coords, L, nc, m):
+    """Atoms in the (2m+1)^3 periodic stencil of every non-empty cell of an nc^3 grid."""
+    idx = np.minimum((np.mod(coords, L) / (L / nc)).astype(int), nc - 1)
+    cnt = np.zeros((nc, nc, nc), dtype=np.int64)
+    np.add.at(cnt, (idx[:, 0], idx[:, 1], idx[:, 2]), 1)
+    tot = np.zeros_like(cnt)
+    for o in np.ndindex(2 * m + 1, 2 * m + 1, 2 * m + 1):
+        tot += np.roll(cnt, shift=tuple(m - np.array(o)), axis=(0, 1, 2))
+    return tot[cnt > 0]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mix_fp16"])
+def test_nlist_bit_exact_dense_cluster(dp, prec):
+    # A compressed 4,000-atom FCC cluster (a = 2.4 A) in a 42 A box, r_c 6 + skin 2: the cells
+    # (10^3, edge 4.2 A, 5^3 stencil) inside the cluster see more candidates than one CTA of the
+    # cell-staged Verlet build holds, the cells at its surface fewer, so both Verlet kernels
+    # write parts of the same list.  Checked for the r_c list of a single evaluation and for the
+    # r_c + skin list an MD run starts from.
+    c = synth.copper_fcc(10, 7, a=2.4, sigma=0.05)
+    L = 42.0
+    s = synth.System(c.coords + 9.0, c.types, np.array([L, 0, 0, 0, L, 0, 0, 0, L], dtype=np.float64), c.type_names)
+    cand = _stencil_candidates(s.coords, L, 10, 2)
+    assert cand.max() > 2048 and cand.min() <= 2048
+    w = synth.xavier_weights(("Cu",), 6.0, 0.5, (320,), 1001)
+    ref_nl, ref_im, _, ovf = oracle.Model(w.to_blob()).nlist(s.coords, s.types, s.box, "cell")
+    assert not ovf
+    m = dp.DPModel(w, prec, max_atoms=s.natoms)
+    x, t = _cuda(s)
+    m.compute(x, t, s.box)
+    nl, im = m.get_nlist()
+    _nl_rows_equal(nl.cpu().numpy(), im.cpu().numpy(), ref_nl, ref_im)
+    st = m.md_state(x.clone(), torch.zeros_like(x), t, s.box, s.masses(), rebuild_every=10)
+    m.verlet(st, 0.5, 0, capture_graph=False)
+    nl, im = m.get_nlist()
+    _nl_rows_equal(nl.cpu().numpy(), im.cpu().numpy(), ref_nl, ref_im)
+    m.close()
+
+
 def test_nlist_bit_exact_copper_full(dp):
     s = synth.copper_fcc(32, 0)
     w = synth.copper_weights()
