@@ -549,7 +549,7 @@ dp_status dp_create(dp_model** out, int ntypes, const char* const* type_map, dou
   A_(cell_of, 4 * N);
   A_(cell_count, 4 * (size_t)m->max_cells); A_(cell_start, 4 * ((size_t)m->max_cells + 1));
   A_(cell_fill, 4 * (size_t)m->max_cells); A_(cell_atoms, 4 * N); A_(cell_xf, 16 * N);
-  A_(vl_j, 4 * N * m->VS); A_(vl_img, 4 * N * m->VS); A_(vl_d0, 16 * N * m->VS); A_(vcount, 4 * N * nt);
+  A_(vl_e, 16 * N * m->VS); A_(vl_img, 4 * N * m->VS); A_(vcount, 4 * N * nt);
   A_(nl_j, 4 * N * m->S); A_(nl_img, 4 * N * m->S);
   A_(nl_d, (prec == DP_FP64 ? 32 : 16) * N * m->S);
   A_(nl_count, 4 * N * nt);
@@ -727,6 +727,8 @@ dp_status dp_get_nlist(dp_model* h, int* nlist, int* images) {
   if (!h || !nlist || !images) return DP_ERR_ARG;
   Model* m = &h->m;
   if (m->natoms < 1) { m->last_error = "no neighbour list yet"; return DP_ERR_ARG; }
+  // the per-step format leaves the image codes out; this pass repeats it with them
+  DP_TRY(launch_format(m, m->natoms, true));
   DP_TRY(launch_get_nlist(m, m->natoms, nlist, images));
   DP_CUDA_TRY(m, cudaStreamSynchronize(m->stream));
   return DP_OK;

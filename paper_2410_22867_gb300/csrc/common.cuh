@@ -145,14 +145,13 @@ struct Model {
   float4* cell_xf = nullptr;  // [N] FP32 positions in cell order (beside cell_atoms)
 
   // Verlet list (r_c + skin)
-  int* vl_j = nullptr;        // [N*VS]
-  int* vl_img = nullptr;      // [N*VS]
-  float4* vl_d0 = nullptr;    // [N*VS] pair vector at rebuild (fp32)
+  float4* vl_e = nullptr;     // [N*VS] pair vector at rebuild (fp32), w = neighbour index
+  int* vl_img = nullptr;      // [N*VS] image code
   int* vcount = nullptr;      // [N*nt]
 
   // formatted list (r_c), compacted per type segment
   int* nl_j = nullptr;        // [N*S]
-  int* nl_img = nullptr;      // [N*S]
+  int* nl_img = nullptr;      // [N*S] image codes, written only for dp_get_nlist
   void* nl_d = nullptr;       // [N*S] float4 (fp32 modes) or dvec4 (fp64)
   int* nl_count = nullptr;    // [N*nt]
 
@@ -299,7 +298,7 @@ dp_status launch_load_positions(Model* m, const double* coords_user, int N);
 // every call, so the skin would only add entries).
 dp_status launch_rebuild(Model* m, int N, bool with_skin);
 dp_status launch_delta(Model* m, int N);
-dp_status launch_format(Model* m, int N);
+dp_status launch_format(Model* m, int N, bool images = false);  // images: also the image codes
 dp_status launch_get_nlist(Model* m, int N, int* nlist, int* images);
 // tab.cu
 dp_status launch_tabulate(Model* m, double x0, double x1, int n);

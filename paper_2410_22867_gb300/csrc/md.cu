@@ -24,25 +24,42 @@ __global__ void k_unpermute(int N, const int* __restrict__ perm, const double* _
   }
 }
 
-// One block per replica: fixed-order tree sums (deterministic).
+// One block per replica: fixed-order tree sums (deterministic: every thread sums a fixed
+// strided subset, four independent loads per pass, then a fixed tree).
 // Per-replica energy and virial: sums of the per-atom values (caller order), or for the
 // virial the per-replica accumulator vir_rep when the backward produced one.
-__global__ void k_rep_reduce(int nrep, const int* __restrict__ rep_off, const double* __restrict__ e_user,
-                             const double* __restrict__ vir_user, const double* __restrict__ vir_rep,
-                             double* energy, double* virial, const int* __restrict__ err) {
-  __shared__ double part[10][256];
+constexpr int kRedThreads = 512;
+__global__ void __launch_bounds__(kRedThreads) k_rep_reduce(int nrep, const int* __restrict__ rep_off,
+                                                           const double* __restrict__ e_user,
+                                                           const double* __restrict__ vir_user,
+                                                           const double* __restrict__ vir_rep, double* energy,
+                                                           double* virial, const int* __restrict__ err) {
+  __shared__ double part[10][kRedThreads];
   int r = blockIdx.x;
   if (r >= nrep) return;
   int beg = rep_off[r], end = rep_off[r + 1];
   double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  for (int u = beg + threadIdx.x; u < end; u += 256) {
-    acc[0] += e_user[u];
-    if (vir_user)
-      for (int q = 0; q < 9; ++q) acc[1 + q] += vir_user[(size_t)u * 9 + q];
+  for (int u0 = beg + threadIdx.x; u0 < end; u0 += 4 * kRedThreads) {
+    double e[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int u = u0 + k * kRedThreads;
+      e[k] = u < end ? e_user[u] : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[0] += e[k];
+    if (vir_user) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int u = u0 + k * kRedThreads;
+        if (u < end)
+          for (int q = 0; q < 9; ++q) acc[1 + q] += vir_user[(size_t)u * 9 + q];
+      }
+    }
   }
   for (int q = 0; q < 10; ++q) part[q][threadIdx.x] = acc[q];
   __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s)
       for (int q = 0; q < 10; ++q) part[q][threadIdx.x] += part[q][threadIdx.x + s];
     __syncthreads();
@@ -116,8 +133,9 @@ dp_status launch_outputs(Model* m, int N, double* energy_rep, double* atom_energ
   k_unpermute<<<cdiv(N, 256), 256, 0, m->stream>>>(N, m->perm, m->e_atom, m->vir_atom, m->force, m->e_user,
                                                    m->vir_user, forces);
   const bool mixed = is_mixed(m);
-  k_rep_reduce<<<m->nrep, 256, 0, m->stream>>>(m->nrep, m->rep_off_dev, m->e_user, mixed ? nullptr : m->vir_user,
-                                                mixed ? m->vir_rep : nullptr, energy_rep, virial_rep, m->err);
+  k_rep_reduce<<<m->nrep, kRedThreads, 0, m->stream>>>(m->nrep, m->rep_off_dev, m->e_user,
+                                                        mixed ? nullptr : m->vir_user, mixed ? m->vir_rep : nullptr,
+                                                        energy_rep, virial_rep, m->err);
   m->launches += 2;
   if (atom_energy)
     DP_CUDA_TRY(m, cudaMemcpyAsync(atom_energy, m->e_user, sizeof(double) * N, cudaMemcpyDeviceToDevice,
@@ -162,8 +180,8 @@ dp_status launch_store_state(Model* m, int N, double* x_user, double* v_user) {
 
 dp_status launch_kinetic(Model* m, int N, double* ke_rep) {
   k_kinetic_atoms<<<cdiv(N, 256), 256, 0, m->stream>>>(N, m->perm, m->v, m->mass, m->ke_user);
-  k_rep_reduce<<<m->nrep, 256, 0, m->stream>>>(m->nrep, m->rep_off_dev, m->ke_user, nullptr, nullptr, ke_rep,
-                                                nullptr, nullptr);
+  k_rep_reduce<<<m->nrep, kRedThreads, 0, m->stream>>>(m->nrep, m->rep_off_dev, m->ke_user, nullptr, nullptr,
+                                                        ke_rep, nullptr, nullptr);
   m->launches += 2;
   DP_LAUNCH_CHECK(m);
   return DP_OK;

@@ -242,9 +242,8 @@ struct VerletArgs {
   const int* cell_start;
   const int* cell_atoms;
   const float4* cell_xf;
-  int* vl_j;
-  int* vl_img;
-  float4* vl_d0;
+  float4* vl_e;                // entry: pair vector at rebuild (fp32), w = neighbour index (bits)
+  int* vl_img;                 // entry: image code (read by the format near the cutoff only)
   int* vcount;
   int* cell_flag;              // per cell: 1 = its atoms are left to k_verlet (null: all atoms)
   int* err;
@@ -274,7 +273,8 @@ __device__ __forceinline__ float fixed_diff(long long qj, long long qi, long lon
 // the list, grouped by neighbour type, in the order found: every consumer is independent
 // of the order within a type (the descriptor is a sum over neighbours; the format is a
 // compaction), and dp_get_nlist sorts a copy into the canonical order.  The pair vector at
-// rebuild is formed exactly from fixed-point positions and stored in FP32.
+// rebuild is formed exactly from fixed-point positions and stored in FP32, with the neighbour's
+// index in its fourth word, so that the per-step format reads one 16-byte entry.
 __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
   __shared__ int cnt[kVerletWarps][kMaxTypes];
   __shared__ int s_beg[kVerletWarps][32], s_off[kVerletWarps][32], s_img[kVerletWarps][32];
@@ -328,7 +328,6 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
           unpack_img(code, n0, n1, n2);
           const qvec4 qj = a.xq[j];
           const size_t e = ebase + a.vcap_off[t] + pos;
-          a.vl_j[e] = j;
           a.vl_img[e] = code;
           long long shq[3];
           if (!g.tri) {
@@ -340,8 +339,8 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
             for (int c = 0; c < 3; ++c)
               shq[c] = (long long)n0 * g.Hq[c] + (long long)n1 * g.Hq[3 + c] + (long long)n2 * g.Hq[6 + c];
           }
-          a.vl_d0[e] = make_float4(fixed_diff(qj.x, qi.x, shq[0]), fixed_diff(qj.y, qi.y, shq[1]),
-                                   fixed_diff(qj.z, qi.z, shq[2]), 0.f);
+          a.vl_e[e] = make_float4(fixed_diff(qj.x, qi.x, shq[0]), fixed_diff(qj.y, qi.y, shq[1]),
+                                  fixed_diff(qj.z, qi.z, shq[2]), __int_as_float(j));
         }
       }
       __syncwarp();
@@ -407,23 +406,28 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
 
 // Verlet list by cell: one CTA per cell stages the candidates of the cell's whole stencil in
 // shared memory once (index, position plus image shift, stencil slot), and each of its warps
-// tests one of the cell's atoms against them, with the same FP32 test, image codes and fixed-point
-// pair vectors as k_verlet.  A cell's atoms share one stencil, so its candidates are read from L2
-// once per cell instead of once per atom.  Cells whose stencil has more than kMaxStencil cells or
+// tests one of the cell's atoms against them, with the same FP32 test and image codes as
+// k_verlet.  A cell's atoms share one stencil, so its candidates are read from L2 once per cell
+// instead of once per atom.  Accepted candidates go to a per-warp queue with their list slots;
+// the exact pair vectors (an L2 gather of the fixed-point position and integer arithmetic) are
+// formed 32 at a time from the queue, with every lane busy, instead of in the test loop where a
+// quarter of the lanes or fewer accept.  Cells whose stencil has more than kMaxStencil cells or
 // more than kCellCap candidates (small or sparse boxes) are flagged and left to k_verlet.
-constexpr int kCellWarps = 4;
+constexpr int kCellWarps = 8;
 constexpr int kCellCap = 2048;
 constexpr int kMaxStencil = 125;
-constexpr size_t kCellSmem = (size_t)kCellCap * (sizeof(float4) + sizeof(int) + 1);
+constexpr int kQueue = 64;
+constexpr size_t kCellSmem = (size_t)kCellCap * (sizeof(float4) + sizeof(int));
 
 __global__ void __launch_bounds__(32 * kCellWarps) k_verlet_cell(VerletArgs a) {
-  extern __shared__ float4 s_cx[];                                   // [kCellCap] position + shift, w = type
-  int* s_cj = reinterpret_cast<int*>(s_cx + kCellCap);               // [kCellCap] atom
-  unsigned char* s_ck = reinterpret_cast<unsigned char*>(s_cj + kCellCap);  // [kCellCap] stencil slot
+  extern __shared__ float4 s_cx[];                      // [kCellCap] position + shift, w = type | stencil slot << 8
+  int* s_cj = reinterpret_cast<int*>(s_cx + kCellCap);  // [kCellCap] atom
   __shared__ int s_beg[kMaxStencil], s_off[kMaxStencil + 1], s_code[kMaxStencil];
   __shared__ float s_sh[kMaxStencil][3];
   __shared__ long long s_shq[kMaxStencil][3];
   __shared__ int s_wsum[kCellWarps], s_total;
+  __shared__ int s_qj[kCellWarps][kQueue], s_qe[kCellWarps][kQueue];  // queue: atom, slot in the row
+  __shared__ unsigned char s_qk[kCellWarps][kQueue];                  // queue: stencil slot
   const int cid = blockIdx.x;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int cb = a.cell_start[cid], ce = a.cell_start[cid + 1];
@@ -438,6 +442,9 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_verlet_cell(VerletArgs a) {
     if (t == 0) a.cell_flag[cid] = 1;
     return;
   }
+  // the slot of offset (0, 0, 0): the only one with image (0, 0, 0) and this very cell, so a
+  // candidate is the centre itself exactly when it is atom i in this slot
+  const int kc = (g.m[0] * sy + g.m[1]) * sz + g.m[2];
   const int rel = cid - g.cell_off;
   const int ci[3] = {rel / (g.nc[1] * g.nc[2]), (rel / g.nc[2]) % g.nc[1], rel % g.nc[2]};
   int num = 0;
@@ -461,7 +468,7 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_verlet_cell(VerletArgs a) {
     num = a.cell_start[c + 1] - s_beg[t];
     s_code[t] = pack_img(n[0], n[1], n[2]);
   }
-  // exclusive prefix of the stencil cells' sizes
+  // exclusive prefix of the stencil cells' sizes (ncell <= 125 < 32 * kCellWarps)
   int incl = num;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -484,27 +491,66 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_verlet_cell(VerletArgs a) {
     a.cell_flag[cid] = 0;
     s_off[ncell] = T;
   }
-  for (int q = t; q < T; q += 32 * kCellWarps) {
-    int lo = 0, hi = ncell - 1;  // the stencil slot holding candidate q
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_off[mid] <= q) lo = mid; else hi = mid - 1;
+  // staging: four candidates per thread per pass, their loads issued together
+  constexpr int kSt = 4;
+  for (int q0 = t; q0 < T; q0 += kSt * 32 * kCellWarps) {
+    int idx[kSt], slot[kSt];
+#pragma unroll
+    for (int u = 0; u < kSt; ++u) {
+      const int q = q0 + u * 32 * kCellWarps;
+      idx[u] = 0;
+      slot[u] = 0;
+      if (q < T) {
+        int lo = 0, hi = ncell - 1;  // the stencil slot holding candidate q
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_off[mid] <= q) lo = mid; else hi = mid - 1;
+        }
+        slot[u] = lo;
+        idx[u] = s_beg[lo] + q - s_off[lo];
+      }
     }
-    const int idx = s_beg[lo] + q - s_off[lo];
-    const float4 xf = a.cell_xf[idx];
-    s_cx[q] = make_float4(xf.x + s_sh[lo][0], xf.y + s_sh[lo][1], xf.z + s_sh[lo][2], xf.w);
-    s_cj[q] = a.cell_atoms[idx];
-    s_ck[q] = (unsigned char)lo;
+    float4 xf[kSt];
+    int ja[kSt];
+#pragma unroll
+    for (int u = 0; u < kSt; ++u) {
+      const bool in = q0 + u * 32 * kCellWarps < T;
+      xf[u] = in ? a.cell_xf[idx[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+      ja[u] = in ? a.cell_atoms[idx[u]] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < kSt; ++u) {
+      const int q = q0 + u * 32 * kCellWarps;
+      if (q < T) {
+        const int k = slot[u];
+        s_cx[q] = make_float4(xf[u].x + s_sh[k][0], xf[u].y + s_sh[k][1], xf[u].z + s_sh[k][2],
+                              __int_as_float(__float_as_int(xf[u].w) | (k << 8)));
+        s_cj[q] = ja[u];
+      }
+    }
   }
   __syncthreads();
   const unsigned lt = (1u << lane) - 1u;
-  const int self_code = pack_img(0, 0, 0);
   for (int ca = cb + w; ca < ce; ca += kCellWarps) {
     const int i = a.cell_atoms[ca];
     const float4 xfi = a.xf[i];
     const qvec4 qi = a.xq[i];
     const size_t ebase = (size_t)i * a.VS;
+    // the queued entries [0, qn): exact pair vectors and the list writes, one entry per lane
+    auto drain = [&](int qn) {
+      __syncwarp();
+      if (lane < qn) {
+        const int j = s_qj[w][lane], k = s_qk[w][lane];
+        const size_t e = ebase + s_qe[w][lane];
+        const qvec4 qj = a.xq[j];
+        a.vl_img[e] = s_code[k];
+        a.vl_e[e] = make_float4(fixed_diff(qj.x, qi.x, s_shq[k][0]), fixed_diff(qj.y, qi.y, s_shq[k][1]),
+                                fixed_diff(qj.z, qi.z, s_shq[k][2]), __int_as_float(j));
+      }
+      __syncwarp();
+    };
     int cnt[kMaxTypes] = {0, 0, 0, 0};  // the same in every lane
+    int qn = 0;                         // queue fill, the same in every lane
     for (int b = 0; b < T; b += 32) {
       const int q = b + lane;
       bool acc = false;
@@ -512,31 +558,44 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_verlet_cell(VerletArgs a) {
       if (q < T) {
         const float4 c4 = s_cx[q];
         j = s_cj[q];
-        k = s_ck[q];
-        if (!(j == i && s_code[k] == self_code)) {
+        const int wk = __float_as_int(c4.w);
+        k = wk >> 8;
+        if (!(j == i && k == kc)) {
           const float dx = c4.x - xfi.x, dy = c4.y - xfi.y, dz = c4.z - xfi.z;
           acc = dx * dx + dy * dy + dz * dz < a.rcs2_hi;
-          tj = __float_as_int(c4.w);
+          tj = wk & 0xff;
         }
       }
+      int off = -1;  // this lane's slot in the row (vcap_off + position), -1: none
 #pragma unroll
       for (int tt = 0; tt < kMaxTypes; ++tt) {
         if (tt >= a.ntypes) break;
         const unsigned mask = __ballot_sync(0xffffffffu, acc && tj == tt);
         if (acc && tj == tt) {
           const int pos = cnt[tt] + __popc(mask & lt);
-          if (pos < a.vcap[tt]) {
-            const qvec4 qj = a.xq[j];
-            const size_t e = ebase + a.vcap_off[tt] + pos;
-            a.vl_j[e] = j;
-            a.vl_img[e] = s_code[k];
-            a.vl_d0[e] = make_float4(fixed_diff(qj.x, qi.x, s_shq[k][0]), fixed_diff(qj.y, qi.y, s_shq[k][1]),
-                                     fixed_diff(qj.z, qi.z, s_shq[k][2]), 0.f);
-          }
+          if (pos < a.vcap[tt]) off = a.vcap_off[tt] + pos;
         }
         cnt[tt] += __popc(mask);
       }
+      const unsigned qm = __ballot_sync(0xffffffffu, off >= 0);
+      if (off >= 0) {
+        const int qs = qn + __popc(qm & lt);
+        s_qj[w][qs] = j;
+        s_qk[w][qs] = (unsigned char)k;
+        s_qe[w][qs] = off;
+      }
+      qn += __popc(qm);
+      if (qn >= 32) {
+        drain(32);
+        // move the rest (fewer than 32) to the front
+        int rj = 0, re = 0, rk = 0;
+        if (lane < qn - 32) { rj = s_qj[w][32 + lane]; re = s_qe[w][32 + lane]; rk = s_qk[w][32 + lane]; }
+        __syncwarp();
+        if (lane < qn - 32) { s_qj[w][lane] = rj; s_qe[w][lane] = re; s_qk[w][lane] = (unsigned char)rk; }
+        qn -= 32;
+      }
     }
+    drain(qn);
 #pragma unroll
     for (int tt = 0; tt < kMaxTypes; ++tt)
       if (lane == tt && tt < a.ntypes) {
@@ -572,12 +631,11 @@ struct FormatArgs {
   const RepGeom* geom;
   const dvec4* x;
   const float4* delta;
-  const int* vl_j;
+  const float4* vl_e;
   const int* vl_img;
-  const float4* vl_d0;
   const int* vcount;
   int* nl_j;
-  int* nl_img;
+  int* nl_img;                 // null: image codes not written (only the test hook reads them)
   void* nl_d;
   int* nl_count;
   int* err;
@@ -599,7 +657,7 @@ __device__ int keep_nearest(const FormatArgs& a, const RepGeom& g, const dvec4& 
     unsigned long long tie = 0;
     int j = 0, code = 0;
     if (q < n) {
-      j = a.vl_j[vb + q];
+      j = __float_as_int(a.vl_e[vb + q].w);
       code = a.vl_img[vb + q];
       int n0, n1, n2;
       unpack_img(code, n0, n1, n2);
@@ -614,7 +672,7 @@ __device__ int keep_nearest(const FormatArgs& a, const RepGeom& g, const dvec4& 
       double pr2 = 0.0, pd[3];
       unsigned long long ptie = 0;
       if (p < n) {
-        const int pj = a.vl_j[vb + p], pcode = a.vl_img[vb + p];
+        const int pj = __float_as_int(a.vl_e[vb + p].w), pcode = a.vl_img[vb + p];
         int m0, m1, m2;
         unpack_img(pcode, m0, m1, m2);
         pr2 = exact_r2(xi, a.x[pj], m0, m1, m2, g, pd);
@@ -633,11 +691,11 @@ __device__ int keep_nearest(const FormatArgs& a, const RepGeom& g, const dvec4& 
     const int pos = kept + __popc(mask & lt);
     if (keep) {
       a.nl_j[ob + pos] = j;
-      a.nl_img[ob + pos] = code;
+      if (a.nl_img) a.nl_img[ob + pos] = code;
       if (kFP64) {
         static_cast<dvec4*>(a.nl_d)[ob + pos] = make_dvec4(dd[0], dd[1], dd[2], 0.0);
       } else {
-        const float4 d0 = a.vl_d0[vb + q];
+        const float4 d0 = a.vl_e[vb + q];
         const float4 dj = a.delta[j];
         static_cast<float4*>(a.nl_d)[ob + pos] =
             make_float4(d0.x + (dj.x - di.x), d0.y + (dj.y - di.y), d0.z + (dj.z - di.z), 0.f);
@@ -664,47 +722,66 @@ __global__ void __launch_bounds__(128) k_format(FormatArgs a) {
     const size_t vb = (size_t)i * a.VS + a.vcap_off[t];
     const size_t ob = (size_t)i * a.S + a.sel_off[t];
     int cnt = 0;
-    for (int b = 0; b < n; b += 32) {
-      int q = b + lane;
-      bool in = false;
-      int j = 0, code = 0;
-      double dd[3];
-      float df[3];
-      if (q < n) {
-        j = a.vl_j[vb + q];
-        code = a.vl_img[vb + q];
-        if (kFP64) {
+    if (kFP64) {
+      for (int b = 0; b < n; b += 32) {
+        const int q = b + lane;
+        bool in = false;
+        int j = 0, code = 0;
+        double dd[3];
+        if (q < n) {
+          j = __float_as_int(a.vl_e[vb + q].w);
+          code = a.vl_img[vb + q];
           int n0, n1, n2;
           unpack_img(code, n0, n1, n2);
           in = exact_r2(xi, a.x[j], n0, n1, n2, g, dd) < a.rc2;
-        } else {
-          float4 d0 = a.vl_d0[vb + q];
-          float4 dj = a.delta[j];
-          df[0] = d0.x + (dj.x - di.x);
-          df[1] = d0.y + (dj.y - di.y);
-          df[2] = d0.z + (dj.z - di.z);
-          float r2f = df[0] * df[0] + df[1] * df[1] + df[2] * df[2];
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, in);
+        const int pos = cnt + __popc(mask & lt);
+        if (in && pos < a.sel[t]) {
+          a.nl_j[ob + pos] = j;
+          if (a.nl_img) a.nl_img[ob + pos] = code;
+          static_cast<dvec4*>(a.nl_d)[ob + pos] = make_dvec4(dd[0], dd[1], dd[2], 0.0);
+        }
+        cnt += __popc(mask);
+      }
+    } else {
+      // Two-stage pipeline over the 32-entry batches: the entries of batch b + 2 and the
+      // neighbours' displacements of batch b + 1 are in flight while batch b is filtered.
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 e0 = lane < n ? a.vl_e[vb + lane] : z4;
+      float4 e1 = lane + 32 < n ? a.vl_e[vb + 32 + lane] : z4;
+      float4 dj0 = lane < n ? a.delta[__float_as_int(e0.w)] : z4;
+      for (int b = 0; b < n; b += 32) {
+        const int q = b + lane;
+        const float4 dj1 = q + 32 < n ? a.delta[__float_as_int(e1.w)] : z4;
+        const float4 e2 = q + 64 < n ? a.vl_e[vb + q + 64] : z4;
+        bool in = false;
+        const int j = __float_as_int(e0.w);
+        const float dfx = e0.x + (dj0.x - di.x), dfy = e0.y + (dj0.y - di.y), dfz = e0.z + (dj0.z - di.z);
+        if (q < n) {
+          const float r2f = dfx * dfx + dfy * dfy + dfz * dfz;
           if (r2f < a.rc2_lo) {
             in = true;
           } else if (r2f < a.rc2_hi) {
+            // exact FP64 test near the cutoff: the only place the image code is read
             int n0, n1, n2;
-            unpack_img(code, n0, n1, n2);
-            in = exact_r2(xi, a.x[j], n0, n1, n2, g, dd) < a.rc2;
+            unpack_img(a.vl_img[vb + q], n0, n1, n2);
+            double dd[3];
+            in = exact_r2(a.x[i], a.x[j], n0, n1, n2, g, dd) < a.rc2;  // x_i re-read: fewer live registers
           }
         }
-      }
-      unsigned mask = __ballot_sync(0xffffffffu, in);
-      int pos = cnt + __popc(mask & lt);
-      if (in && pos < a.sel[t]) {
-        a.nl_j[ob + pos] = j;
-        a.nl_img[ob + pos] = code;
-        if (kFP64) {
-          static_cast<dvec4*>(a.nl_d)[ob + pos] = make_dvec4(dd[0], dd[1], dd[2], 0.0);
-        } else {
-          static_cast<float4*>(a.nl_d)[ob + pos] = make_float4(df[0], df[1], df[2], 0.f);
+        const unsigned mask = __ballot_sync(0xffffffffu, in);
+        const int pos = cnt + __popc(mask & lt);
+        if (in && pos < a.sel[t]) {
+          a.nl_j[ob + pos] = j;
+          if (a.nl_img) a.nl_img[ob + pos] = a.vl_img[vb + q];
+          static_cast<float4*>(a.nl_d)[ob + pos] = make_float4(dfx, dfy, dfz, 0.f);
         }
+        cnt += __popc(mask);
+        e0 = e1;
+        e1 = e2;
+        dj0 = dj1;
       }
-      cnt += __popc(mask);
     }
     if (cnt > a.sel[t]) {
       if (kNearest) {
@@ -814,7 +891,7 @@ dp_status launch_rebuild(Model* m, int N, bool with_skin) {
   a.rcs2_hi = (float)(a.rcs2 + band);
   a.itype = m->itype; a.irep = m->irep; a.geom = m->geom; a.x = m->x; a.xf = m->xf; a.xq = m->xq;
   a.cell_of = m->cell_of; a.cell_start = m->cell_start; a.cell_atoms = m->cell_atoms; a.cell_xf = m->cell_xf;
-  a.vl_j = m->vl_j; a.vl_img = m->vl_img; a.vl_d0 = m->vl_d0; a.vcount = m->vcount; a.err = m->err;
+  a.vl_e = m->vl_e; a.vl_img = m->vl_img; a.vcount = m->vcount; a.err = m->err;
   // cells by k_verlet_cell; the atoms of the cells it flags (cell_fill is free again after the
   // scatter and holds the flags) by k_verlet
   a.cell_flag = m->cell_fill;
@@ -834,7 +911,7 @@ dp_status launch_delta(Model* m, int N) {
   return DP_OK;
 }
 
-dp_status launch_format(Model* m, int N) {
+dp_status launch_format(Model* m, int N, bool images) {
   FormatArgs a;
   a.N = N; a.ntypes = m->ntypes; a.VS = m->VS; a.S = m->S;
   for (int t = 0; t <= m->ntypes; ++t) { a.vcap_off[t] = m->vcap_off[t]; a.sel_off[t] = m->sel_off[t]; }
@@ -846,8 +923,9 @@ dp_status launch_format(Model* m, int N) {
   a.rc2_lo = (float)(a.rc2 - band);
   a.rc2_hi = (float)(a.rc2 + band);
   a.irep = m->irep; a.perm = m->perm; a.geom = m->geom; a.x = m->x; a.delta = m->delta;
-  a.vl_j = m->vl_j; a.vl_img = m->vl_img; a.vl_d0 = m->vl_d0; a.vcount = m->vcount;
-  a.nl_j = m->nl_j; a.nl_img = m->nl_img; a.nl_d = m->nl_d; a.nl_count = m->nl_count; a.err = m->err;
+  a.vl_e = m->vl_e; a.vl_img = m->vl_img; a.vcount = m->vcount;
+  a.nl_j = m->nl_j; a.nl_img = images ? m->nl_img : nullptr; a.nl_d = m->nl_d; a.nl_count = m->nl_count;
+  a.err = m->err;
   const dim3 grid(cdiv(N, 4));
   if (m->prec == DP_FP64) {
     if (m->nearest) k_format<true, true><<<grid, 128, 0, m->stream>>>(a);
