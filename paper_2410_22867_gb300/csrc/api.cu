@@ -102,12 +102,18 @@ dp_status parse_blob(const unsigned char* p, size_t n, Parsed& o, std::string& w
 }
 
 // ------------------------------------------------------------------ replicas
-dp_status setup_replicas(Model* m, int nrep, const int* offs, const double* boxes, int N) {
+// with_skin: cells for the r_c + skin list of an MD run; otherwise for the r_c list of a single
+// evaluation (smaller cells, fewer candidates per atom).
+dp_status setup_replicas(Model* m, int nrep, const int* offs, const double* boxes, int N, bool with_skin) {
   if (nrep < 1 || nrep > m->max_reps) { m->last_error = "nrep out of range"; return DP_ERR_CAPACITY; }
-  // the pinned staging may still feed an earlier async copy
-  DP_CUDA_TRY(m, cudaStreamSynchronize(m->stream));
-  int* off_h = reinterpret_cast<int*>(m->geom_host + m->max_reps);
-  const double rcs = m->rc + m->skin;
+  // Two pinned staging buffers, written alternately: the one written now fed the copies of the
+  // call before last, and the event recorded after those copies has (almost always) completed,
+  // so consecutive calls do not wait for the device.  The current one is switched only on success.
+  const int sb = (m->geom_host == m->geom_stage[0]) ? 1 : 0;
+  DP_CUDA_TRY(m, cudaEventSynchronize(m->geom_ev[sb]));
+  RepGeom* gh = m->geom_stage[sb];
+  int* off_h = reinterpret_cast<int*>(gh + m->max_reps);
+  const double rcs = m->rc + (with_skin ? m->skin : 0.0);
   // Cells of edge >= (r_c + skin) / 2 and a 5 x 5 x 5 stencil when they fit the allocated cell
   // list (about half the candidates of edge >= r_c + skin with 3 x 3 x 3), else full-size cells.
   int cells = 0;
@@ -115,7 +121,7 @@ dp_status setup_replicas(Model* m, int nrep, const int* offs, const double* boxe
     cells = 0;
     for (int r = 0; r < nrep; ++r) {
       const double* b = boxes + 9 * r;
-      RepGeom& g = m->geom_host[r];
+      RepGeom& g = gh[r];
       std::memset(&g, 0, sizeof(g));
       // any right-handed cell: finite entries, positive volume; inverse = adjugate / det
       double cof[9];
@@ -178,9 +184,11 @@ dp_status setup_replicas(Model* m, int nrep, const int* offs, const double* boxe
   if (cells > m->max_cells) { m->last_error = "too many cells for the allocated cell list"; return DP_ERR_CAPACITY; }
   m->nrep = nrep;
   m->ncells = cells;
-  DP_CUDA_TRY(m, cudaMemcpyAsync(m->geom, m->geom_host, sizeof(RepGeom) * nrep, cudaMemcpyHostToDevice, m->stream));
+  DP_CUDA_TRY(m, cudaMemcpyAsync(m->geom, gh, sizeof(RepGeom) * nrep, cudaMemcpyHostToDevice, m->stream));
   DP_CUDA_TRY(m, cudaMemcpyAsync(m->rep_off_dev, off_h, sizeof(int) * (nrep + 1), cudaMemcpyHostToDevice,
                                  m->stream));
+  DP_CUDA_TRY(m, cudaEventRecord(m->geom_ev[sb], m->stream));
+  m->geom_host = gh;
   return DP_OK;
 }
 
@@ -360,7 +368,7 @@ dp_status run_md(Model* m, dp_md_state* st, double dt, int nsteps, int capture, 
   }
   if (!resume) {
     m->md_valid = false;
-    DP_TRY(setup_replicas(m, nrep, st->atom_offsets, st->boxes, N));
+    DP_TRY(setup_replicas(m, nrep, st->atom_offsets, st->boxes, N, true));
     m->natoms = N;
     // masses per type into the device small table (as doubles after the int area)
     double* mass_t_dev = reinterpret_cast<double*>(m->small_i + 32);
@@ -577,7 +585,13 @@ dp_status dp_create(dp_model** out, int ntypes, const char* const* type_map, dou
   A_(pg_w, 24 * N);
   A_(pg_scal, 64);
 #undef A_
-  if (halloc(m, &m->geom_host, sizeof(RepGeom) * R + sizeof(int) * (R + 1) + 64) != DP_OK) return fail(DP_ERR_OOM, m->last_error);
+  for (int b = 0; b < 2; ++b) {
+    if (halloc(m, &m->geom_stage[b], sizeof(RepGeom) * R + sizeof(int) * (R + 1) + 64) != DP_OK)
+      return fail(DP_ERR_OOM, m->last_error);
+    if (cudaEventCreateWithFlags(&m->geom_ev[b], cudaEventDisableTiming) != cudaSuccess)
+      return fail(DP_ERR_CUDA, "cannot create an event");
+  }
+  m->geom_host = m->geom_stage[0];
   if (halloc(m, &m->err_host, 64) != DP_OK) return fail(DP_ERR_OOM, m->last_error);
 
   {
@@ -603,7 +617,7 @@ dp_status dp_compute_batch(dp_model* h, int nrep, const int* atom_offsets, const
   const int N = atom_offsets[nrep];
   if (N < 1 || N > m->max_atoms) { m->last_error = "natoms out of range"; return DP_ERR_CAPACITY; }
   m->md_valid = false;
-  DP_TRY(setup_replicas(m, nrep, atom_offsets, boxes, N));
+  DP_TRY(setup_replicas(m, nrep, atom_offsets, boxes, N, false));
   m->natoms = N;
   DP_TRY(launch_type_sort(m, types, N));
   DP_TRY(launch_load_positions(m, coords, N));
@@ -802,6 +816,8 @@ void dp_destroy(dp_model* h) {
   cudaStreamSynchronize(m->stream);
   drop_graphs(m);
   if (m->capture_stream) cudaStreamDestroy(m->capture_stream);
+  for (auto& e : m->geom_ev)
+    if (e) cudaEventDestroy(e);
   for (void* p : m->dev_allocs) cudaFree(p);
   for (void* p : m->host_allocs) cudaFreeHost(p);
   m->dev_allocs.clear();
@@ -828,7 +844,7 @@ extern "C" dp_status dp_param_grad(dp_model* h, int natoms, const double* coords
   }
   const int offs[2] = {0, natoms};
   m->md_valid = false;
-  DP_TRY(setup_replicas(m, 1, offs, box, natoms));
+  DP_TRY(setup_replicas(m, 1, offs, box, natoms, false));
   m->natoms = natoms;
   DP_TRY(launch_type_sort(m, types, natoms));
   DP_TRY(launch_load_positions(m, coords, natoms));

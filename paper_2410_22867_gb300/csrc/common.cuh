@@ -132,7 +132,9 @@ struct Model {
 
   // replicas
   RepGeom* geom = nullptr;    // device [max_reps]
-  RepGeom* geom_host = nullptr;  // pinned host staging
+  RepGeom* geom_host = nullptr;  // the current geometry: one of the two staging buffers below
+  RepGeom* geom_stage[2] = {nullptr, nullptr};  // pinned host staging, written alternately
+  cudaEvent_t geom_ev[2] = {nullptr, nullptr};  // recorded after the copies out of each buffer
   int nrep = 0;
   int ncells = 0;
 

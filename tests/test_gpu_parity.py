@@ -59,9 +59,10 @@ def test_nlist_bit_exact(dp, prec, case):
 
 @pytest.mark.parametrize("prec", ["fp64", "mix_fp16"])
 def test_nlist_bit_exact_sparse_box(dp, prec):
-    # A 108-atom copper cluster in a 70 A box, straddling the periodic corner.  Half-size cells
-    # would need 14^3 = 2744 cells, more than the cell list holds for 108 atoms (1196), so the
-    # library falls back to cells of edge >= r_c + skin (7^3).
+    # A 108-atom copper cluster in a 70 A box, straddling the periodic corner.  A single
+    # evaluation sizes its cells by r_c: half-size cells would need 17^3 = 4913 cells, more than
+    # the cell list holds for 108 atoms (1196), so the library falls back to cells of edge >= r_c
+    # (8^3).
     c = synth.copper_fcc(3, 5)
     L = 70.0
     coords = np.mod(c.coords - 4.0, L)
@@ -91,11 +92,11 @@ def _stencil_candidates(coords, L, nc, m):
 
 @pytest.mark.parametrize("prec", ["fp64", "mix_fp16"])
 def test_nlist_bit_exact_dense_cluster(dp, prec):
-    # A compressed 4,000-atom FCC cluster (a = 2.4 A) in a 42 A box, r_c 6 + skin 2: the cells
-    # (10^3, edge 4.2 A, 5^3 stencil) inside the cluster see more candidates than one CTA of the
-    # cell-staged Verlet build holds, the cells at its surface fewer, so both Verlet kernels
-    # write parts of the same list.  Checked for the r_c list of a single evaluation and for the
-    # r_c + skin list an MD run starts from.
+    # A compressed 4,000-atom FCC cluster (a = 2.4 A) in a 42 A box, r_c 6 + skin 2.  The r_c + skin
+    # list an MD run starts from uses 10^3 cells (edge 4.2 A, 5^3 stencil): those inside the
+    # cluster see more candidates than one CTA of the cell-staged Verlet build holds, those at its
+    # surface fewer, so both Verlet kernels write parts of that list.  The r_c list of a single
+    # evaluation (cells of edge >= r_c / 2) is checked as well.
     c = synth.copper_fcc(10, 7, a=2.4, sigma=0.05)
     L = 42.0
     s = synth.System(c.coords + 9.0, c.types, np.array([L, 0, 0, 0, L, 0, 0, 0, L], dtype=np.float64), c.type_names)
