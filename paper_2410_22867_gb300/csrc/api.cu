@@ -184,6 +184,8 @@ dp_status setup_replicas(Model* m, int nrep, const int* offs, const double* boxe
   if (cells > m->max_cells) { m->last_error = "too many cells for the allocated cell list"; return DP_ERR_CAPACITY; }
   m->nrep = nrep;
   m->ncells = cells;
+  m->max_rep_atoms = 0;
+  for (int r = 0; r < nrep; ++r) m->max_rep_atoms = std::max(m->max_rep_atoms, off_h[r + 1] - off_h[r]);
   DP_CUDA_TRY(m, cudaMemcpyAsync(m->geom, gh, sizeof(RepGeom) * nrep, cudaMemcpyHostToDevice, m->stream));
   DP_CUDA_TRY(m, cudaMemcpyAsync(m->rep_off_dev, off_h, sizeof(int) * (nrep + 1), cudaMemcpyHostToDevice,
                                  m->stream));
@@ -557,7 +559,7 @@ dp_status dp_create(dp_model** out, int ntypes, const char* const* type_map, dou
   A_(cell_of, 4 * N);
   A_(cell_count, 4 * (size_t)m->max_cells); A_(cell_start, 4 * ((size_t)m->max_cells + 1));
   A_(cell_fill, 4 * (size_t)m->max_cells); A_(cell_atoms, 4 * N); A_(cell_xf, 16 * N);
-  A_(vl_e, 16 * N * m->VS); A_(vl_img, 4 * N * m->VS); A_(vcount, 4 * N * nt);
+  A_(vl_e, 16 * N * m->VS); A_(vl_img, 4 * N * m->VS); A_(vl_work, 4 * (N + 1)); A_(vcount, 4 * N * nt);
   A_(nl_j, 4 * N * m->S); A_(nl_img, 4 * N * m->S);
   A_(nl_d, (prec == DP_FP64 ? 32 : 16) * N * m->S);
   A_(nl_count, 4 * N * nt);
@@ -584,6 +586,8 @@ dp_status dp_create(dp_model** out, int ntypes, const char* const* type_map, dou
   A_(pg_roff, 4 * m->pg_roff_cap);
   A_(pg_w, 24 * N);
   A_(pg_scal, 64);
+  m->red_cap = rep_reduce_slots(max_atoms, max_replicas);
+  A_(red_part, 80 * m->red_cap);
 #undef A_
   for (int b = 0; b < 2; ++b) {
     if (halloc(m, &m->geom_stage[b], sizeof(RepGeom) * R + sizeof(int) * (R + 1) + 64) != DP_OK)

@@ -136,7 +136,10 @@ struct Model {
   RepGeom* geom_stage[2] = {nullptr, nullptr};  // pinned host staging, written alternately
   cudaEvent_t geom_ev[2] = {nullptr, nullptr};  // recorded after the copies out of each buffer
   int nrep = 0;
+  int max_rep_atoms = 0;      // atoms of the largest replica (chunks of the per-replica sums)
   int ncells = 0;
+  double* red_part = nullptr;  // per-replica sums: chunk partials [nrep][nchunk][10]
+  size_t red_cap = 0;          // chunk slots of red_part
 
   // cell list
   int* cell_of = nullptr;
@@ -149,6 +152,7 @@ struct Model {
   // Verlet list (r_c + skin)
   float4* vl_e = nullptr;     // [N*VS] pair vector at rebuild (fp32), w = neighbour index
   int* vl_img = nullptr;      // [N*VS] image code
+  int* vl_work = nullptr;     // [N + 1] atoms the per-atom Verlet kernel builds, their count last
   int* vcount = nullptr;      // [N*nt]
 
   // formatted list (r_c), compacted per type segment
@@ -340,6 +344,7 @@ dp_status launch_kick(Model* m, int N, double dt);
 dp_status launch_load_state(Model* m, int N, const double* v_user, const double* mass_by_type);
 dp_status launch_store_state(Model* m, int N, double* x_user, double* v_user);
 dp_status launch_kinetic(Model* m, int N, double* ke_rep);
+size_t rep_reduce_slots(int max_atoms, int max_reps);  // chunk slots of red_part (10 doubles each)
 dp_status launch_nan_energy(Model* m, double* energy, int n);
 
 }  // namespace dpg

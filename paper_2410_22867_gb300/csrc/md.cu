@@ -24,20 +24,24 @@ __global__ void k_unpermute(int N, const int* __restrict__ perm, const double* _
   }
 }
 
-// One block per replica: fixed-order tree sums (deterministic: every thread sums a fixed
-// strided subset, four independent loads per pass, then a fixed tree).
 // Per-replica energy and virial: sums of the per-atom values (caller order), or for the
-// virial the per-replica accumulator vir_rep when the backward produced one.
-constexpr int kRedThreads = 512;
-__global__ void __launch_bounds__(kRedThreads) k_rep_reduce(int nrep, const int* __restrict__ rep_off,
+// virial the per-replica accumulator vir_rep when the backward produced one.  Deterministic:
+// block (c, r) sums chunk c (kRedChunk atoms) of replica r over a fixed strided partition (four
+// independent loads per pass) and a fixed tree; with one chunk per replica it writes the result,
+// otherwise its partial, which k_rep_final adds in chunk order.
+constexpr int kRedThreads = 256;
+constexpr int kRedChunk = 8192;
+__global__ void __launch_bounds__(kRedThreads) k_rep_reduce(int nrep, int nchunk, const int* __restrict__ rep_off,
                                                            const double* __restrict__ e_user,
                                                            const double* __restrict__ vir_user,
                                                            const double* __restrict__ vir_rep, double* energy,
-                                                           double* virial, const int* __restrict__ err) {
+                                                           double* virial, double* part_out,
+                                                           const int* __restrict__ err) {
   __shared__ double part[10][kRedThreads];
-  int r = blockIdx.x;
+  const int r = blockIdx.y, c = blockIdx.x;
   if (r >= nrep) return;
-  int beg = rep_off[r], end = rep_off[r + 1];
+  const int rb = rep_off[r], re = rep_off[r + 1];
+  const int beg = min(re, rb + c * kRedChunk), end = min(re, beg + kRedChunk);
   double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (int u0 = beg + threadIdx.x; u0 < end; u0 += 4 * kRedThreads) {
     double e[4];
@@ -59,16 +63,35 @@ __global__ void __launch_bounds__(kRedThreads) k_rep_reduce(int nrep, const int*
   }
   for (int q = 0; q < 10; ++q) part[q][threadIdx.x] = acc[q];
   __syncthreads();
-  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s)
-      for (int q = 0; q < 10; ++q) part[q][threadIdx.x] += part[q][threadIdx.x + s];
+  for (int st = kRedThreads / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+      for (int q = 0; q < 10; ++q) part[q][threadIdx.x] += part[q][threadIdx.x + st];
     __syncthreads();
+  }
+  if (nchunk > 1) {
+    if (threadIdx.x < 10) part_out[((size_t)r * nchunk + c) * 10 + threadIdx.x] = part[threadIdx.x][0];
+    return;
   }
   if (threadIdx.x == 0) {
     bool bad = err && *err != 0;
     if (energy) energy[r] = bad ? __longlong_as_double(0x7ff8000000000000ll) : part[0][0];
     if (virial)
       for (int q = 0; q < 9; ++q) virial[r * 9 + q] = vir_rep ? vir_rep[r * 9 + q] : part[1 + q][0];
+  }
+}
+
+// The chunk partials of each replica added in chunk order (lane q: quantity q).
+__global__ void k_rep_final(int nrep, int nchunk, const double* __restrict__ part, const double* __restrict__ vir_rep,
+                            double* energy, double* virial, const int* __restrict__ err) {
+  const int r = blockIdx.x, q = threadIdx.x;
+  if (r >= nrep || q >= 10) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += part[((size_t)r * nchunk + c) * 10 + q];
+  if (q == 0) {
+    bool bad = err && *err != 0;
+    if (energy) energy[r] = bad ? __longlong_as_double(0x7ff8000000000000ll) : s;
+  } else if (virial) {
+    virial[r * 9 + q - 1] = vir_rep ? vir_rep[r * 9 + q - 1] : s;
   }
 }
 
@@ -128,15 +151,42 @@ __global__ void k_nan(double* p, int n) {
 
 }  // namespace
 
+// Chunk slots of the reduction workspace: every replica may need ceil(max_atoms / kRedChunk).
+size_t rep_reduce_slots(int max_atoms, int max_reps) {
+  return (size_t)max_reps * ((size_t)max_atoms / kRedChunk + 1);
+}
+
+namespace {
+
+// Per-replica sums of per-atom values (energy, and the per-atom virial unless vir_rep holds it).
+dp_status launch_rep_reduce(Model* m, const double* e_user, const double* vir_user, const double* vir_rep,
+                            double* energy, double* virial, const int* err) {
+  const int nchunk = std::max(1, (m->max_rep_atoms + kRedChunk - 1) / kRedChunk);
+  if (nchunk > 1 && (size_t)m->nrep * nchunk > m->red_cap) {
+    m->last_error = "reduction workspace too small";
+    return DP_ERR_CAPACITY;
+  }
+  k_rep_reduce<<<dim3(nchunk, m->nrep), kRedThreads, 0, m->stream>>>(m->nrep, nchunk, m->rep_off_dev, e_user, vir_user,
+                                                                     vir_rep, energy, virial, m->red_part, err);
+  m->launches += 1;
+  if (nchunk > 1) {
+    k_rep_final<<<m->nrep, 32, 0, m->stream>>>(m->nrep, nchunk, m->red_part, vir_rep, energy, virial, err);
+    m->launches += 1;
+  }
+  return DP_OK;
+}
+
+}  // namespace
+
 dp_status launch_outputs(Model* m, int N, double* energy_rep, double* atom_energy, double* forces,
                          double* virial_rep) {
   k_unpermute<<<cdiv(N, 256), 256, 0, m->stream>>>(N, m->perm, m->e_atom, m->vir_atom, m->force, m->e_user,
                                                    m->vir_user, forces);
   const bool mixed = is_mixed(m);
-  k_rep_reduce<<<m->nrep, kRedThreads, 0, m->stream>>>(m->nrep, m->rep_off_dev, m->e_user,
-                                                        mixed ? nullptr : m->vir_user, mixed ? m->vir_rep : nullptr,
-                                                        energy_rep, virial_rep, m->err);
-  m->launches += 2;
+  const dp_status rs = launch_rep_reduce(m, m->e_user, mixed ? nullptr : m->vir_user, mixed ? m->vir_rep : nullptr,
+                                         energy_rep, virial_rep, m->err);
+  if (rs != DP_OK) return rs;
+  m->launches += 1;
   if (atom_energy)
     DP_CUDA_TRY(m, cudaMemcpyAsync(atom_energy, m->e_user, sizeof(double) * N, cudaMemcpyDeviceToDevice,
                                    m->stream));
@@ -180,9 +230,9 @@ dp_status launch_store_state(Model* m, int N, double* x_user, double* v_user) {
 
 dp_status launch_kinetic(Model* m, int N, double* ke_rep) {
   k_kinetic_atoms<<<cdiv(N, 256), 256, 0, m->stream>>>(N, m->perm, m->v, m->mass, m->ke_user);
-  k_rep_reduce<<<m->nrep, kRedThreads, 0, m->stream>>>(m->nrep, m->rep_off_dev, m->ke_user, nullptr, nullptr,
-                                                        ke_rep, nullptr, nullptr);
-  m->launches += 2;
+  const dp_status rs = launch_rep_reduce(m, m->ke_user, nullptr, nullptr, ke_rep, nullptr, nullptr);
+  if (rs != DP_OK) return rs;
+  m->launches += 1;
   DP_LAUNCH_CHECK(m);
   return DP_OK;
 }

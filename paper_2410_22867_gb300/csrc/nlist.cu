@@ -190,27 +190,51 @@ __global__ void k_wrap_bin(int N, const int* __restrict__ irep, const int* __res
   atomicAdd(&cell_count[cid], 1);
 }
 
-__global__ void k_scan_cells(int ncells, const int* __restrict__ cell_count, int* cell_start) {
-  __shared__ int part[1024];
+// Exclusive scan of the cell counts by one CTA: four consecutive cells per thread, 4096 per
+// pass, warp-shuffle scans of the thread sums.
+__global__ void __launch_bounds__(1024) k_scan_cells(int ncells, const int* __restrict__ cell_count,
+                                                    int* cell_start) {
+  __shared__ int ws[32];
   __shared__ int carry;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  for (int base = 0; base < ncells; base += 1024) {
-    int i = base + threadIdx.x;
-    int v = (i < ncells) ? cell_count[i] : 0;
-    part[threadIdx.x] = v;
-    __syncthreads();
-    for (int s = 1; s < 1024; s <<= 1) {
-      int add = (threadIdx.x >= s) ? part[threadIdx.x - s] : 0;
-      __syncthreads();
-      part[threadIdx.x] += add;
-      __syncthreads();
+  for (int base = 0; base < ncells; base += 4096) {
+    const int i0 = base + 4 * threadIdx.x;
+    int v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = i0 + k < ncells ? cell_count[i0 + k] : 0;
+    const int sum = (v[0] + v[1]) + (v[2] + v[3]);
+    int x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
-    if (i < ncells) cell_start[i] = carry + part[threadIdx.x] - v;
+    if (lane == 31) ws[w] = x;
     __syncthreads();
-    if (threadIdx.x == 1023) carry += part[1023];
+    if (w == 0) {
+      int t = ws[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      ws[lane] = t;
+    }
     __syncthreads();
+    const int c0 = carry;
+    int e = c0 + (w > 0 ? ws[w - 1] : 0) + x - sum;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (i0 + k < ncells) cell_start[i0 + k] = e;
+      e += v[k];
+    }
+    const int total = ws[31];
+    __syncthreads();  // carry and ws are read before they change
+    if (threadIdx.x == 0) carry = c0 + total;
   }
+  __syncthreads();
   if (threadIdx.x == 0) cell_start[ncells] = carry;
 }
 
@@ -245,7 +269,8 @@ struct VerletArgs {
   float4* vl_e;                // entry: pair vector at rebuild (fp32), w = neighbour index (bits)
   int* vl_img;                 // entry: image code (read by the format near the cutoff only)
   int* vcount;
-  int* cell_flag;              // per cell: 1 = its atoms are left to k_verlet (null: all atoms)
+  int* work;                   // atoms left to k_verlet by k_verlet_cell (null: all atoms)
+  int* work_n;                 // their number
   int* err;
 };
 
@@ -280,9 +305,10 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
   __shared__ int s_beg[kVerletWarps][32], s_off[kVerletWarps][32], s_img[kVerletWarps][32];
   __shared__ float s_sh[kVerletWarps][32][3];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int i = blockIdx.x * kVerletWarps + w;
-  if (i >= a.N) return;
-  if (a.cell_flag && a.cell_flag[a.cell_of[i]] == 0) return;  // done by k_verlet_cell
+  const int nwork = a.work ? *a.work_n : a.N;
+  for (int wi = blockIdx.x * kVerletWarps + w; wi < nwork; wi += gridDim.x * kVerletWarps) {
+  const int i = a.work ? a.work[wi] : wi;
+  __syncwarp();
   if (lane < kMaxTypes) cnt[w][lane] = 0;
   __syncwarp();
   const RepGeom& g = a.geom[a.irep[i]];
@@ -402,6 +428,7 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
     }
     a.vcount[(size_t)i * a.ntypes + lane] = nt_;
   }
+  }  // atoms of the work list
 }
 
 // Verlet list by cell: one CTA per cell stages the candidates of the cell's whole stencil in
@@ -425,21 +452,24 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_verlet_cell(VerletArgs a) {
   __shared__ int s_beg[kMaxStencil], s_off[kMaxStencil + 1], s_code[kMaxStencil];
   __shared__ float s_sh[kMaxStencil][3];
   __shared__ long long s_shq[kMaxStencil][3];
-  __shared__ int s_wsum[kCellWarps], s_total;
+  __shared__ int s_wsum[kCellWarps], s_total, s_wbase;
   __shared__ int s_qj[kCellWarps][kQueue], s_qe[kCellWarps][kQueue];  // queue: atom, slot in the row
   __shared__ unsigned char s_qk[kCellWarps][kQueue];                  // queue: stencil slot
   const int cid = blockIdx.x;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int cb = a.cell_start[cid], ce = a.cell_start[cid + 1];
-  if (cb == ce) {
-    if (t == 0) a.cell_flag[cid] = 0;
-    return;
-  }
+  if (cb == ce) return;
+  // the cell's atoms go to k_verlet's work list (a decision the whole CTA takes together)
+  auto hand_over = [&]() {
+    if (t == 0) s_wbase = atomicAdd(a.work_n, ce - cb);
+    __syncthreads();
+    for (int q = t; q < ce - cb; q += 32 * kCellWarps) a.work[s_wbase + q] = a.cell_atoms[cb + q];
+  };
   const RepGeom& g = a.geom[a.irep[a.cell_atoms[cb]]];
   const int sy = 2 * g.m[1] + 1, sz = 2 * g.m[2] + 1;
   const int ncell = (2 * g.m[0] + 1) * sy * sz;
   if (ncell > kMaxStencil) {
-    if (t == 0) a.cell_flag[cid] = 1;
+    hand_over();
     return;
   }
   // the slot of offset (0, 0, 0): the only one with image (0, 0, 0) and this very cell, so a
@@ -484,13 +514,10 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_verlet_cell(VerletArgs a) {
   __syncthreads();
   const int T = s_total;
   if (T > kCellCap) {
-    if (t == 0) a.cell_flag[cid] = 1;
+    hand_over();
     return;
   }
-  if (t == 0) {
-    a.cell_flag[cid] = 0;
-    s_off[ncell] = T;
-  }
+  if (t == 0) s_off[ncell] = T;
   // staging: four candidates per thread per pass, their loads issued together
   constexpr int kSt = 4;
   for (int q0 = t; q0 < T; q0 += kSt * 32 * kCellWarps) {
@@ -551,13 +578,20 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_verlet_cell(VerletArgs a) {
     };
     int cnt[kMaxTypes] = {0, 0, 0, 0};  // the same in every lane
     int qn = 0;                         // queue fill, the same in every lane
+    // the next batch's candidate is read from shared memory one pass ahead
+    float4 c4n = lane < T ? s_cx[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    int jn = lane < T ? s_cj[lane] : -1;
     for (int b = 0; b < T; b += 32) {
       const int q = b + lane;
+      const float4 c4 = c4n;
+      const int j = jn;
+      if (q + 32 < T) {
+        c4n = s_cx[q + 32];
+        jn = s_cj[q + 32];
+      }
       bool acc = false;
-      int j = -1, tj = 0, k = 0;
+      int tj = 0, k = 0;
       if (q < T) {
-        const float4 c4 = s_cx[q];
-        j = s_cj[q];
         const int wk = __float_as_int(c4.w);
         k = wk >> 8;
         if (!(j == i && k == kc)) {
@@ -892,12 +926,14 @@ dp_status launch_rebuild(Model* m, int N, bool with_skin) {
   a.itype = m->itype; a.irep = m->irep; a.geom = m->geom; a.x = m->x; a.xf = m->xf; a.xq = m->xq;
   a.cell_of = m->cell_of; a.cell_start = m->cell_start; a.cell_atoms = m->cell_atoms; a.cell_xf = m->cell_xf;
   a.vl_e = m->vl_e; a.vl_img = m->vl_img; a.vcount = m->vcount; a.err = m->err;
-  // cells by k_verlet_cell; the atoms of the cells it flags (cell_fill is free again after the
-  // scatter and holds the flags) by k_verlet
-  a.cell_flag = m->cell_fill;
+  // cells by k_verlet_cell; the atoms of the cells it hands over by k_verlet, whose grid-stride
+  // loop over the work list costs little when the list is empty
+  a.work = m->vl_work;
+  a.work_n = m->vl_work + m->max_atoms;
+  DP_CUDA_TRY(m, cudaMemsetAsync(a.work_n, 0, sizeof(int), s));
   DP_CUDA_TRY(m, ensure_smem(reinterpret_cast<const void*>(k_verlet_cell), kCellSmem));
   k_verlet_cell<<<m->ncells, 32 * kCellWarps, kCellSmem, s>>>(a);
-  k_verlet<<<cdiv(N, kVerletWarps), 32 * kVerletWarps, 0, s>>>(a);
+  k_verlet<<<std::min(cdiv(N, kVerletWarps), 8 * num_sms()), 32 * kVerletWarps, 0, s>>>(a);
   m->launches += 5;
   DP_LAUNCH_CHECK(m);
   return DP_OK;

@@ -151,6 +151,21 @@ def test_fp64_matches_oracle(dp, n_mol, seed):
     np.testing.assert_allclose(out["virial"].cpu().numpy(), ref["virial"], rtol=1e-9, atol=1e-12 * Fs)
 
 
+def test_fp64_energy_over_reduction_chunks(dp):
+    # 12,288 atoms: the per-replica sums of energy and virial run over two chunks of 8,192
+    # atoms and a second pass that adds the chunk partials
+    s = synth.water_box(4096, 5)
+    w = synth.water_weights()
+    ref = oracle.Model(w.to_blob()).compute(s.coords, s.types, s.box)
+    m = dp.DPModel(w, "fp64", max_atoms=s.natoms)
+    x, t = _cuda(s)
+    out = m.compute(x, t, s.box)
+    assert out["energy"].item() == pytest.approx(ref["energy"], rel=1e-11)
+    assert out["energy"].item() == pytest.approx(out["atom_energy"].sum().item(), rel=1e-13)
+    Fs = np.abs(ref["forces"]).max()
+    np.testing.assert_allclose(out["virial"].cpu().numpy(), ref["virial"], rtol=1e-9, atol=1e-12 * Fs)
+
+
 def test_fp64_copper_small(dp):
     s = synth.copper_fcc(4, 2)
     w = synth.copper_weights()
