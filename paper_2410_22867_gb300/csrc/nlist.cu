@@ -779,16 +779,17 @@ __global__ void __launch_bounds__(128) k_format(FormatArgs a) {
         cnt += __popc(mask);
       }
     } else {
-      // Two-stage pipeline over the 32-entry batches: the entries of batch b + 2 and the
+      // Pipeline over the 32-entry batches: the entries of batches b + 1 .. b + 3 and the
       // neighbours' displacements of batch b + 1 are in flight while batch b is filtered.
       const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
       float4 e0 = lane < n ? a.vl_e[vb + lane] : z4;
       float4 e1 = lane + 32 < n ? a.vl_e[vb + 32 + lane] : z4;
+      float4 e2 = lane + 64 < n ? a.vl_e[vb + 64 + lane] : z4;
       float4 dj0 = lane < n ? a.delta[__float_as_int(e0.w)] : z4;
       for (int b = 0; b < n; b += 32) {
         const int q = b + lane;
         const float4 dj1 = q + 32 < n ? a.delta[__float_as_int(e1.w)] : z4;
-        const float4 e2 = q + 64 < n ? a.vl_e[vb + q + 64] : z4;
+        const float4 e3 = q + 96 < n ? a.vl_e[vb + q + 96] : z4;
         bool in = false;
         const int j = __float_as_int(e0.w);
         const float dfx = e0.x + (dj0.x - di.x), dfy = e0.y + (dj0.y - di.y), dfz = e0.z + (dj0.z - di.z);
@@ -814,6 +815,7 @@ __global__ void __launch_bounds__(128) k_format(FormatArgs a) {
         cnt += __popc(mask);
         e0 = e1;
         e1 = e2;
+        e2 = e3;
         dj0 = dj1;
       }
     }
