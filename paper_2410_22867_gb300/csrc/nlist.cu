@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet(VerletArgs a) {
 // the exact pair vectors (an L2 gather of the fixed-point position and integer arithmetic) are
 // formed 32 at a time from the queue, with every lane busy, instead of in the test loop where a
 // quarter of the lanes or fewer accept.  Cells whose stencil has more than kMaxStencil cells or
-// more than kCellCap candidates (small or sparse boxes) are flagged and left to k_verlet.
+// more than kCellCap candidates (small, sparse or triclinic boxes) hand their atoms to k_verlet.
 constexpr int kCellWarps = 8;
 constexpr int kCellCap = 2048;
 constexpr int kMaxStencil = 125;
