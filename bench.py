@@ -260,12 +260,25 @@ def kernel_times(ph):
             "fitting": ph[2], "dE_dT": max(0.0, ph[3] - ph[6]), "embedding_backward": ph[6]}
 
 
-def roofline(prec, kernel, ms, N, n_neigh, alu):
+def hbm_bytes_per_atom(kernel, ntypes):
+    """Algorithmic HBM bytes per atom of the mixed-precision dE/dT and descriptor kernels:
+    dE/dT reads dE/dD (1600 x fp16) and T (400 x FP32) and writes dE/dT (400 x FP32); the
+    descriptor reads the partial T of each neighbour type (400 x FP32 each) and writes T
+    (400 x FP32) and D (1600 x 16 bit)."""
+    if kernel == "dE_dT":
+        return 2 * 1600 + 4 * 400 + 4 * 400
+    if kernel == "descriptor":
+        return 4 * 400 * ntypes + 4 * 400 + 2 * 1600
+    return None
+
+
+def roofline(prec, kernel, ms, N, n_neigh, alu, ntypes=1):
     """Roofline entry of one kernel of a force evaluation.  alu: measured_peaks().
     Mixed precisions: embedding kernels against max(tensor, SFU) with the SFU rate measured
     by dp_measure_peak('tanh'); fitting against the burst bf16 tensor peak (the kernel is timed
-    in millisecond phases, not a sustained loop).  FP32 / FP64: FMA-pipe work of the dense
-    contractions against the measured FFMA / DFMA rate."""
+    in millisecond phases, not a sustained loop); dE/dT and descriptor against the measured
+    HBM copy rate.  FP32 / FP64: FMA-pipe work of the dense contractions against the measured
+    FFMA / DFMA rate."""
     pk, src = peaks()
     t = ms * 1e-3
     mixed = prec.startswith("mix")
@@ -292,8 +305,13 @@ def roofline(prec, kernel, ms, N, n_neigh, alu):
                     "frac": flop / t / 1e12 / tens, "peak_source": f"{src} bf16 burst (fp16 runs at the bf16 rate)"})
         return out
     if kernel in ("format", "dE_dT", "descriptor"):
-        out.update({"bound": "hbm", "achieved": None, "peak": pk.get("hbm_gbs"), "unit": "GB/s", "frac": None,
-                    "peak_source": f"{src} hbm copy"})
+        bpa = hbm_bytes_per_atom(kernel, ntypes) if mixed else None
+        ach = bpa * N / t / 1e9 if (bpa and t > 0) else None
+        hbm = pk.get("hbm_gbs")
+        out.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": (ach / hbm) if (ach and hbm) else None, "peak_source": f"{src} hbm copy"})
+        if bpa:
+            out["bytes_per_atom"] = bpa
         return out
     key = "dfma" if prec == "fp64" else "ffma"
     peak = (alu.get(key) or 0.0) / 1e12
@@ -354,8 +372,8 @@ def run_mine(args, world, rank, local):
         alu = measured_peaks(dp)
         kern = kernel_times(phases)
         dominant = max(kern, key=kern.get)
-        extra["roofline"] = roofline(prec, dominant, kern[dominant], N, n_neigh, alu)
-        extra["rooflines"] = {k: roofline(prec, k, v, N, n_neigh, alu) for k, v in kern.items()}
+        extra["roofline"] = roofline(prec, dominant, kern[dominant], N, n_neigh, alu, w.ntypes)
+        extra["rooflines"] = {k: roofline(prec, k, v, N, n_neigh, alu, w.ntypes) for k, v in kern.items()}
         extra["kernels_ms"] = {k: round(v, 4) for k, v in kern.items()}
         extra["measured_peaks"] = {"values": alu, "units": {"tanh": "1/s", "ex2": "1/s", "rcp": "1/s",
                                                             "ffma": "FLOP/s", "dfma": "FLOP/s"},
@@ -484,7 +502,7 @@ def ladder(args, stream, alu):
                 r = m.compute(x, t, s.box)
             e = {"value": s.natoms / (ms * 1e-3), "unit": "atom-steps/s", "ms_per_step": ms, "steps": steps,
                  "ns_per_day_0.5fs": (1e3 / ms) * 0.5 * 86400 * 1e-6,
-                 "roofline": roofline(prec, dom, kern[dom], s.natoms, n_neigh, alu),
+                 "roofline": roofline(prec, dom, kern[dom], s.natoms, n_neigh, alu, w.ntypes),
                  "kernels_ms": {k: round(v, 4) for k, v in kern.items()}}
             if prec == "fp64":
                 ref = {k: v.clone() for k, v in r.items()}
