@@ -83,7 +83,7 @@ typedef enum {
  *                sel, type names, then FP64 parameters in the documented order).
  *   prec         arithmetic policy (dp_precision).
  *   max_atoms    capacity in atoms summed over replicas; max_replicas capacity in boxes.
- *   skin         Verlet-list skin (A); the list holds pairs within rcut + skin.
+ *   skin         Verlet-list skin (A); the list of an MD run holds pairs within rcut + skin.
  *   cuda_stream  cudaStream_t to run on (NULL = default stream).
  * Weights are copied to device memory owned by the model.
  */
@@ -98,8 +98,10 @@ dp_status dp_create(dp_model** out, int ntypes, const char* const* type_map, dou
  *   box [9] host.  Outputs (device FP64): energy [1], atom_energy [natoms]
  *   (nullable), forces [natoms*3], virial [9] (nullable).
  * Positions are wrapped into the box and the neighbour list is rebuilt on every
- * call.  On a device-side error the outputs are undefined and energy is NaN;
- * dp_sync returns the error.
+ * call, within rcut only (no skin: nothing reuses it).  The call invalidates the
+ * MD state held by the model (a later dp_verlet_step with resume set is refused).
+ * On a device-side error the outputs are undefined and energy is NaN; dp_sync
+ * returns the error.
  */
 dp_status dp_compute(dp_model* m, int natoms, const double* coords, const int* types,
                      const double* box, double* energy, double* atom_energy, double* forces,
