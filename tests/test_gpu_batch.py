@@ -166,3 +166,31 @@ def test_autotune_choices_and_results(dp, water_weights):
     m2.md_run_batch(st, 0.5, 2)
     assert all(g > 0 for g in m2.autotune(0))
     m2.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mix_fp16"])
+def test_batch_sums_over_uneven_chunks(dp, water_weights, prec):
+    # Replicas of 64, 4096 and 37 molecules: the per-replica energy and virial sums run in
+    # chunks of 8,192 atoms, two for the large box and empty trailing chunks for the small
+    # ones, before the second pass adds each replica's chunks in order.
+    reps = [synth.water_box(64, 1), synth.water_box(4096, 2), synth.water_box(37, 3)]
+    coords, types, offs, boxes = synth.concat(reps)
+    m = dp.DPModel(water_weights, prec, max_atoms=len(types), max_replicas=len(reps))
+    x = torch.tensor(coords, device="cuda")
+    t = torch.tensor(types, device="cuda")
+    out = m.compute_batch(x, t, offs, boxes)
+    Ei = out["atom_energy"].cpu().numpy()
+    orc = oracle.Model(water_weights.to_blob())
+    for r, s in enumerate(reps):
+        sl = slice(offs[r], offs[r + 1])
+        # the sum over chunks equals this replica's per-atom energies summed on the host
+        assert out["energy"][r].item() == pytest.approx(Ei[sl].sum(), rel=1e-12)
+        ref = orc.compute(s.coords, s.types, s.box)
+        if prec == "fp64":
+            assert out["energy"][r].item() == pytest.approx(ref["energy"], rel=1e-11)
+            Fs = np.abs(ref["forces"]).max()
+            np.testing.assert_allclose(out["virial"][r].cpu().numpy(), ref["virial"], rtol=1e-9, atol=1e-12 * Fs)
+        else:
+            # the benchmark spec energy bar per atom
+            assert abs(out["energy"][r].item() - ref["energy"]) / s.natoms <= 1e-4
+    m.close()
